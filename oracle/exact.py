@@ -1,0 +1,364 @@
+"""Exact solvers for the replica Ising lattice: the oracle's own pins.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+* ``replica_links``      -- the link set of the replica lattice of section 3
+                            (eq. for H/T with couplings beta^(k,k), beta^(k,k+1)).
+* ``log_z_enumerate``    -- ln Z by brute-force enumeration of all states.
+* ``log_z2_transfer``    -- ln Z_2(l) by a transfer matrix along Euclidean time.
+* ``log_z_kaufman``      -- ln Z of the periodic 2D Ising torus in closed form
+                            (Kaufman 1949, ref. cited in section 4).
+* ``exact_path_measure`` -- the exact distribution of (final state, W_int) of the
+                            non-equilibrium Metropolis dynamics of Appendix A,
+                            propagated state by state for tiny lattices.
+
+Sites are numbered in the natural order ((r * L_t + t) * L_y + y) * L + x with
+n = 2 replicas; the cut is at tau_c = 0 (links t = 0 -> 1), region A = {x < l},
+and the switched column is x = l (section 3, protocol paragraph).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+N_REPLICA = 2
+
+
+def _site(L, L_t, L_y, r, t, y, x):
+    return ((r * L_t + t) * L_y + y) * L + x
+
+
+@dataclass
+class Links:
+    """Links of the replica lattice, each an (i, j) site pair.
+
+    full: couplings fixed at beta; self_: the switched column's links inside a
+    replica, coupling beta (1 - lambda); glue: the switched column's links to the
+    next replica, coupling beta lambda (section 3, linear protocol)."""
+    full: np.ndarray
+    self_: np.ndarray
+    glue: np.ndarray
+    n_sites: int
+
+
+def replica_links(d: int, L: int, L_t: int, l: int) -> Links:
+    """Every link once, from each site towards +x, +y (3D) and +t.
+
+    The +t link leaving t = 0 crosses the cut: for x < l it lands in replica
+    r + 1 (glued), for x > l in replica r, and for x = l both links exist with
+    the switched couplings (section 3, replica H/T and the linear protocol).
+    """
+    L_y = L if d == 3 else 1
+    full, self_, glue = [], [], []
+    for r in range(N_REPLICA):
+        for t in range(L_t):
+            for y in range(L_y):
+                for x in range(L):
+                    i = _site(L, L_t, L_y, r, t, y, x)
+                    full.append((i, _site(L, L_t, L_y, r, t, y, (x + 1) % L)))
+                    if d == 3:
+                        full.append((i, _site(L, L_t, L_y, r, t, (y + 1) % L_y, x)))
+                    tn = (t + 1) % L_t
+                    same = _site(L, L_t, L_y, r, tn, y, x)
+                    if t != 0:
+                        full.append((i, same))
+                        continue
+                    other = _site(L, L_t, L_y, (r + 1) % N_REPLICA, tn, y, x)
+                    if x < l:
+                        full.append((i, other))
+                    elif x > l:
+                        full.append((i, same))
+                    else:
+                        self_.append((i, same))
+                        glue.append((i, other))
+    as_arr = lambda v: np.array(v, dtype=np.int64).reshape(-1, 2)
+    return Links(as_arr(full), as_arr(self_), as_arr(glue), N_REPLICA * L_t * L_y * L)
+
+
+def _spins_of_states(n_sites: int) -> np.ndarray:
+    """sigma[state, i] = +1 if bit i of state is 0 else -1 (int8)."""
+    states = np.arange(1 << n_sites, dtype=np.int64)
+    bits = (states[:, None] >> np.arange(n_sites, dtype=np.int64)[None, :]) & 1
+    return (1 - 2 * bits).astype(np.int8)
+
+
+def _bond_sums(sigma: np.ndarray, pairs: np.ndarray) -> np.ndarray:
+    if len(pairs) == 0:
+        return np.zeros(sigma.shape[0], dtype=np.int64)
+    return (sigma[:, pairs[:, 0]].astype(np.int64) * sigma[:, pairs[:, 1]]).sum(axis=1)
+
+
+def _logsumexp(v: np.ndarray) -> float:
+    m = float(np.max(v))
+    return m + math.log(float(np.sum(np.exp(v - m))))
+
+
+def log_z_enumerate(d: int, L: int, L_t: int, l: int, beta: float, lam: float = 0.0) -> float:
+    """ln Z_2 of the replica lattice at protocol parameter lambda by summing
+    exp(-H/T) over all 2^V states (H/T of section 3 with the switched column's
+    couplings beta (1 - lambda), beta lambda).  V <= 20."""
+    lk = replica_links(d, L, L_t, l)
+    sigma = _spins_of_states(lk.n_sites)
+    e = (_bond_sums(sigma, lk.full) + (1.0 - lam) * _bond_sums(sigma, lk.self_)
+         + lam * _bond_sums(sigma, lk.glue))
+    return _logsumexp(beta * e)
+
+
+def log_z_single_enumerate(d: int, L: int, L_t: int, beta: float) -> float:
+    """ln Z of one periodic L^(d-1) x L_t Ising lattice by enumeration (eq. Ising_model)."""
+    L_y = L if d == 3 else 1
+    n = L_t * L_y * L
+    sigma = _spins_of_states(n)
+    pairs = []
+    for t in range(L_t):
+        for y in range(L_y):
+            for x in range(L):
+                i = (t * L_y + y) * L + x
+                pairs.append((i, (t * L_y + y) * L + (x + 1) % L))
+                if d == 3:
+                    pairs.append((i, (t * L_y + (y + 1) % L_y) * L + x))
+                pairs.append((i, (((t + 1) % L_t) * L_y + y) * L + x))
+    return _logsumexp(beta * _bond_sums(sigma, np.array(pairs)))
+
+
+# ----------------------------------------------------------- transfer matrix --
+def _slice_transfer(d: int, L: int, beta: float):
+    """Transfer matrix T(a, b) = w_space(a) w_time(a, b) between consecutive time
+    slices of one replica, normalised by its largest eigenvalue (ratios of
+    partition functions at equal L_t are unaffected).  Returns (T, column_of_bit)."""
+    L_y = L if d == 3 else 1
+    S = L * L_y
+    sig = _spins_of_states(S).astype(np.int64)        # bit (y * L + x)
+    space = np.zeros(1 << S, dtype=np.int64)
+    for y in range(L_y):
+        for x in range(L):
+            i = y * L + x
+            space += sig[:, i] * sig[:, y * L + (x + 1) % L]
+            if d == 3:
+                space += sig[:, i] * sig[:, ((y + 1) % L_y) * L + x]
+    overlap = sig @ sig.T                               # sum_x a(x) b(x)
+    T = np.exp(beta * space)[:, None] * np.exp(beta * overlap)
+    lam_max = np.max(np.abs(np.linalg.eigvals(T)))
+    column = np.array([i % L for i in range(S)])
+    return T / lam_max, column
+
+
+def log_z2_transfer(d: int, L: int, L_t: int, ls, beta: float) -> np.ndarray:
+    """ln Z_2(l) (up to an l-independent constant) for each l in ls.
+
+    Away from the cut both replicas evolve with T^(L_t) from slice t = 1 around
+    to the cut; the cut swaps the columns x < l of the two replicas' t = 1
+    slices (section 3: glue links join replica r at t = 0 to replica r+1 at
+    t = 1).  Hence Z_2(l) = sum_{a,b} P(a, mix(b, a)) P(b, mix(a, b)) with
+    P = T^(L_t) and mix(u, v) = u on columns x < l, v elsewhere.  The constant
+    is the same for every l at fixed (d, L, L_t, beta), so differences are exact.
+    """
+    T, column = _slice_transfer(d, L, beta)
+    P = np.linalg.matrix_power(T, L_t)
+    n = P.shape[0]
+    a = np.arange(n, dtype=np.int64)
+    out = []
+    for l in ls:
+        mask = 0
+        for bit, col in enumerate(column):
+            if col < l:
+                mask |= 1 << bit
+        A, B = np.meshgrid(a, a, indexing="ij")
+        mix_ba = (B & mask) | (A & ~mask)
+        mix_ab = (A & mask) | (B & ~mask)
+        z = np.sum(P[A, mix_ba] * P[B, mix_ab])
+        out.append(math.log(z))
+    return np.array(out)
+
+
+def delta_s2_transfer(d: int, L: int, L_t: int, beta: float) -> np.ndarray:
+    """Exact Delta S_2(l -> l+1) = -ln[Z_2(l+1)/Z_2(l)] for l = 0..L-1
+    (section 2, eq. trace_of_rho_n_as_ratio_of_partition_functions with n = 2)."""
+    lz = log_z2_transfer(d, L, L_t, range(L + 1), beta)
+    return -(lz[1:] - lz[:-1])
+
+
+# ----------------------------------------------------------------- Kaufman ---
+def log_z_kaufman(m: int, n: int, beta: float) -> float:
+    """ln Z of the periodic m x n square-lattice Ising model, coupling K = beta,
+    from Kaufman's solution (Phys. Rev. 76 (1949) 1232; the paper's ref. for
+    the 2D model in section 4):
+
+        Z = 1/2 (2 sinh 2K)^(mn/2) [Z1 + Z2 + Z3 + Z4],
+        Z1 = prod_{r<n} 2 cosh(m g_{2r+1}/2),  Z2 = prod 2 sinh(m g_{2r+1}/2),
+        Z3 = prod_{r<n} 2 cosh(m g_{2r}/2),    Z4 = prod 2 sinh(m g_{2r}/2),
+        cosh g_k = cosh 2K coth 2K - cos(pi k / n)  (k > 0),
+        g_0 = 2K + ln tanh K  (signed).
+    """
+    K = beta
+    c = math.cosh(2 * K) / math.tanh(2 * K)
+
+    def gamma(k):
+        if k == 0:
+            return 2 * K + math.log(math.tanh(K))
+        return math.acosh(c - math.cos(math.pi * k / n))
+
+    logs = []
+    signs = []
+    for parity, fn in ((1, "cosh"), (1, "sinh"), (0, "cosh"), (0, "sinh")):
+        lg, sg = 0.0, 1.0
+        for r in range(n):
+            g = gamma(2 * r + parity)
+            v = 2 * (math.cosh(m * g / 2) if fn == "cosh" else math.sinh(m * g / 2))
+            if v == 0.0:
+                lg, sg = -math.inf, 0.0
+                break
+            lg += math.log(abs(v))
+            sg *= math.copysign(1.0, v)
+        logs.append(lg)
+        signs.append(sg)
+    top = max(lg for lg in logs if lg > -math.inf)
+    total = sum(s * math.exp(lg - top) for s, lg in zip(signs, logs) if lg > -math.inf)
+    return math.log(0.5) + (m * n / 2) * math.log(2 * math.sinh(2 * K)) + top + math.log(total)
+
+
+# ------------------------------------------------------ exact path measure ---
+def _threshold(beta: float, m: int, n_step: int | None) -> int:
+    """The 32-bit Metropolis threshold floor(2^32 exp(-x)) saturated at 2^32 - 1,
+    x = 2 beta m (bulk) or (2 beta m)/N (switched site); flips with probability
+    T / 2^32."""
+    if n_step is None:
+        x = 2.0 * beta * float(m)
+    else:
+        x = (2.0 * beta * float(m)) / float(n_step)
+    return min(int(math.floor(math.ldexp(math.exp(-x), 32))), 2 ** 32 - 1)
+
+
+class _Dynamics:
+    """Single-site Metropolis probabilities of every site in every state of a
+    tiny replica lattice, at the start geometry or at protocol step k."""
+
+    def __init__(self, d, L, L_t, l, beta, n_step, direction, quantised):
+        self.d, self.L, self.L_t, self.l = d, L, L_t, l
+        self.beta, self.N, self.dir = beta, n_step, direction
+        self.quantised = quantised
+        self._cache = {}
+        self.links = replica_links(d, L, L_t, l)
+        self.V = self.links.n_sites
+        self.sigma = _spins_of_states(self.V).astype(np.int64)
+        L_y = L if d == 3 else 1
+        self.colour = np.zeros(self.V, dtype=np.int64)
+        for r in range(N_REPLICA):
+            for t in range(L_t):
+                for y in range(L_y):
+                    for x in range(L):
+                        self.colour[_site(L, L_t, L_y, r, t, y, x)] = (x + y + t) % 2
+        # per-site neighbour lists by link class (links are undirected)
+        self.nb = {cls: [[] for _ in range(self.V)] for cls in ("full", "self", "glue")}
+        for cls, pairs in (("full", self.links.full), ("self", self.links.self_),
+                           ("glue", self.links.glue)):
+            for i, j in pairs:
+                self.nb[cls][i].append(j)
+                self.nb[cls][j].append(i)
+
+    def flip_prob(self, i: int, k: int | None) -> np.ndarray:
+        """P(flip site i | state) for all states.  k = None: thermalisation at
+        the start geometry (forward: self-linked column, reverse: glued)."""
+        key = (i, k)
+        if key not in self._cache:
+            self._cache[key] = self._flip_prob(i, k)
+        return self._cache[key]
+
+    def _flip_prob(self, i: int, k: int | None) -> np.ndarray:
+        s = self.sigma
+        a = np.zeros(s.shape[0], dtype=np.int64)
+        for j in self.nb["full"][i]:
+            a += s[:, i] * s[:, j]
+        special = bool(self.nb["self"][i])
+        if special and k is None:
+            # the switched column is a bulk site at the start geometry
+            key = "self" if self.dir > 0 else "glue"
+            for j in self.nb[key][i]:
+                a += s[:, i] * s[:, j]
+            special = False
+        if not special:
+            m = a
+            x = 2.0 * self.beta * m
+            nstep = None
+        else:
+            (js,), (jg,) = self.nb["self"][i], self.nb["glue"][i]
+            b = s[:, i] * s[:, js]
+            c = s[:, i] * s[:, jg]
+            kp = k + 1                       # the update of step k uses lambda_{k+1}
+            w_self = self.N - kp if self.dir > 0 else kp
+            w_glue = kp if self.dir > 0 else self.N - kp
+            m = a * self.N + b * w_self + c * w_glue
+            x = (2.0 * self.beta * m) / self.N
+            nstep = self.N
+        if self.quantised:
+            um, inv = np.unique(m, return_inverse=True)
+            pu = np.array([1.0 if mm <= 0 else _threshold(self.beta, int(mm), nstep) / 2.0 ** 32
+                           for mm in um])
+            p = pu[inv.reshape(-1)]
+        else:
+            p = np.minimum(1.0, np.exp(-x))
+        return p
+
+    def sweep(self, f: np.ndarray, k: int | None) -> np.ndarray:
+        """Apply one checkerboard sweep (colour 0 then colour 1) to a density f
+        over states (last axis).  Sites of one colour are independent given the
+        other colour, so their single-site kernels are applied one after another."""
+        for col in (0, 1):
+            for i in np.nonzero(self.colour == col)[0]:
+                p = self.flip_prob(int(i), k)
+                partner = np.arange(f.shape[-1]) ^ (1 << int(i))
+                f = f * (1.0 - p) + (f * p)[..., partner]
+        return f
+
+    def work_increment(self) -> np.ndarray:
+        """dE(state) with dW_k = (beta/N) dE = H_{lambda_{k+1}} - H_{lambda_k}
+        (Appendix A, eq. work_in_one_MC_step): sum over the switched links of
+        (self - glue) bond products, sign flipped for the reverse protocol."""
+        e = _bond_sums(self.sigma, self.links.self_) - _bond_sums(self.sigma, self.links.glue)
+        return e if self.dir > 0 else -e
+
+    def energy(self, lam: float) -> np.ndarray:
+        lk = self.links
+        return -(_bond_sums(self.sigma, lk.full) + (1 - lam) * _bond_sums(self.sigma, lk.self_)
+                 + lam * _bond_sums(self.sigma, lk.glue))
+
+
+def exact_path_measure(d, L, L_t, l, beta, n_step, n_sweep, n_therm, *, direction=1,
+                       quantised=True, start="hot"):
+    """Exact joint law of (W_int, final state) of the non-equilibrium dynamics.
+
+    start="hot": uniform start (independent random spins) followed by n_therm
+    sweeps at the start geometry, as the Monte Carlo trajectories do;
+    start="equilibrium": exact Boltzmann weights pi_{lambda_0} (Appendix A,
+    eq. equilibrium_distribution), for the Jarzynski identity.
+    Returns (w_values, F) with F[w_index, state] the probability.
+    """
+    dyn = _Dynamics(d, L, L_t, l, beta, n_step, direction, quantised)
+    n_states = 1 << dyn.V
+    lam0 = 0.0 if direction > 0 else 1.0
+    if start == "hot":
+        f = np.full(n_states, 1.0 / n_states)
+        for _ in range(n_therm):
+            f = dyn.sweep(f, None)
+    else:
+        e = -beta * dyn.energy(lam0)
+        w = np.exp(e - e.max())
+        f = w / w.sum()
+    de = dyn.work_increment()
+    wmax = int(np.max(np.abs(de))) * n_step
+    F = np.zeros((2 * wmax + 1, n_states))
+    F[wmax] = f
+    for k in range(n_step):
+        G = np.zeros_like(F)
+        for dv in np.unique(de):
+            sel = de == dv
+            if dv >= 0:
+                G[dv:, sel] += F[:F.shape[0] - dv, sel]
+            else:
+                G[:dv, sel] += F[-dv:, sel]
+        F = G
+        for _ in range(n_sweep):
+            F = dyn.sweep(F, k)
+    return np.arange(-wmax, wmax + 1), F

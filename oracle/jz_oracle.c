@@ -1,0 +1,384 @@
+/*
+ * jz_oracle.c -- plain, slow CPU oracle for the Jarzynski replica-gluing method
+ * of Bulgarelli & Panero, "Entanglement entropy from non-equilibrium Monte Carlo
+ * simulations" (arXiv:2304.03311).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the checker, not the product: only the
+ * test suite, the smoke check and the CPU-baseline leg of the benchmark may load
+ * it.  It shares no code, header, table or constant generator with the CUDA
+ * library; both sides are written from the paper plus the bit-level conventions
+ * listed below, each in its own code.
+ *
+ * What it computes (paper section 3, eq. for H/T of the replica lattice, and
+ * Appendix A, eqs. A.1-A.6):
+ *   - n = 2 replicas of a periodic L^(d-1) x L_t Ising lattice, H/T = -beta sum s_i s_j
+ *     (section 1, eq. Ising_model);
+ *   - a cut at time slice tau_c = 0: the temporal link (x, t=0) - (x, t=1) joins
+ *     replica r to replica r+1 (mod n) for x < l and stays inside replica r for
+ *     x > l (section 3, the "beta^(k,k)" / "beta^(k,k+1)" couplings);
+ *   - the column x = l is switched: its self links carry beta (1 - lambda), its
+ *     glue links beta lambda, lambda_k = k/N (section 3, linear protocol);
+ *   - each trajectory: independent hot start, n_therm checkerboard Metropolis
+ *     sweeps at lambda_0, then for k = 0..N-1: accumulate
+ *     dW_k = H_{lambda_{k+1}}[phi_k] - H_{lambda_k}[phi_k] (Appendix A, eq.
+ *     work_in_one_MC_step) and update with the kernel at lambda_{k+1} (the
+ *     remark after eq. discretized_average_exp_work).
+ *   The work is kept as the exact integer W_int = sum_k dE_k with
+ *   dE_k = sum_{r,y} s^r(l,y,0) [s^r(l,y,1) - s^{r+1}(l,y,1)] so that
+ *   W = (beta / N) W_int; the reverse protocol (lambda from 1 to 0, start at
+ *   geometry l+1) flips the sign of dE_k.
+ *
+ * Bit-level conventions (not fixed by the paper; shared only as a written
+ * contract with the CUDA path, never as code):
+ *   colour       c = (x + y + t) mod 2; a sweep updates colour 0 then colour 1.
+ *   rows         R = (r * L_t + t) * L_y + y   (L_y = L in 3D, 1 in 2D).
+ *   row sites    the sites of colour c in row R are x = 2h + p, p = (c + t + y) mod 2,
+ *                h = 0 .. L/2-1; site h uses word (h mod 4) of Philox block q = h/4.
+ *   Philox       Philox4x32-10, key = (lo32(seed), hi32(seed)),
+ *                counter = (R * G + q, s, traj, c | dir<<1 | l<<2 | phase<<30),
+ *                G = ceil((L/2)/4), s = global sweep index (thermalisation sweeps
+ *                0..n_therm-1, protocol sweep i of step k: n_therm + k n_sweep + i),
+ *                dir = 0 forward / 1 reverse, phase = 0 sweep / 1 hot start (s = 0).
+ *   hot start    s_i = +1 if the top bit of its word is 0, else -1.
+ *   acceptance   flip iff m <= 0 or u < T, u the site's 32-bit word.
+ *                Bulk site: m = s_i sum_j s_j, T = floor(ldexp(exp(-x), 32))
+ *                saturated at 2^32 - 1, x = 2.0*beta*(double)m.
+ *                Switched site (x = l, t in {0,1}) during the protocol, step k:
+ *                a = s_i sum over its 2d-1 full-beta neighbours, b = s_i s_self,
+ *                c = s_i s_glue, m = a N + b w_self + c w_glue with
+ *                (w_self, w_glue) = (N-k-1, k+1) forward, (k+1, N-k-1) reverse,
+ *                x = (2.0*beta*(double)m)/(double)N, same T formula.
+ *                During thermalisation the switched column is a bulk site,
+ *                self-linked (forward) or glued (reverse).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ORACLE_MUTANT plants one known mistake for the tests that show the pins
+ * catch it (0 = the correct oracle; the library is always built with 0):
+ *   1 update of step k at lambda_k      2 work taken after the sweeps
+ *   3 region A not glued                4 forward start geometry glued at x = l
+ *   5 one spatial link dropped          6 sign of the work flipped
+ *   7 Boltzmann factor exp(-beta m)     */
+#ifndef ORACLE_MUTANT
+#define ORACLE_MUTANT 0
+#endif
+
+/* ---------------------------------------------------------------- Philox ---
+ * Philox4x32 with 10 rounds, from the definition in Salmon, Moraes, Dror and
+ * Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11): each round
+ * multiplies counter words 0 and 2 by the two round constants, swaps the high
+ * halves across and xors in the counter words 1, 3 and the round key; the key
+ * is bumped by the two Weyl constants between rounds. */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* ------------------------------------------------------------ thresholds ---
+ * Metropolis acceptance exp(-Delta H / T) with Delta H / T = 2 beta m (bulk) or
+ * 2 beta m / N (switched site), quantised to 32 bits: P(u < T) = T / 2^32. */
+static uint32_t quantise(double x)
+{
+    /* floor(2^32 e^-x), saturated at 2^32 - 1 (reached only when e^-x rounds
+     * to 1, e.g. beta = 0) */
+    double v = floor(ldexp(exp(-x), 32));
+    return v >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)v;
+}
+
+uint32_t oracle_threshold_bulk(double beta, int m)
+{
+    if (m <= 0) return 0xFFFFFFFFu; /* never consulted: m <= 0 always flips */
+    double x = (ORACLE_MUTANT == 7 ? 1.0 : 2.0) * beta * (double)m;
+    return quantise(x);
+}
+
+uint32_t oracle_threshold_cut(double beta, long long m, int n_step)
+{
+    if (m <= 0) return 0xFFFFFFFFu;
+    double x = (2.0 * beta * (double)m) / (double)n_step;
+    return quantise(x);
+}
+
+/* -------------------------------------------------------------- geometry --- */
+typedef struct {
+    int d, L, Lt, Ly, n;
+    int l;        /* the switched column                                     */
+    int dir;      /* +1 forward (l -> l+1), -1 reverse (l+1 -> l)            */
+} geom_t;
+
+static int site_of(const geom_t *g, int r, int t, int y, int x)
+{
+    return ((r * g->Lt + t) * g->Ly + y) * g->L + x;
+}
+
+static int wrap(int v, int n) { return ((v % n) + n) % n; }
+
+/* Classes of a link seen from a site. */
+enum { FULL = 0, SELF = 1, GLUE = 2 };
+
+/* Lists the 2d links of site (r,t,y,x): nbr[] = partner site, cls[] = FULL for a
+ * beta link, SELF / GLUE for the two switched links of the column x = l.
+ * protocol = 0 during thermalisation (switched column reduced to a bulk site),
+ * 1 during the non-equilibrium protocol.  Returns the number of entries (2d, or
+ * 2d+1 for a switched site, which has both a SELF and a GLUE partner). */
+static int links_of(const geom_t *g, int r, int t, int y, int x, int protocol,
+                    int nbr[8], int cls[8])
+{
+    int k = 0;
+    /* spatial x direction */
+    if (ORACLE_MUTANT != 5) {
+        nbr[k] = site_of(g, r, t, y, wrap(x - 1, g->L)); cls[k++] = FULL;
+    }
+    nbr[k] = site_of(g, r, t, y, wrap(x + 1, g->L)); cls[k++] = FULL;
+    /* spatial y direction (3D only) */
+    if (g->d == 3) {
+        nbr[k] = site_of(g, r, t, wrap(y - 1, g->Ly), x); cls[k++] = FULL;
+        nbr[k] = site_of(g, r, t, wrap(y + 1, g->Ly), x); cls[k++] = FULL;
+    }
+    /* temporal links: the link (t, t+1) is the cut link iff t == 0 */
+    for (int side = 0; side < 2; ++side) {
+        /* side 0: the link below the site (t-1, t); side 1: above (t, t+1) */
+        int tn = side == 0 ? wrap(t - 1, g->Lt) : wrap(t + 1, g->Lt);
+        int lower_t = side == 0 ? tn : t;      /* time of the link's lower end */
+        int is_cut = (lower_t == 0);
+        if (!is_cut) {
+            nbr[k] = site_of(g, r, tn, y, x); cls[k++] = FULL;
+            continue;
+        }
+        /* across the cut, the glue partner of replica r is replica r+1 above
+         * the cut and replica r-1 below it */
+        int rg = side == 1 ? wrap(r + 1, g->n) : wrap(r - 1, g->n);
+        int self_site = site_of(g, r, tn, y, x);
+        int glue_site = site_of(g, rg, tn, y, x);
+        if (x < g->l) {
+            nbr[k] = ORACLE_MUTANT == 3 ? self_site : glue_site; cls[k++] = FULL;
+        } else if (x > g->l) {
+            nbr[k] = self_site; cls[k++] = FULL;
+        } else if (!protocol) {
+            /* thermalisation at the start geometry: forward starts at
+             * lambda = 0 (self-linked), reverse at lambda = 1 (glued) */
+            nbr[k] = (g->dir > 0) != (ORACLE_MUTANT == 4) ? self_site : glue_site;
+            cls[k++] = FULL;
+        } else {
+            nbr[k] = self_site; cls[k++] = SELF;
+            nbr[k] = glue_site; cls[k++] = GLUE;
+        }
+    }
+    return k;
+}
+
+/* ------------------------------------------------------------ trajectory --- */
+typedef struct {
+    geom_t g;
+    double beta;
+    int n_step, n_sweep, n_therm;
+    uint32_t key[2];
+    uint32_t bulk_T[8];   /* indexed by m/2 for m = 2, 4, ..., 2d */
+    const uint32_t *cut_T; /* [n_step][table], see cut_index() */
+} run_t;
+
+/* The switched-site table of one step is indexed by a (odd, |a| <= 2d-1), b, c. */
+static int cut_index(const geom_t *g, int a, int b, int c)
+{
+    int ia = (a + 2 * g->d - 1) / 2;
+    return (ia * 2 + (b > 0)) * 2 + (c > 0);
+}
+
+static uint32_t word_for(const run_t *R, int colour, int phase, int sweep,
+                         long long traj, int r, int t, int y, int x)
+{
+    const geom_t *g = &R->g;
+    int Lh = g->L / 2;
+    int G = (Lh + 3) / 4;
+    int row = (r * g->Lt + t) * g->Ly + y;
+    int h = x / 2;
+    uint32_t ctr[4], out[4];
+    ctr[0] = (uint32_t)(row * G + h / 4);
+    ctr[1] = (uint32_t)sweep;
+    ctr[2] = (uint32_t)traj;
+    ctr[3] = (uint32_t)colour | ((uint32_t)(g->dir < 0) << 1) |
+             ((uint32_t)g->l << 2) | ((uint32_t)phase << 30);
+    oracle_philox4x32_10(ctr, R->key, out);
+    return out[h % 4];
+}
+
+static int colour_of(int t, int y, int x) { return (x + y + t) & 1; }
+
+/* One checkerboard sweep at protocol step k (k < 0: thermalisation). */
+static void sweep(const run_t *R, int8_t *s, long long traj, int sweep_index, int k)
+{
+    const geom_t *g = &R->g;
+    int protocol = k >= 0;
+    long long N = R->n_step;
+    long long w_self = 0, w_glue = 0;
+    if (protocol) {
+        long long kp = ORACLE_MUTANT == 1 ? k : k + 1; /* step k updates at lambda_{k+1} */
+        w_self = g->dir > 0 ? N - kp : kp;
+        w_glue = g->dir > 0 ? kp : N - kp;
+    }
+    for (int colour = 0; colour < 2; ++colour) {
+        for (int r = 0; r < g->n; ++r)
+        for (int t = 0; t < g->Lt; ++t)
+        for (int y = 0; y < g->Ly; ++y)
+        for (int x = 0; x < g->L; ++x) {
+            if (colour_of(t, y, x) != colour) continue;
+            int i = site_of(g, r, t, y, x);
+            int nbr[8], cls[8];
+            int nl = links_of(g, r, t, y, x, protocol, nbr, cls);
+            int a = 0, b = 0, c = 0, special = 0;
+            for (int j = 0; j < nl; ++j) {
+                int prod = s[i] * s[nbr[j]];
+                if (cls[j] == FULL) a += prod;
+                else if (cls[j] == SELF) { b = prod; special = 1; }
+                else { c = prod; special = 1; }
+            }
+            uint32_t u = word_for(R, colour, 0, sweep_index, traj, r, t, y, x);
+            int flip;
+            if (!special) {
+                int m = a;
+                flip = (m <= 0) || (u < R->bulk_T[m / 2]);
+            } else {
+                long long m = (long long)a * N + b * w_self + c * w_glue;
+                const uint32_t *T = R->cut_T + (size_t)k * (size_t)(8 * g->d);
+                flip = (m <= 0) || (u < T[cut_index(g, a, b, c)]);
+            }
+            if (flip) s[i] = (int8_t)(-s[i]);
+        }
+    }
+}
+
+/* dE_k = H_{lambda_{k+1}} - H_{lambda_k} on the current configuration, in
+ * units of beta / N (Appendix A, eq. work_in_one_MC_step). */
+static long long work_increment(const run_t *R, const int8_t *s)
+{
+    const geom_t *g = &R->g;
+    long long e = 0;
+    for (int r = 0; r < g->n; ++r)
+    for (int y = 0; y < g->Ly; ++y) {
+        int lo = site_of(g, r, 0, y, g->l);
+        int up_self = site_of(g, r, 1, y, g->l);
+        int up_glue = site_of(g, wrap(r + 1, g->n), 1, y, g->l);
+        e += (long long)s[lo] * (s[up_self] - s[up_glue]);
+    }
+    return (g->dir > 0) != (ORACLE_MUTANT == 6) ? e : -e;
+}
+
+static void hot_start(const run_t *R, int8_t *s, long long traj)
+{
+    const geom_t *g = &R->g;
+    for (int r = 0; r < g->n; ++r)
+    for (int t = 0; t < g->Lt; ++t)
+    for (int y = 0; y < g->Ly; ++y)
+    for (int x = 0; x < g->L; ++x) {
+        uint32_t u = word_for(R, colour_of(t, y, x), 1, 0, traj, r, t, y, x);
+        s[site_of(g, r, t, y, x)] = (u >> 31) ? -1 : 1;
+    }
+}
+
+static long long run_trajectory(const run_t *R, long long traj, int8_t *s)
+{
+    hot_start(R, s, traj);
+    for (int i = 0; i < R->n_therm; ++i) sweep(R, s, traj, i, -1);
+    long long w = 0;
+    for (int k = 0; k < R->n_step; ++k) {
+        if (ORACLE_MUTANT != 2) w += work_increment(R, s);
+        for (int i = 0; i < R->n_sweep; ++i)
+            sweep(R, s, traj, R->n_therm + k * R->n_sweep + i, k);
+        if (ORACLE_MUTANT == 2) w += work_increment(R, s);
+    }
+    return w;
+}
+
+/* ------------------------------------------------------------- entry point --
+ * Runs trajectories traj0 .. traj0+n_traj-1 of one transformation l -> l+1
+ * (dir = +1) or l+1 -> l (dir = -1).  work_out[i] = W_int of trajectory
+ * traj0 + i; spins_out (nullable) receives the final configuration of each
+ * trajectory as int8 +-1 in the natural order [traj][r][t][y][x].
+ * n_threads > 0 sets the OpenMP thread count (trajectories are independent, so
+ * the result does not depend on it).  Returns 0, or -1 on bad arguments. */
+int oracle_run(int d, int L, int Lt, double beta, int l, int n_step, int n_sweep,
+               int n_therm, int dir, uint64_t seed, long long traj0, int n_traj,
+               int n_threads, long long *work_out, int8_t *spins_out)
+{
+    if ((d != 2 && d != 3) || L < 2 || Lt < 2 || (L & 1) || (Lt & 1)) return -1;
+    if (l < 0 || l >= L || n_step < 1 || n_sweep < 0 || n_therm < 0) return -1;
+    if (dir != 1 && dir != -1) return -1;
+    run_t R;
+    memset(&R, 0, sizeof R);
+    R.g.d = d; R.g.L = L; R.g.Lt = Lt; R.g.Ly = d == 3 ? L : 1; R.g.n = 2;
+    R.g.l = l; R.g.dir = dir;
+    R.beta = beta; R.n_step = n_step; R.n_sweep = n_sweep; R.n_therm = n_therm;
+    R.key[0] = (uint32_t)seed; R.key[1] = (uint32_t)(seed >> 32);
+    for (int m = 2; m <= 2 * d; m += 2) R.bulk_T[m / 2] = oracle_threshold_bulk(beta, m);
+    int per_step = 8 * d;
+    uint32_t *cut = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n_step * per_step);
+    if (!cut) return -1;
+    for (int k = 0; k < n_step; ++k) {
+        long long kp = k + 1;
+        long long w_self = dir > 0 ? n_step - kp : kp;
+        long long w_glue = dir > 0 ? kp : n_step - kp;
+        for (int a = -(2 * d - 1); a <= 2 * d - 1; a += 2)
+        for (int b = -1; b <= 1; b += 2)
+        for (int c = -1; c <= 1; c += 2) {
+            long long m = (long long)a * n_step + b * w_self + c * w_glue;
+            cut[(size_t)k * per_step + cut_index(&R.g, a, b, c)] =
+                oracle_threshold_cut(beta, m, n_step);
+        }
+    }
+    R.cut_T = cut;
+    int V = 2 * L * Lt * R.g.Ly;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+    int failed = 0;
+#pragma omp parallel
+    {
+        int8_t *s = (int8_t *)malloc((size_t)V);
+        if (!s) {
+#pragma omp atomic write
+            failed = 1;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int i = 0; i < n_traj; ++i) {
+            if (!s) continue;
+            work_out[i] = run_trajectory(&R, traj0 + i, s);
+            if (spins_out) memcpy(spins_out + (size_t)i * V, s, (size_t)V);
+        }
+        free(s);
+    }
+    free(cut);
+    return failed ? -1 : 0;
+}
+
+/* Number of OpenMP threads a parallel region would use (1 without OpenMP). */
+int oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
