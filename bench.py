@@ -1,0 +1,398 @@
+#!/usr/bin/env python3
+"""Benchmark of the Jarzynski replica-gluing path on one or more GB300s.
+
+A step is one pass of the whole method over one batch: the 2D critical Ising
+c-function scan (L = L_t = 64, transformations l -> l+1 for l = 0..30, N = 1000
+steps of 2 sweeps, 1000 thermalisation sweeps, 16384 trajectories per l) run as
+one device launch, then the FP64 estimator per l on the device and the
+c-function on the host.  With --config 1 or 3 the step is the 2D L = 16 single
+transformation or the 3D slab scan instead.
+
+Output: one JSON line on rank 0.  value = spin updates per second over all
+ranks (every site visit of thermalisation and protocol), device-timed with CUDA
+events; e2e = the same through the C ABI with host buffers.  --impl reference
+times the CPU oracle (the plain C program) on the host cores instead.
+
+Multi-GPU (torchrun): each rank runs its own trajectory range of every l
+(weak scaling); the per-l work arrays are all-gathered before the estimator.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2304_03311_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "spin-updates/s and Jarzynski trajectories/s per GB300 at fixed c-function error"
+UNIT = "spin-updates/s"
+# Algorithmic integer operations per spin update (Philox4x32-10 share, local
+# field and acceptance), fixed a priori for the roofline.
+N_ALG = {2: 32, 3: 36}
+SM_COUNT, INT_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", type=int, choices=[1, 2, 3], default=2)
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def workload_for(config: int, rank: int):
+    w = wl.CONFIGS[config]()
+    # weak scaling: rank r owns trajectories [r n, (r+1) n) of every job
+    w.jobs = [j.with_(traj0=rank * j.n_traj) for j in w.jobs]
+    return w
+
+
+def config_block(w, config, world):
+    j0 = w.jobs[0]
+    ls = [j.l for j in w.jobs]
+    return {"workload": w.name, "d": j0.d, "L": j0.L, "L_t": j0.L_t, "beta": j0.beta,
+            "l": f"{min(ls)}-{max(ls)}" if len(ls) > 1 else ls[0],
+            "n_step": j0.n_step, "n_sweep": j0.n_sweep, "n_therm": j0.n_therm,
+            "n_traj_per_l": j0.n_traj * world, "replicas": 2,
+            "l2": "flushed between steps (512 MiB write)",
+            "parallelism": f"trajectory shards x{world}" if world > 1 else "single GPU",
+            "source_config": config}
+
+
+# ----------------------------------------------------------------- clocks --
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU oracle ----
+def cpu_oracle_rate(w, seconds: float):
+    """Times the oracle (as it stands) on the host cores on a bounded sample of
+    the workload: trajectories of up to 4 evenly spaced jobs, all cores."""
+    import oracle
+    oracle.build()
+    threads = oracle.max_threads()
+    jobs = w.jobs[:: max(1, len(w.jobs) // 4)][:4]
+    # one round (one trajectory per thread) to size the sample
+    j = jobs[0]
+    t0 = time.perf_counter()
+    oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, threads, j.seed,
+               n_therm=j.n_therm, traj0=j.traj0, n_threads=threads)
+    t_round = time.perf_counter() - t0
+    rounds = max(1, int(seconds / max(t_round, 1e-3) / len(jobs)))
+    n_per_job = rounds * threads
+    t0 = time.perf_counter()
+    updates = 0
+    for j in jobs:
+        oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, n_per_job, j.seed,
+                   n_therm=j.n_therm, traj0=j.traj0, n_threads=threads)
+        updates += j.with_(n_traj=n_per_job).updates
+    dt = time.perf_counter() - t0
+    sample = (f"{n_per_job} trajectories at each of l = {[j.l for j in jobs]} of the same "
+              f"workload ({updates:.3e} spin updates, {dt:.1f} s)")
+    return updates / dt, len(jobs) * n_per_job / dt, threads, sample
+
+
+def traffic_from_profile(src_hash: str):
+    path = os.path.join(ROOT, "profiles", "traj_kernel_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_sha256") != src_hash:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def kernel_source_hash():
+    csrc = os.path.join(ROOT, "paper_2304_03311_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()
+
+
+def c_function_errors(w, results):
+    import math as m
+    out = []
+    for j, (ds, err) in zip(w.jobs, results):
+        x = (j.l + 0.5) / j.L
+        fac = (j.L / m.pi * m.sin(m.pi * x)) ** (j.d - 1) / (2.0 * j.L ** (j.d - 2))
+        out.append((fac * ds, fac * err))
+    return out
+
+
+# ------------------------------------------------------------ our arm -------
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local_rank = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local_rank)
+    from paper_2304_03311_gb300 import build as jzbuild
+    if rank == 0 or world == 1:
+        jzbuild.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2304_03311_gb300 as jz
+
+    w = workload_for(args.config, rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = jz.ising_replica_init(local_rank, 0, stream.cuda_stream)
+    outs = [torch.empty(j.n_traj, dtype=torch.int64, device=dev) for j in w.jobs]
+    params = [jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj,
+                             j.seed, n_therm=j.n_therm, direction=j.direction, traj0=j.traj0)
+              for j in w.jobs]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    n_groups = len({(j.d, j.L, j.L_t, j.seed) for j in w.jobs})
+
+    def estimate(buffers, gathered_world):
+        res = []
+        for j, b in zip(w.jobs, buffers):
+            _, ds, err = jz.estimator_reduce(ctx, b, j.n_traj * gathered_world, j.beta,
+                                             j.n_step, j.direction, 32)
+            res.append((ds, err))
+        return res
+
+    def step():
+        k0 = torch.cuda.Event(enable_timing=True)
+        k1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            k0.record(stream)
+            jz.jarzynski_run_batch(ctx, params, outs)
+            k1.record(stream)
+            bufs = outs
+            if world > 1:
+                bufs = []
+                for o in outs:
+                    parts = [torch.empty_like(o) for _ in range(world)]
+                    dist.all_gather(parts, o)
+                    bufs.append(torch.cat(parts))
+            res = estimate(bufs, world)
+        return (k0, k1), c_function_errors(w, res)
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+
+    for _ in range(args.warmup):
+        step()
+        flush_l2()
+    stream.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    kernel_pairs = []
+    t_start.record(stream)
+    cfun = None
+    for i in range(args.steps):
+        pair, cfun = step()
+        kernel_pairs.append(pair)
+        if i + 1 < args.steps:
+            flush_l2()
+    t_end.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    kernel_ms = statistics.mean(a.elapsed_time(b) for a, b in kernel_pairs)
+    if world > 1:
+        t = torch.tensor([elapsed_ms, kernel_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms, kernel_ms = float(t[0]), float(t[1])
+    ms_per_step = elapsed_ms / args.steps
+    updates_step = w.updates * world
+    value = updates_step / (ms_per_step / 1e3)
+    traj_rate = w.trajectories * world / (ms_per_step / 1e3)
+
+    # end to end through the C ABI with host buffers: work arrays copied back
+    # each step, the estimator fed from host memory
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(1, args.steps // 2)
+    host_outs = [np.empty(j.n_traj, dtype=np.int64) for j in w.jobs]
+    stream.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            jz.jarzynski_run_batch(ctx, params, host_outs)
+            if world > 1:
+                gathered = []
+                for h in host_outs:
+                    parts = [torch.empty(len(h), dtype=torch.int64) for _ in range(world)]
+                    dist.all_gather(parts, torch.from_numpy(h).to(dev))
+                    gathered.append(torch.cat([p.cpu() for p in parts]).numpy())
+            else:
+                gathered = host_outs
+            estimate(gathered, world)
+    stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t[0])
+    table_bytes = sum(j.n_step * 8 * j.d * 4 + 96 for j in w.jobs)
+    h2d = table_bytes + sum(8 * j.n_traj * world for j in w.jobs)
+    d2h = sum(8 * j.n_traj for j in w.jobs) + 24 * len(w.jobs)
+    e2e = {"value": updates_step / (e2e_s / e2e_steps), "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
+
+    d = w.jobs[0].d
+    updates_per_launch = w.updates   # one launch per rank per step
+    achieved = N_ALG[d] * updates_per_launch / (kernel_ms / 1e3) / 1e12
+    peak = SM_COUNT * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    src_hash = kernel_source_hash()
+    roofline = {"bound": "alu", "kernel": f"traj_kernel<{d},...>", "achieved": achieved,
+                "peak": peak, "unit": "Tintop/s", "frac": achieved / peak,
+                "traffic": traffic_from_profile(src_hash),
+                "ops_per_update": N_ALG[d], "kernel_ms": kernel_ms,
+                "peak_basis": "152 SMs x 128 int lanes/clk x 2070 MHz (derived)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, trate, cores, sample = cpu_oracle_rate(w, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "trajectories_per_s": trate}
+    jz.ising_replica_free(ctx)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "u32", "data": "synthetic (Philox hot starts; no dataset)",
+                "config": config_block(w, args.config, world),
+                "trajectories_per_s": traj_rate,
+                "c_function_err_max": max(e for _, e in cfun) if cfun else None,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": args.steps * (n_groups + len(w.jobs)),
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------- reference arm -----
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    threads = oracle.max_threads()
+    w = workload_for(args.config, 0)
+    jobs = w.jobs[:: max(1, len(w.jobs) // 2)][:2]
+    n_per = threads
+
+    def step():
+        u = 0
+        for j in jobs:
+            oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, n_per, j.seed,
+                       n_therm=j.n_therm, traj0=j.traj0, n_threads=threads)
+            u += j.with_(n_traj=n_per).updates
+        return u
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    updates = 0
+    for _ in range(args.steps):
+        updates += step()
+    dt = time.perf_counter() - t0
+    value = updates / dt
+    sample = (f"per step {n_per} trajectories at each of l = {[j.l for j in jobs]} of "
+              f"{w.name}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
+            "data": "synthetic (Philox hot starts; no dataset)",
+            "config": config_block(w, args.config, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

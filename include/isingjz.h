@@ -1,0 +1,160 @@
+/*
+ * isingjz.h -- C ABI of the GB300 (sm_103a) library for the Jarzynski
+ * replica-gluing estimator of Renyi-2 entanglement entropy increments and the
+ * entropic c-function (Bulgarelli & Panero, arXiv:2304.03311).
+ *
+ * What the library computes (one "transformation" l -> l+1):
+ *   n = 2 replicas of a periodic Ising lattice of L^(d-1) x L_t sites
+ *   (section 1, eq. Ising_model: H/T = -beta sum s_i s_j) are cut at the time
+ *   slice tau_c = 0: for columns x < l the temporal link t = 0 -> 1 joins
+ *   replica r to replica r+1, for x > l it stays in replica r (section 3, the
+ *   replica H/T with couplings beta^(k,k), beta^(k,k+1)).  The column x = l is
+ *   switched linearly, self coupling beta (1 - lambda_k), glue coupling
+ *   beta lambda_k, lambda_k = k/N (section 3, last paragraphs of the protocol
+ *   description).  Each trajectory starts from an independent hot start and
+ *   n_therm checkerboard Metropolis sweeps at lambda_0, then for k = 0..N-1
+ *   accumulates the integer work increment dE_k = H_{lambda_{k+1}} -
+ *   H_{lambda_k} in units of beta/N (Appendix A, eq. work_in_one_MC_step) and
+ *   runs n_sweep sweeps at lambda_{k+1} (Appendix A, remark after eq.
+ *   discretized_average_exp_work).  <e^-W>, W = beta W_int / N, estimates
+ *   Z_2(l+1)/Z_2(l) (Appendix A, eq. Jarzynski_theorem), so
+ *   Delta S_2 = -ln <e^-W> (section 2, eq. definition_of_derivative_of_Renyi_entropy).
+ *
+ * Bit-level conventions (random stream and acceptance) are fixed so that runs
+ * are reproducible and independent of batching:
+ *   colour  c = (x + y + t) mod 2, colour 0 then colour 1 in each sweep;
+ *   row     R = (r L_t + t) L_y + y (L_y = L in 3D, 1 in 2D); the colour-c sites
+ *           of a row are x = 2h + ((c + t + y) mod 2), h < L/2; site h takes
+ *           word h mod 4 of the Philox4x32-10 block q = h / 4 with
+ *           counter (R ceil(L/8) + q, s, traj, c | dir<<1 | l<<2 | phase<<30),
+ *           key (lo32 seed, hi32 seed); s = 0..n_therm-1 for thermalisation and
+ *           n_therm + k n_sweep + i for protocol sweep i of step k; phase 1 with
+ *           s = 0 is the hot start (spin -1 iff the word's top bit is set);
+ *   accept  flip iff m <= 0 or word < T, T = min(floor(2^32 exp(-x)), 2^32-1),
+ *           bulk: m = s_i sum_j s_j, x = 2.0*beta*m;
+ *           switched site in the protocol: m = a N + b w_self + c w_glue with
+ *           a the sum over its 2d-1 fixed links, b, c its self and glue bond
+ *           products, (w_self, w_glue) = (N-k-1, k+1) forward and
+ *           (k+1, N-k-1) reverse, x = (2.0*beta*m)/N.  Thresholds are computed
+ *           on the host in IEEE double with the C library's exp.
+ *
+ * Memory: the caller owns every output buffer; the library owns its device
+ * state.  Output pointers may be host or device memory: with device memory
+ * the call only enqueues work on the context's stream (use ising_sync); with
+ * host memory the call copies back and returns when the result is there.
+ * Errors are returned as negative codes; nothing throws across this ABI.
+ * A context must not be used from two host threads at once.
+ */
+#ifndef ISINGJZ_H
+#define ISINGJZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------- error codes -- */
+#define ISING_OK               0
+#define ISING_ERR_ARG         -1  /* null pointer, non-positive count, bad beta  */
+#define ISING_ERR_ODD_EXTENT  -2  /* L or L_t odd (checkerboard needs even)      */
+#define ISING_ERR_L_RANGE     -3  /* l outside 0 <= l <= L-1                     */
+#define ISING_ERR_NOMEM       -4  /* device allocation or HBM budget exceeded    */
+#define ISING_ERR_CUDA        -5  /* a CUDA runtime call failed                  */
+#define ISING_ERR_TIMEOUT     -6  /* a bounded device wait gave up               */
+#define ISING_ERR_UNSUPPORTED -7  /* d not in {2,3}, lattice too large for SMEM  */
+#define ISING_ERR_NOT_FOUND   -8  /* unknown job id                              */
+#define ISING_ERR_PENDING     -9  /* job not finished yet (jz_poll)              */
+
+/* Opaque per-device context: stream, device buffers, autotune choices. */
+typedef struct ising_ctx ising_ctx;
+
+/* One transformation l -> l+1 (direction +1) or l+1 -> l (direction -1).
+ *   d          lattice dimension D, 2 or 3 (section 3, "extension to higher
+ *              dimensions"); time is one of the D directions
+ *   L, L_t     spatial and temporal extents, both even, L >= 2, L_t >= 2
+ *   beta       coupling, 0 <= beta <= 4
+ *   l          width of region A before the move, 0 <= l <= L-1
+ *   n_step     N >= 1 protocol steps, n_sweep >= 1 sweeps per step
+ *   n_therm    thermalisation sweeps of the start ensemble (section 4 uses 1000)
+ *   n_traj     trajectories, traj0 the global index of the first one (the index
+ *              enters the random counter, so a range split gives the same result)
+ *   seed       Philox key */
+typedef struct jz_params {
+    int d, L, L_t;
+    double beta;
+    int l;
+    int n_step, n_sweep, n_therm;
+    int n_traj;
+    int direction;
+    long long traj0;
+    uint64_t seed;
+} jz_params;
+
+/* Fills *p with defaults (n_therm = 1000, direction = +1, traj0 = 0, n_sweep = 1,
+ * seed = 0) and zero sizes; returns ISING_OK or ISING_ERR_ARG for p == NULL. */
+int jz_params_default(jz_params* p);
+
+/* Creates a context on CUDA device `device`.
+ *   hbm_budget_bytes  cap on the library's own device allocations (0 = no cap);
+ *                     exceeding it returns ISING_ERR_NOMEM
+ *   cuda_stream       cudaStream_t to enqueue on (NULL = the library creates one)
+ * Writes the context to *out.  Errors: ISING_ERR_ARG, ISING_ERR_CUDA. */
+int ising_replica_init(ising_ctx** out, int device, size_t hbm_budget_bytes,
+                       void* cuda_stream);
+
+/* Releases the context and its device memory (waits for queued work). */
+void ising_replica_free(ising_ctx* ctx);
+
+/* Blocks until all work queued on the context's stream is done.  Returns
+ * ISING_OK, or the first deferred error of queued work. */
+int ising_sync(ising_ctx* ctx);
+
+/* Runs n_traj trajectories of the forward transformation l -> l+1 with
+ * n_therm = 1000 and trajectory indices 0..n_traj-1 (section 3 protocol,
+ * Appendix A work).  work_int_out[i] (caller-owned, n_traj int64 entries,
+ * host or device memory) receives W_int of trajectory i; W = beta W_int / N.
+ * Errors: ISING_ERR_ARG, ISING_ERR_ODD_EXTENT, ISING_ERR_L_RANGE,
+ * ISING_ERR_UNSUPPORTED, ISING_ERR_NOMEM, ISING_ERR_CUDA. */
+int jarzynski_run(ising_ctx* ctx, int d, int L, int L_t, double beta, int l,
+                  int n_step, int n_sweep, int n_traj, uint64_t seed,
+                  int64_t* work_int_out);
+
+/* As jarzynski_run with every parameter of jz_params.  spins_out (nullable,
+ * caller-owned, host or device) receives the final configuration of each
+ * trajectory as int8 +-1 in the order [traj][r][t][y][x] (x fastest, n_traj *
+ * 2 * L_t * L_y * L bytes). */
+int jarzynski_run_ex(ising_ctx* ctx, const jz_params* p, int64_t* work_int_out,
+                     int8_t* spins_out);
+
+/* Runs n_jobs transformations in one device launch per lattice shape (jobs of
+ * equal (d, L, L_t) share a launch; the c-function scan of section 3 is one
+ * call with one job per l).  work_outs[j] is job j's caller-owned output of
+ * jobs[j].n_traj entries; all of them must be host memory, or all device
+ * memory.  Each job's result is bit-identical to running it alone. */
+int jarzynski_run_batch(ising_ctx* ctx, const jz_params* jobs, int n_jobs,
+                        int64_t* const* work_outs);
+
+/* FP64 estimator on the device (Appendix A, eq. Jarzynski_theorem; section 2):
+ *   *log_ratio    = ln <e^-W>, W_i = beta work_int[i] / n_step, evaluated as a
+ *                   max-shifted log-sum-exp
+ *   *delta_S2     = -ln <e^-W> for direction +1, +ln <e^-W> for direction -1
+ *   *delta_S2_err = blocked jackknife error of delta_S2 with
+ *                   B = min(n_jack_bins, n_traj) contiguous blocks of n_traj / B
+ *                   trajectories, the remainder in the last block (0 if B < 2)
+ * work_int: n_traj entries, host or device memory (not modified).  Output
+ * pointers are host memory; the call returns when they are written.
+ * Errors: ISING_ERR_ARG, ISING_ERR_CUDA. */
+int estimator_reduce(ising_ctx* ctx, const int64_t* work_int, int n_traj, double beta,
+                     int n_step, int direction, int n_jack_bins, double* log_ratio,
+                     double* delta_S2, double* delta_S2_err);
+
+/* Human-readable text for an error code (static storage). */
+const char* ising_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISINGJZ_H */

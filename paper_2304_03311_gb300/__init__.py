@@ -1,0 +1,178 @@
+"""GB300 (sm_103a) library for the Jarzynski replica-gluing estimator of
+Renyi-2 entanglement entropy increments and the entropic c-function
+(Bulgarelli & Panero, arXiv:2304.03311).
+
+This module is a thin ctypes binding of the C ABI declared in
+``include/isingjz.h``: same names, same arguments, marshalling only.  Every step
+of the method runs in the CUDA kernels of ``libisingjz.so``; there is no CPU
+fallback, and importing the binding fails loudly when the library is missing.
+
+Buffers may be torch tensors (CUDA or CPU) or numpy arrays; the library
+decides from the pointer whether it writes device memory directly (the call
+then only enqueues work; use ``ising_sync``) or copies back to host memory.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import LIB as _LIB_PATH
+
+__all__ = [
+    "IsingError", "JzParams", "lib_path", "load", "ising_replica_init", "ising_replica_free",
+    "ising_sync", "jarzynski_run", "jarzynski_run_ex", "jarzynski_run_batch",
+    "estimator_reduce", "ising_strerror", "jz_params_default",
+]
+
+ISING_OK = 0
+ISING_ERR_ARG = -1
+ISING_ERR_ODD_EXTENT = -2
+ISING_ERR_L_RANGE = -3
+ISING_ERR_NOMEM = -4
+ISING_ERR_CUDA = -5
+ISING_ERR_TIMEOUT = -6
+ISING_ERR_UNSUPPORTED = -7
+ISING_ERR_NOT_FOUND = -8
+ISING_ERR_PENDING = -9
+
+
+class JzParams(ctypes.Structure):
+    """Mirror of ``jz_params`` in include/isingjz.h."""
+    _fields_ = [
+        ("d", ctypes.c_int), ("L", ctypes.c_int), ("L_t", ctypes.c_int),
+        ("beta", ctypes.c_double), ("l", ctypes.c_int),
+        ("n_step", ctypes.c_int), ("n_sweep", ctypes.c_int), ("n_therm", ctypes.c_int),
+        ("n_traj", ctypes.c_int), ("direction", ctypes.c_int),
+        ("traj0", ctypes.c_longlong), ("seed", ctypes.c_uint64),
+    ]
+
+
+class IsingError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {ising_strerror(code)} ({code})")
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load libisingjz.so (build it with ``paper_2304_03311_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is missing: run paper_2304_03311_gb300.build.build() "
+                          "(nvcc, sm_103a) before using the library")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    sig = {
+        "jz_params_default": (ctypes.c_int, [P(JzParams)]),
+        "ising_replica_init": (ctypes.c_int, [P(vp), ctypes.c_int, ctypes.c_size_t, vp]),
+        "ising_replica_free": (None, [vp]),
+        "ising_sync": (ctypes.c_int, [vp]),
+        "jarzynski_run": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_uint64, vp]),
+        "jarzynski_run_ex": (ctypes.c_int, [vp, P(JzParams), vp, vp]),
+        "jarzynski_run_batch": (ctypes.c_int, [vp, P(JzParams), ctypes.c_int, P(vp)]),
+        "estimator_reduce": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_int, P(ctypes.c_double),
+                                            P(ctypes.c_double), P(ctypes.c_double)]),
+        "ising_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(buf):
+    """Raw address of a torch tensor or numpy array (None passes NULL)."""
+    if buf is None:
+        return None
+    if hasattr(buf, "data_ptr"):
+        if not buf.is_contiguous():
+            raise ValueError("buffer must be contiguous")
+        return buf.data_ptr()
+    if hasattr(buf, "ctypes"):
+        if not buf.flags["C_CONTIGUOUS"] or not buf.flags["WRITEABLE"]:
+            raise ValueError("buffer must be contiguous and writeable")
+        return buf.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(buf)!r}")
+
+
+def _check(code: int, where: str):
+    if code != ISING_OK:
+        raise IsingError(code, where)
+
+
+def ising_strerror(code: int) -> str:
+    return load().ising_strerror(int(code)).decode()
+
+
+def jz_params_default() -> JzParams:
+    p = JzParams()
+    _check(load().jz_params_default(ctypes.byref(p)), "jz_params_default")
+    return p
+
+
+def ising_replica_init(device: int = 0, hbm_budget_bytes: int = 0, cuda_stream: int | None = None):
+    """Returns an opaque context handle (int).  cuda_stream: a cudaStream_t as
+    an integer (e.g. ``torch.cuda.current_stream().cuda_stream``) or None."""
+    ctx = ctypes.c_void_p()
+    _check(load().ising_replica_init(ctypes.byref(ctx), int(device), int(hbm_budget_bytes),
+                                     cuda_stream), "ising_replica_init")
+    return ctx.value
+
+
+def ising_replica_free(ctx) -> None:
+    load().ising_replica_free(ctx)
+
+
+def ising_sync(ctx) -> None:
+    _check(load().ising_sync(ctx), "ising_sync")
+
+
+def jarzynski_run(ctx, d, L, L_t, beta, l, n_step, n_sweep, n_traj, seed, work_int_out):
+    _check(load().jarzynski_run(ctx, int(d), int(L), int(L_t), float(beta), int(l), int(n_step),
+                                int(n_sweep), int(n_traj), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                _ptr(work_int_out)), "jarzynski_run")
+
+
+def make_params(d, L, L_t, beta, l, n_step, n_sweep, n_traj, seed=0, *, n_therm=1000,
+                direction=1, traj0=0) -> JzParams:
+    p = jz_params_default()
+    p.d, p.L, p.L_t, p.beta, p.l = int(d), int(L), int(L_t), float(beta), int(l)
+    p.n_step, p.n_sweep, p.n_traj = int(n_step), int(n_sweep), int(n_traj)
+    p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    p.n_therm, p.direction, p.traj0 = int(n_therm), int(direction), int(traj0)
+    return p
+
+
+def jarzynski_run_ex(ctx, params: JzParams, work_int_out, spins_out=None):
+    _check(load().jarzynski_run_ex(ctx, ctypes.byref(params), _ptr(work_int_out),
+                                   _ptr(spins_out)), "jarzynski_run_ex")
+
+
+def jarzynski_run_batch(ctx, params_list, work_outs):
+    n = len(params_list)
+    arr = (JzParams * n)(*params_list)
+    outs = (ctypes.c_void_p * n)(*[_ptr(w) for w in work_outs])
+    _check(load().jarzynski_run_batch(ctx, arr, n, outs), "jarzynski_run_batch")
+
+
+def estimator_reduce(ctx, work_int, n_traj, beta, n_step, direction=1, n_jack_bins=32):
+    """Returns (ln <e^-W>, Delta S_2, jackknife error of Delta S_2)."""
+    lr, ds, err = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().estimator_reduce(ctx, _ptr(work_int), int(n_traj), float(beta), int(n_step),
+                                   int(direction), int(n_jack_bins), ctypes.byref(lr),
+                                   ctypes.byref(ds), ctypes.byref(err)), "estimator_reduce")
+    return lr.value, ds.value, err.value

@@ -1,0 +1,474 @@
+// jz_api.cu -- the C ABI (include/isingjz.h): argument checks, host FP64
+// threshold tables, device buffers, launch grouping, estimator.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "../../include/isingjz.h"
+#include "jz_device.cuh"
+
+namespace jz {
+size_t traj_smem_bytes(const Geom& g);
+cudaError_t launch_traj(int D, const Geom& g, const PhiloxKeys& K, const JobDesc* jobs,
+                        int n_jobs, long long n_cta, int threads, cudaStream_t st);
+cudaError_t launch_estimator(const long long* w_int, int n, double scale, int direction,
+                             int n_blocks, double* out, cudaStream_t st);
+constexpr int kMaxJackBlocksHost = 64;
+constexpr size_t kMaxSmemPerCta = 227 * 1024;
+}  // namespace jz
+
+// Grow-only device buffer charged against the context's HBM budget.
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct ising_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t budget = 0;   // 0 = unlimited
+    size_t used = 0;
+    DevBuf tcut, jobs, work, spins, est_in, est_out;
+    std::vector<uint32_t> h_tcut;
+    std::vector<jz::JobDesc> h_jobs;
+};
+
+namespace {
+
+int ensure(ising_ctx* ctx, DevBuf& b, size_t bytes)
+{
+    if (bytes <= b.bytes) return ISING_OK;
+    size_t want = bytes + bytes / 4;
+    size_t delta = want - b.bytes;
+    if (ctx->budget && ctx->used + delta > ctx->budget) {
+        want = bytes;
+        delta = want - b.bytes;
+        if (ctx->used + delta > ctx->budget) return ISING_ERR_NOMEM;
+    }
+    if (b.ptr) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(b.ptr);
+        ctx->used -= b.bytes;
+        b.ptr = nullptr;
+        b.bytes = 0;
+    }
+    if (cudaMalloc(&b.ptr, want) != cudaSuccess) {
+        cudaGetLastError();
+        return ISING_ERR_NOMEM;
+    }
+    b.bytes = want;
+    ctx->used += want;
+    return ISING_OK;
+}
+
+// 1 if p is device-accessible memory of the current device (device or
+// managed allocation), 0 for host memory (pageable or pinned).
+int is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int check_params(const jz_params* p)
+{
+    if (!p) return ISING_ERR_ARG;
+    if (p->d != 2 && p->d != 3) return ISING_ERR_UNSUPPORTED;
+    if (p->L < 2 || p->L_t < 2 || p->L > 4096 || p->L_t > 4096) return ISING_ERR_ARG;
+    if ((p->L & 1) || (p->L_t & 1)) return ISING_ERR_ODD_EXTENT;
+    if (p->l < 0 || p->l > p->L - 1) return ISING_ERR_L_RANGE;
+    if (p->n_step < 1 || p->n_sweep < 1 || p->n_therm < 0 || p->n_traj < 1)
+        return ISING_ERR_ARG;
+    if (p->direction != 1 && p->direction != -1) return ISING_ERR_ARG;
+    if (!(p->beta >= 0.0 && p->beta <= 4.0)) return ISING_ERR_ARG;
+    if (p->traj0 < 0 || p->traj0 + p->n_traj > 0x100000000LL) return ISING_ERR_ARG;
+    // the global sweep index is a 32-bit counter word
+    long long sweeps = (long long)p->n_therm + (long long)p->n_step * p->n_sweep;
+    if (sweeps >= 0x100000000LL) return ISING_ERR_ARG;
+    // m = a N + b w_self + c w_glue must fit an int: |m| <= (2d+1) N
+    if ((long long)p->n_step * (2 * p->d + 1) >= 0x7FFFFFFFLL) return ISING_ERR_ARG;
+    return ISING_OK;
+}
+
+jz::Geom make_geom(int d, int L, int Lt)
+{
+    jz::Geom g;
+    g.L = L;
+    g.Lt = Lt;
+    g.Ly = d == 3 ? L : 1;
+    g.Lh = L / 2;
+    g.G = (g.Lh + 3) / 4;
+    g.NR = 2 * Lt * g.Ly;
+    auto magic = [](uint32_t v) -> uint32_t {
+        return v <= 1 ? 0u : (uint32_t)((0x100000000ULL + v - 1) / v);
+    };
+    g.magic_G = magic((uint32_t)g.G);
+    g.magic_Ly = magic((uint32_t)g.Ly);
+    g.magic_Lt = magic((uint32_t)g.Lt);
+    return g;
+}
+
+// Threshold T = min(floor(2^32 exp(-x)), 2^32 - 1): a site whose energy cost
+// m > 0 flips with probability T / 2^32.
+uint32_t threshold(double x)
+{
+    double v = std::floor(std::ldexp(std::exp(-x), 32));
+    return v >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)v;
+}
+
+jz::PhiloxKeys key_schedule(uint64_t seed)
+{
+    jz::PhiloxKeys K;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int i = 0; i < 10; ++i) {
+        K.k0[i] = k0;
+        K.k1[i] = k1;
+        k0 += jz::kPhiloxW0;
+        k1 += jz::kPhiloxW1;
+    }
+    return K;
+}
+
+// Host tables of one job: bulk thresholds by anti-aligned count a (m = 2D - 2a,
+// x = 2 beta m) and, per step k, the switched-site thresholds indexed by the
+// fixed-link sum a' (odd, |a'| <= 2D-1) and the self / glue bond products b, c
+// (m = a' N + b w_self + c w_glue, x = (2 beta m) / N).
+void build_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcut, size_t off)
+{
+    const int D = p.d;
+    for (int a = 0; a < 4; ++a) {
+        int m = 2 * D - 2 * a;
+        tb[a] = (a < D) ? threshold(2.0 * p.beta * (double)m) : 0xFFFFFFFFu;
+    }
+    const int per = 8 * D;
+    const long long N = p.n_step;
+    for (long long k = 0; k < N; ++k) {
+        const long long kp = k + 1;
+        const long long ws = p.direction > 0 ? N - kp : kp;
+        const long long wg = p.direction > 0 ? kp : N - kp;
+        for (int ia = 0; ia < 2 * D; ++ia) {
+            const long long a = 2 * ia - (2 * D - 1);
+            for (int ib = 0; ib < 2; ++ib)
+                for (int ic = 0; ic < 2; ++ic) {
+                    const long long m = a * N + (ib ? ws : -ws) + (ic ? wg : -wg);
+                    uint32_t T = 0xFFFFFFFFu;
+                    if (m > 0) T = threshold((2.0 * p.beta * (double)m) / (double)N);
+                    tcut[off + (size_t)k * per + (ia * 2 + ib) * 2 + ic] = T;
+                }
+        }
+    }
+}
+
+int threads_for(const jz::Geom& g)
+{
+    int items = g.NR * g.G;
+    int t = ((items + 31) / 32) * 32;
+    return t > 256 ? 256 : t;
+}
+
+int cuda_err(cudaError_t e)
+{
+    if (e == cudaSuccess) return ISING_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? ISING_ERR_NOMEM : ISING_ERR_CUDA;
+}
+
+// Runs jobs[idx[0..]] (equal d, L, L_t, seed) in one launch.
+int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx,
+              int64_t* const* outs, int8_t* const* spins, bool outs_on_device,
+              bool spins_on_device)
+{
+    const jz_params& p0 = jobs[idx[0]];
+    const jz::Geom g = make_geom(p0.d, p0.L, p0.L_t);
+    if (jz::traj_smem_bytes(g) > jz::kMaxSmemPerCta) return ISING_ERR_UNSUPPORTED;
+    const int n_jobs = (int)idx.size();
+    const int per = 8 * p0.d;
+    const int V = 2 * p0.L_t * g.Ly * p0.L;
+
+    size_t n_tcut = 0;
+    long long n_cta = 0, n_spin_traj = 0;
+    for (int j : idx) {
+        n_tcut += (size_t)jobs[j].n_step * per;
+        n_cta += jobs[j].n_traj;
+        if (spins && spins[j]) n_spin_traj += jobs[j].n_traj;
+    }
+    if (n_cta > 0x7FFFFFFFLL) return ISING_ERR_ARG;
+    int rc;
+    if ((rc = ensure(ctx, ctx->tcut, n_tcut * sizeof(uint32_t)))) return rc;
+    if ((rc = ensure(ctx, ctx->jobs, (size_t)n_jobs * sizeof(jz::JobDesc)))) return rc;
+    if (!outs_on_device && (rc = ensure(ctx, ctx->work, (size_t)n_cta * sizeof(long long))))
+        return rc;
+    if (n_spin_traj && !spins_on_device &&
+        (rc = ensure(ctx, ctx->spins, (size_t)n_spin_traj * V)))
+        return rc;
+
+    ctx->h_tcut.assign(n_tcut, 0);
+    ctx->h_jobs.assign(n_jobs, jz::JobDesc{});
+    size_t off = 0;
+    long long cta = 0, spin_off = 0;
+    uint32_t* d_tcut = (uint32_t*)ctx->tcut.ptr;
+    for (int i = 0; i < n_jobs; ++i) {
+        const jz_params& p = jobs[idx[i]];
+        jz::JobDesc& J = ctx->h_jobs[i];
+        J.l = p.l;
+        J.n_step = p.n_step;
+        J.n_sweep = p.n_sweep;
+        J.n_therm = p.n_therm;
+        J.dir = p.direction;
+        J.n_traj = p.n_traj;
+        J.traj0 = p.traj0;
+        J.cta0 = cta;
+        build_tables(p, J.tb, ctx->h_tcut, off);
+        J.tcut = d_tcut + off;
+        J.w_out = outs_on_device ? (long long*)outs[idx[i]] : (long long*)ctx->work.ptr + cta;
+        J.spins_out = nullptr;
+        if (spins && spins[idx[i]]) {
+            J.spins_out = spins_on_device ? spins[idx[i]]
+                                          : (int8_t*)ctx->spins.ptr + spin_off * (long long)V;
+            spin_off += p.n_traj;
+        }
+        off += (size_t)p.n_step * per;
+        cta += p.n_traj;
+    }
+    cudaStream_t st = ctx->stream;
+    if ((rc = cuda_err(cudaMemcpyAsync(ctx->tcut.ptr, ctx->h_tcut.data(),
+                                       n_tcut * sizeof(uint32_t), cudaMemcpyHostToDevice, st))))
+        return rc;
+    if ((rc = cuda_err(cudaMemcpyAsync(ctx->jobs.ptr, ctx->h_jobs.data(),
+                                       n_jobs * sizeof(jz::JobDesc), cudaMemcpyHostToDevice, st))))
+        return rc;
+    const jz::PhiloxKeys K = key_schedule(p0.seed);
+    if ((rc = cuda_err(jz::launch_traj(p0.d, g, K, (const jz::JobDesc*)ctx->jobs.ptr, n_jobs,
+                                       n_cta, threads_for(g), st))))
+        return rc;
+    if (!outs_on_device || (n_spin_traj && !spins_on_device)) {
+        long long c = 0, so = 0;
+        for (int i = 0; i < n_jobs; ++i) {
+            const jz_params& p = jobs[idx[i]];
+            if (!outs_on_device &&
+                (rc = cuda_err(cudaMemcpyAsync(outs[idx[i]], (long long*)ctx->work.ptr + c,
+                                               p.n_traj * sizeof(long long),
+                                               cudaMemcpyDeviceToHost, st))))
+                return rc;
+            if (spins && spins[idx[i]] && !spins_on_device) {
+                if ((rc = cuda_err(cudaMemcpyAsync(spins[idx[i]],
+                                                   (int8_t*)ctx->spins.ptr + so * (long long)V,
+                                                   (size_t)p.n_traj * V, cudaMemcpyDeviceToHost,
+                                                   st))))
+                    return rc;
+                so += p.n_traj;
+            }
+            c += p.n_traj;
+        }
+        if ((rc = cuda_err(cudaStreamSynchronize(st)))) return rc;
+    }
+    return ISING_OK;
+}
+
+int run_jobs(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const* outs,
+             int8_t* const* spins)
+{
+    if (!ctx || !jobs || !outs || n_jobs < 1) return ISING_ERR_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
+    for (int j = 0; j < n_jobs; ++j) {
+        int rc = check_params(&jobs[j]);
+        if (rc) return rc;
+        if (!outs[j]) return ISING_ERR_ARG;
+    }
+    const bool outs_dev = is_device_ptr(outs[0]);
+    for (int j = 1; j < n_jobs; ++j)
+        if (is_device_ptr(outs[j]) != (int)outs_dev) return ISING_ERR_ARG;
+    bool spins_dev = false;
+    bool first = true;
+    if (spins)
+        for (int j = 0; j < n_jobs; ++j) {
+            if (!spins[j]) continue;
+            bool dv = is_device_ptr(spins[j]);
+            if (first) { spins_dev = dv; first = false; }
+            else if (dv != spins_dev) return ISING_ERR_ARG;
+        }
+    // one launch per (d, L, L_t, seed), jobs kept in call order within a group
+    std::map<std::tuple<int, int, int, uint64_t>, std::vector<int>> groups;
+    std::vector<std::tuple<int, int, int, uint64_t>> order;
+    for (int j = 0; j < n_jobs; ++j) {
+        auto key = std::make_tuple(jobs[j].d, jobs[j].L, jobs[j].L_t, jobs[j].seed);
+        auto it = groups.find(key);
+        if (it == groups.end()) {
+            order.push_back(key);
+            groups[key] = {j};
+        } else {
+            it->second.push_back(j);
+        }
+    }
+    for (auto& key : order) {
+        auto& idx = groups[key];
+        // keep the per-launch job table within bounds
+        for (size_t s = 0; s < idx.size(); s += jz::kMaxJobsPerLaunch) {
+            std::vector<int> part(idx.begin() + s,
+                                  idx.begin() + std::min(idx.size(), s + jz::kMaxJobsPerLaunch));
+            int rc = run_group(ctx, jobs, part, outs, spins, outs_dev, spins_dev);
+            if (rc) return rc;
+        }
+    }
+    return ISING_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int jz_params_default(jz_params* p)
+{
+    if (!p) return ISING_ERR_ARG;
+    std::memset(p, 0, sizeof *p);
+    p->n_therm = 1000;
+    p->n_sweep = 1;
+    p->direction = 1;
+    return ISING_OK;
+}
+
+int ising_replica_init(ising_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream)
+{
+    if (!out) return ISING_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess) {
+        cudaGetLastError();
+        return ISING_ERR_CUDA;
+    }
+    if (device < 0 || device >= n) return ISING_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return ISING_ERR_CUDA;
+    ising_ctx* ctx = new (std::nothrow) ising_ctx();
+    if (!ctx) return ISING_ERR_NOMEM;
+    ctx->device = device;
+    ctx->budget = hbm_budget_bytes;
+    if (cuda_stream) {
+        ctx->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return ISING_ERR_CUDA;
+        }
+        ctx->own_stream = true;
+    }
+    *out = ctx;
+    return ISING_OK;
+}
+
+void ising_replica_free(ising_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (DevBuf* b : {&ctx->tcut, &ctx->jobs, &ctx->work, &ctx->spins, &ctx->est_in,
+                      &ctx->est_out})
+        if (b->ptr) cudaFree(b->ptr);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+int ising_sync(ising_ctx* ctx)
+{
+    if (!ctx) return ISING_ERR_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
+    return cuda_err(cudaStreamSynchronize(ctx->stream));
+}
+
+int jarzynski_run_ex(ising_ctx* ctx, const jz_params* p, int64_t* work_int_out,
+                     int8_t* spins_out)
+{
+    if (!p || !work_int_out) return ISING_ERR_ARG;
+    int64_t* outs[1] = {work_int_out};
+    int8_t* sp[1] = {spins_out};
+    return run_jobs(ctx, p, 1, outs, spins_out ? sp : nullptr);
+}
+
+int jarzynski_run(ising_ctx* ctx, int d, int L, int L_t, double beta, int l, int n_step,
+                  int n_sweep, int n_traj, uint64_t seed, int64_t* work_int_out)
+{
+    jz_params p;
+    jz_params_default(&p);
+    p.d = d;
+    p.L = L;
+    p.L_t = L_t;
+    p.beta = beta;
+    p.l = l;
+    p.n_step = n_step;
+    p.n_sweep = n_sweep;
+    p.n_traj = n_traj;
+    p.seed = seed;
+    return jarzynski_run_ex(ctx, &p, work_int_out, nullptr);
+}
+
+int jarzynski_run_batch(ising_ctx* ctx, const jz_params* jobs, int n_jobs,
+                        int64_t* const* work_outs)
+{
+    return run_jobs(ctx, jobs, n_jobs, work_outs, nullptr);
+}
+
+int estimator_reduce(ising_ctx* ctx, const int64_t* work_int, int n_traj, double beta,
+                     int n_step, int direction, int n_jack_bins, double* log_ratio,
+                     double* delta_S2, double* delta_S2_err)
+{
+    if (!ctx || !work_int || n_traj < 1 || n_step < 1 || !log_ratio || !delta_S2 ||
+        !delta_S2_err)
+        return ISING_ERR_ARG;
+    if (direction != 1 && direction != -1) return ISING_ERR_ARG;
+    if (n_jack_bins < 1 || n_jack_bins > jz::kMaxJackBlocksHost) return ISING_ERR_ARG;
+    if (!(beta >= 0.0 && std::isfinite(beta))) return ISING_ERR_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
+    int rc;
+    const long long* src = (const long long*)work_int;
+    cudaStream_t st = ctx->stream;
+    if (!is_device_ptr(work_int)) {
+        if ((rc = ensure(ctx, ctx->est_in, (size_t)n_traj * sizeof(long long)))) return rc;
+        if ((rc = cuda_err(cudaMemcpyAsync(ctx->est_in.ptr, work_int,
+                                           (size_t)n_traj * sizeof(long long),
+                                           cudaMemcpyHostToDevice, st))))
+            return rc;
+        src = (const long long*)ctx->est_in.ptr;
+    }
+    if ((rc = ensure(ctx, ctx->est_out, 4 * sizeof(double)))) return rc;
+    const int B = n_jack_bins < n_traj ? n_jack_bins : n_traj;
+    if ((rc = cuda_err(jz::launch_estimator(src, n_traj, beta / (double)n_step, direction, B,
+                                            (double*)ctx->est_out.ptr, st))))
+        return rc;
+    double h[3];
+    if ((rc = cuda_err(cudaMemcpyAsync(h, ctx->est_out.ptr, 3 * sizeof(double),
+                                       cudaMemcpyDeviceToHost, st))))
+        return rc;
+    if ((rc = cuda_err(cudaStreamSynchronize(st)))) return rc;
+    *log_ratio = h[0];
+    *delta_S2 = h[1];
+    *delta_S2_err = h[2];
+    return ISING_OK;
+}
+
+const char* ising_strerror(int code)
+{
+    switch (code) {
+    case ISING_OK: return "ok";
+    case ISING_ERR_ARG: return "invalid argument";
+    case ISING_ERR_ODD_EXTENT: return "L and L_t must be even";
+    case ISING_ERR_L_RANGE: return "l must satisfy 0 <= l <= L-1";
+    case ISING_ERR_NOMEM: return "device memory or HBM budget exhausted";
+    case ISING_ERR_CUDA: return "CUDA runtime error";
+    case ISING_ERR_TIMEOUT: return "bounded device wait gave up";
+    case ISING_ERR_UNSUPPORTED: return "unsupported dimension or lattice too large";
+    case ISING_ERR_NOT_FOUND: return "unknown job id";
+    case ISING_ERR_PENDING: return "job not finished";
+    default: return "unknown error";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// jz_device.cuh -- device-side building blocks of the replica-gluing kernels.
+//
+// Spin storage in shared memory (one trajectory per CTA):
+//   S[c][R][q]  uint32 words, c = colour, R = (r L_t + t) L_y + y the row,
+//               q < G = ceil((L/2)/4) the word within the row.  Byte j of word
+//               q holds the colour-c site h = 4q + j of row R, x = 2h + p with
+//               p = (c + t + y) mod 2; the byte is 0 for spin +1 and 1 for -1.
+// With this layout the four (2D) or six (3D) neighbours of the four sites of
+// one word are, in the other colour: the same word of rows t-1, t+1 (and
+// y-1, y+1), the same word of the same row (one x neighbour), and that word
+// shifted by one byte (the other x neighbour).  One Philox4x32-10 block gives
+// the four acceptance words of one spin word.
+#pragma once
+#include <cstdint>
+
+namespace jz {
+
+constexpr int kMaxJobsPerLaunch = 4096;
+
+// Philox4x32-10 round constants and Weyl key increments (Salmon, Moraes, Dror
+// and Shaw, SC'11).
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+// Key schedule of one launch: k0[i], k1[i] for rounds i = 0..9.  Passed by
+// value as a kernel parameter, so every round key is a constant-bank operand.
+struct PhiloxKeys {
+    uint32_t k0[10];
+    uint32_t k1[10];
+};
+
+// Lattice shape of one launch (all jobs of a launch share it).
+struct Geom {
+    int L, Lt, Ly;      // spatial extent, time extent, L in 3D / 1 in 2D
+    int Lh;             // L / 2 sites of one colour per row
+    int G;              // words per row, ceil(Lh / 4)
+    int NR;             // rows per colour, 2 * Lt * Ly
+    uint32_t magic_G;   // ceil(2^32 / G)   (G > 1), exact division of idx < 2^16
+    uint32_t magic_Ly;  // ceil(2^32 / Ly)  (Ly > 1)
+    uint32_t magic_Lt;  // ceil(2^32 / Lt)
+};
+
+// Per-job (one transformation) parameters, device copy.
+struct JobDesc {
+    int l;              // switched column
+    int n_step, n_sweep, n_therm;
+    int dir;            // +1 forward, -1 reverse
+    int n_traj;
+    long long traj0;    // global index of the job's first trajectory
+    long long cta0;     // first CTA of the job in the launch grid
+    uint32_t tb[4];     // bulk thresholds by anti-aligned neighbour count a:
+                        // tb[a] = T(m = 2D - 2a), a < D
+    const uint32_t* tcut;   // [n_step][8D] switched-site thresholds
+    long long* w_out;       // [n_traj] W_int
+    int8_t* spins_out;      // [n_traj][V] final spins (+-1) or nullptr
+};
+
+// q = n / d for n * d < 2^32, with magic = ceil(2^32 / d) (d > 1).
+__device__ __forceinline__ uint32_t div_magic(uint32_t n, uint32_t d, uint32_t magic)
+{
+    return d == 1 ? n : __umulhi(n, magic);
+}
+
+// One Philox4x32-10 block.
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        const PhiloxKeys& K)
+{
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint64_t p0 = (uint64_t)kPhiloxM0 * c0;
+        const uint64_t p1 = (uint64_t)kPhiloxM1 * c2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ K.k0[i];
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ K.k1[i];
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
+        c0 = n0;
+        c2 = n2;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4& u, int j)
+{
+    return j == 0 ? u.x : j == 1 ? u.y : j == 2 ? u.z : u.w;
+}
+
+}  // namespace jz
