@@ -136,6 +136,14 @@ int jarzynski_run_ex(ising_ctx* ctx, const jz_params* p, int64_t* work_int_out,
 int jarzynski_run_batch(ising_ctx* ctx, const jz_params* jobs, int n_jobs,
                         int64_t* const* work_outs);
 
+/* The plain GPU form of the same computation, kept as the comparison baseline:
+ * one trajectory per launch sequence, one launch per half-sweep, spins in
+ * global memory (section 3 protocol, Appendix A work; same random stream and
+ * acceptance conventions, so outputs are bit-identical to jarzynski_run_ex).
+ * Arguments, buffers and errors as for jarzynski_run_ex.  Slow by design. */
+int jarzynski_run_plain(ising_ctx* ctx, const jz_params* p, int64_t* work_int_out,
+                        int8_t* spins_out);
+
 /* FP64 estimator on the device (Appendix A, eq. Jarzynski_theorem; section 2):
  *   *log_ratio    = ln <e^-W>, W_i = beta work_int[i] / n_step, evaluated as a
  *                   max-shifted log-sum-exp
@@ -149,6 +157,17 @@ int jarzynski_run_batch(ising_ctx* ctx, const jz_params* jobs, int n_jobs,
 int estimator_reduce(ising_ctx* ctx, const int64_t* work_int, int n_traj, double beta,
                      int n_step, int direction, int n_jack_bins, double* log_ratio,
                      double* delta_S2, double* delta_S2_err);
+
+/* Measurement utility; the paper has no counterpart.  Runs an integer-issue
+ * probe on `device` over all SMs at full occupancy and writes its rate:
+ *   kind 0: three-input logic (LOP3) chains      -> thread-instructions/s
+ *   kind 1: 32-bit multiply-add (IMAD) chains     -> thread-instructions/s
+ *   kind 2: 1:1:1 IMAD / LOP3 / IADD3 mix         -> thread-instructions/s
+ *   kind 3: Philox4x32-10 blocks                  -> blocks/s
+ * These are the measured ceilings of the trajectory kernel's roofline.  Uses
+ * the legacy default stream and synchronises the device.
+ * Errors: ISING_ERR_ARG (kind or rate), ISING_ERR_CUDA. */
+int ising_probe(int device, int kind, double* rate);
 
 /* Human-readable text for an error code (static storage). */
 const char* ising_strerror(int code);

@@ -20,8 +20,8 @@ from .build import LIB as _LIB_PATH
 
 __all__ = [
     "IsingError", "JzParams", "lib_path", "load", "ising_replica_init", "ising_replica_free",
-    "ising_sync", "jarzynski_run", "jarzynski_run_ex", "jarzynski_run_batch",
-    "estimator_reduce", "ising_strerror", "jz_params_default",
+    "ising_sync", "jarzynski_run", "jarzynski_run_ex", "jarzynski_run_batch", "jarzynski_run_plain",
+    "estimator_reduce", "ising_strerror", "jz_params_default", "ising_probe",
 ]
 
 ISING_OK = 0
@@ -81,10 +81,12 @@ def load():
                                          ctypes.c_int, ctypes.c_int, ctypes.c_uint64, vp]),
         "jarzynski_run_ex": (ctypes.c_int, [vp, P(JzParams), vp, vp]),
         "jarzynski_run_batch": (ctypes.c_int, [vp, P(JzParams), ctypes.c_int, P(vp)]),
+        "jarzynski_run_plain": (ctypes.c_int, [vp, P(JzParams), vp, vp]),
         "estimator_reduce": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_int, P(ctypes.c_double),
                                             P(ctypes.c_double), P(ctypes.c_double)]),
         "ising_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "ising_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -162,6 +164,11 @@ def jarzynski_run_ex(ctx, params: JzParams, work_int_out, spins_out=None):
                                    _ptr(spins_out)), "jarzynski_run_ex")
 
 
+def jarzynski_run_plain(ctx, params: JzParams, work_int_out, spins_out=None):
+    _check(load().jarzynski_run_plain(ctx, ctypes.byref(params), _ptr(work_int_out),
+                                      _ptr(spins_out)), "jarzynski_run_plain")
+
+
 def jarzynski_run_batch(ctx, params_list, work_outs):
     n = len(params_list)
     arr = (JzParams * n)(*params_list)
@@ -176,3 +183,11 @@ def estimator_reduce(ctx, work_int, n_traj, beta, n_step, direction=1, n_jack_bi
                                    int(direction), int(n_jack_bins), ctypes.byref(lr),
                                    ctypes.byref(ds), ctypes.byref(err)), "estimator_reduce")
     return lr.value, ds.value, err.value
+
+
+def ising_probe(device: int, kind: int) -> float:
+    """Integer-issue probe rate (see include/isingjz.h): kinds 0-2 in
+    thread-instructions/s, kind 3 in Philox4x32-10 blocks/s."""
+    r = ctypes.c_double()
+    _check(load().ising_probe(int(device), int(kind), ctypes.byref(r)), "ising_probe")
+    return r.value

@@ -19,6 +19,11 @@ cudaError_t launch_traj(int D, const Geom& g, const PhiloxKeys& K, const JobDesc
                         int n_jobs, long long n_cta, int threads, cudaStream_t st);
 cudaError_t launch_estimator(const long long* w_int, int n, double scale, int direction,
                              int n_blocks, double* out, cudaStream_t st);
+double run_probe(int kind, int device);
+cudaError_t plain_trajectory(int D, const Geom& g, const PhiloxKeys& K, int l, int dir,
+                             int n_step, int n_sweep, int n_therm, uint32_t traj,
+                             const uint32_t tb[4], const uint32_t* tcut, int8_t* s,
+                             long long* w, cudaStream_t st);
 constexpr int kMaxJackBlocksHost = 64;
 constexpr size_t kMaxSmemPerCta = 227 * 1024;
 }  // namespace jz
@@ -39,6 +44,8 @@ struct ising_ctx {
     std::vector<uint32_t> h_tcut;
     std::vector<jz::JobDesc> h_jobs;
 };
+
+static_assert(sizeof(jz_params) == 64, "jz_params layout is part of the ABI");
 
 namespace {
 
@@ -416,6 +423,52 @@ int jarzynski_run_batch(ising_ctx* ctx, const jz_params* jobs, int n_jobs,
     return run_jobs(ctx, jobs, n_jobs, work_outs, nullptr);
 }
 
+int jarzynski_run_plain(ising_ctx* ctx, const jz_params* p, int64_t* work_int_out,
+                        int8_t* spins_out)
+{
+    if (!ctx || !p || !work_int_out) return ISING_ERR_ARG;
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
+    const jz::Geom g = make_geom(p->d, p->L, p->L_t);
+    const int V = 2 * p->L_t * g.Ly * p->L;
+    const bool w_dev = is_device_ptr(work_int_out);
+    const bool s_dev = spins_out && is_device_ptr(spins_out);
+    const size_t n_tcut = (size_t)p->n_step * 8 * p->d;
+    if ((rc = ensure(ctx, ctx->tcut, n_tcut * sizeof(uint32_t)))) return rc;
+    if (!w_dev && (rc = ensure(ctx, ctx->work, (size_t)p->n_traj * sizeof(long long)))) return rc;
+    if (!s_dev && (rc = ensure(ctx, ctx->spins, (size_t)(spins_out ? p->n_traj : 1) * V)))
+        return rc;
+    ctx->h_tcut.assign(n_tcut, 0);
+    uint32_t tb[4];
+    build_tables(*p, tb, ctx->h_tcut, 0);
+    cudaStream_t st = ctx->stream;
+    if ((rc = cuda_err(cudaMemcpyAsync(ctx->tcut.ptr, ctx->h_tcut.data(), n_tcut * sizeof(uint32_t),
+                                       cudaMemcpyHostToDevice, st))))
+        return rc;
+    const jz::PhiloxKeys K = key_schedule(p->seed);
+    long long* w = w_dev ? (long long*)work_int_out : (long long*)ctx->work.ptr;
+    for (int i = 0; i < p->n_traj; ++i) {
+        int8_t* s = s_dev ? spins_out + (size_t)i * V
+                          : (int8_t*)ctx->spins.ptr + (spins_out ? (size_t)i * V : 0);
+        if ((rc = cuda_err(jz::plain_trajectory(p->d, g, K, p->l, p->direction, p->n_step,
+                                                p->n_sweep, p->n_therm,
+                                                (uint32_t)(p->traj0 + i), tb,
+                                                (const uint32_t*)ctx->tcut.ptr, s, w + i, st))))
+            return rc;
+    }
+    if (!w_dev &&
+        (rc = cuda_err(cudaMemcpyAsync(work_int_out, w, (size_t)p->n_traj * sizeof(long long),
+                                       cudaMemcpyDeviceToHost, st))))
+        return rc;
+    if (spins_out && !s_dev &&
+        (rc = cuda_err(cudaMemcpyAsync(spins_out, ctx->spins.ptr, (size_t)p->n_traj * V,
+                                       cudaMemcpyDeviceToHost, st))))
+        return rc;
+    if (!w_dev || (spins_out && !s_dev)) return cuda_err(cudaStreamSynchronize(st));
+    return ISING_OK;
+}
+
 int estimator_reduce(ising_ctx* ctx, const int64_t* work_int, int n_traj, double beta,
                      int n_step, int direction, int n_jack_bins, double* log_ratio,
                      double* delta_S2, double* delta_S2_err)
@@ -451,6 +504,25 @@ int estimator_reduce(ising_ctx* ctx, const int64_t* work_int, int n_traj, double
     *log_ratio = h[0];
     *delta_S2 = h[1];
     *delta_S2_err = h[2];
+    return ISING_OK;
+}
+
+int ising_probe(int device, int kind, double* rate)
+{
+    if (!rate || kind < 0 || kind > 3) return ISING_ERR_ARG;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess) {
+        cudaGetLastError();
+        return ISING_ERR_CUDA;
+    }
+    if (device < 0 || device >= n) return ISING_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return ISING_ERR_CUDA;
+    const double r = jz::run_probe(kind, device);
+    if (r < 0) {
+        cudaGetLastError();
+        return ISING_ERR_CUDA;
+    }
+    *rate = r;
     return ISING_OK;
 }
 

@@ -96,6 +96,23 @@ def test_largest_3d_lattice_fits_and_matches(ctx):
     np.testing.assert_array_equal(Sg, So)
 
 
+@pytest.mark.parametrize("job", [SMALL[0], SMALL[2], SMALL[6], SMALL[9], SMALL[4]],
+                         ids=["2d", "2d_rev", "2d_ragged", "3d_ragged_rev", "Lt2"])
+def test_plain_baseline_is_bit_exact(ctx, job):
+    """The plain one-lattice-per-launch form gives the same bits as the fused
+    kernel and the oracle."""
+    w = torch.empty(job.n_traj, dtype=torch.int64, device="cuda")
+    s = torch.empty(job.n_traj * job.sites, dtype=torch.int8, device="cuda")
+    p = jz.make_params(job.d, job.L, job.L_t, job.beta, job.l, job.n_step, job.n_sweep,
+                       job.n_traj, job.seed, n_therm=job.n_therm, direction=job.direction,
+                       traj0=job.traj0)
+    jz.jarzynski_run_plain(ctx, p, w, s)
+    jz.ising_sync(ctx)
+    Wo, So = oracle_run(job)
+    np.testing.assert_array_equal(w.cpu().numpy(), Wo)
+    np.testing.assert_array_equal(s.cpu().numpy().reshape(job.n_traj, -1), So)
+
+
 def test_host_and_device_outputs_agree(ctx):
     job = SMALL[1]
     Wd, Sd = gpu_run(ctx, job, on_device=True)
