@@ -66,6 +66,7 @@ extern "C" {
 #define ISING_ERR_UNSUPPORTED -7  /* d not in {2,3}, lattice too large for SMEM  */
 #define ISING_ERR_NOT_FOUND   -8  /* unknown job id                              */
 #define ISING_ERR_PENDING     -9  /* job not finished yet (jz_poll)              */
+#define ISING_ERR_SCRATCH_LIMIT -10 /* too large for jarzynski_run_noalloc     */
 
 /* Opaque per-device context: stream, device buffers, autotune choices. */
 typedef struct ising_ctx ising_ctx;
@@ -143,6 +144,32 @@ int jarzynski_run_batch(ising_ctx* ctx, const jz_params* jobs, int n_jobs,
  * Arguments, buffers and errors as for jarzynski_run_ex.  Slow by design. */
 int jarzynski_run_plain(ising_ctx* ctx, const jz_params* p, int64_t* work_int_out,
                         int8_t* spins_out);
+
+/* Same computation as jarzynski_run_ex, without allocating anything; the
+ * paper has no counterpart.  It exists for callers that may not allocate
+ * device memory themselves or through us: a plug-in inside an application
+ * whose allocator has already reserved the GPU's memory, or a loop that must
+ * not stall in cudaMalloc / cudaFree (both can synchronise the device).
+ * This call makes no cudaMalloc, cudaFree or other allocating call.  Its
+ * scratch (one job descriptor and the N x 8d switched-site thresholds) lives
+ * in a single file-scope device array of 1 MiB, which every GPU that loads
+ * the library keeps until the process exits.
+ *   p             the transformation; final spins are not returned
+ *   work_int_out  caller-owned DEVICE memory, p->n_traj int64 entries
+ *   cuda_stream   cudaStream_t to enqueue on (NULL = the legacy default stream)
+ * Returns once the work is enqueued: synchronise the stream before reading
+ * work_int_out.  Results are bit-identical to jarzynski_run_ex.
+ * Limit: p->n_step * 8 * p->d <= 262080 threshold words (N <= 16380 in 2D,
+ * N <= 10920 in 3D); larger protocols return ISING_ERR_SCRATCH_LIMIT, host
+ * output memory returns ISING_ERR_ARG, other errors as jarzynski_run_ex.
+ * The first call on a device (the calling thread's current device) looks up
+ * the array's device address once; make that first call before any stream
+ * capture.  All calls share the one array and leave their contents in it;
+ * nothing there needs to start at zero because each call rewrites everything
+ * it reads.  Calls whose GPU work can overlap (different streams with no
+ * ordering between them) race on the array: issue them on one stream or
+ * synchronise in between. */
+int jarzynski_run_noalloc(const jz_params* p, int64_t* work_int_out, void* cuda_stream);
 
 /* FP64 estimator on the device (Appendix A, eq. Jarzynski_theorem; section 2):
  *   *log_ratio    = ln <e^-W>, W_i = beta work_int[i] / n_step, evaluated as a

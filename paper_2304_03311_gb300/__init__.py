@@ -22,6 +22,7 @@ __all__ = [
     "IsingError", "JzParams", "lib_path", "load", "ising_replica_init", "ising_replica_free",
     "ising_sync", "jarzynski_run", "jarzynski_run_ex", "jarzynski_run_batch", "jarzynski_run_plain",
     "estimator_reduce", "ising_strerror", "jz_params_default", "ising_probe",
+    "jarzynski_run_noalloc",
 ]
 
 ISING_OK = 0
@@ -34,6 +35,7 @@ ISING_ERR_TIMEOUT = -6
 ISING_ERR_UNSUPPORTED = -7
 ISING_ERR_NOT_FOUND = -8
 ISING_ERR_PENDING = -9
+ISING_ERR_SCRATCH_LIMIT = -10
 
 
 class JzParams(ctypes.Structure):
@@ -82,6 +84,7 @@ def load():
         "jarzynski_run_ex": (ctypes.c_int, [vp, P(JzParams), vp, vp]),
         "jarzynski_run_batch": (ctypes.c_int, [vp, P(JzParams), ctypes.c_int, P(vp)]),
         "jarzynski_run_plain": (ctypes.c_int, [vp, P(JzParams), vp, vp]),
+        "jarzynski_run_noalloc": (ctypes.c_int, [P(JzParams), vp, vp]),
         "estimator_reduce": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_int, P(ctypes.c_double),
                                             P(ctypes.c_double), P(ctypes.c_double)]),
@@ -167,6 +170,13 @@ def jarzynski_run_ex(ctx, params: JzParams, work_int_out, spins_out=None):
 def jarzynski_run_plain(ctx, params: JzParams, work_int_out, spins_out=None):
     _check(load().jarzynski_run_plain(ctx, ctypes.byref(params), _ptr(work_int_out),
                                       _ptr(spins_out)), "jarzynski_run_plain")
+
+
+def jarzynski_run_noalloc(params: JzParams, work_int_out, cuda_stream: int | None = None):
+    """The allocation-free entry point (see include/isingjz.h): work_int_out
+    must be device memory; returns once the work is enqueued on cuda_stream."""
+    _check(load().jarzynski_run_noalloc(ctypes.byref(params), _ptr(work_int_out), cuda_stream),
+           "jarzynski_run_noalloc")
 
 
 def jarzynski_run_batch(ctx, params_list, work_outs):

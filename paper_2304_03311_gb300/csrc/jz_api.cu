@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <tuple>
 #include <vector>
@@ -539,8 +540,99 @@ const char* ising_strerror(int code)
     case ISING_ERR_UNSUPPORTED: return "unsupported dimension or lattice too large";
     case ISING_ERR_NOT_FOUND: return "unknown job id";
     case ISING_ERR_PENDING: return "job not finished";
+    case ISING_ERR_SCRATCH_LIMIT:
+        return "protocol too long for the fixed scratch of jarzynski_run_noalloc";
     default: return "unknown error";
     }
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------ no-allocation path --
+// jarzynski_run_noalloc: the trajectory kernel with its scratch (job
+// descriptor + switched-site thresholds) in one fixed device array instead of
+// context buffers, for callers that cannot allocate device memory.
+namespace {
+constexpr size_t kNoAllocScratchBytes = (size_t)1 << 20;   // 1 MiB per device
+constexpr size_t kNoAllocJobBytes = 256;                   // descriptor slot
+constexpr size_t kNoAllocMaxThresholds =
+    (kNoAllocScratchBytes - kNoAllocJobBytes) / sizeof(uint32_t);   // 262080 words
+constexpr int kNoAllocMaxDevices = 64;
+static_assert(sizeof(jz::JobDesc) <= kNoAllocJobBytes, "descriptor slot too small");
+}  // namespace
+
+// Held by every GPU that loads the library, until exit.  Host code sees only a
+// host-side stand-in under this name; the device address comes from
+// cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+std::mutex g_noalloc_mutex;                         // guards the two below
+void* g_noalloc_dev_addr[kNoAllocMaxDevices] = {};  // per-device address of the array
+// host staging of the thresholds, sized once at load so calls never allocate
+std::vector<uint32_t> g_noalloc_host_tcut(kNoAllocMaxThresholds);
+
+// Device address of the scratch array on `device` (current), looked up on the
+// first call for that device.
+int noalloc_scratch_address(int device, void** out)
+{
+    if (device < 0 || device >= kNoAllocMaxDevices) return ISING_ERR_UNSUPPORTED;
+    if (!g_noalloc_dev_addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return ISING_ERR_CUDA;
+        }
+        g_noalloc_dev_addr[device] = p;
+    }
+    *out = g_noalloc_dev_addr[device];
+    return ISING_OK;
+}
+}  // namespace
+
+extern "C" int jarzynski_run_noalloc(const jz_params* p, int64_t* work_int_out, void* cuda_stream)
+{
+    if (!p || !work_int_out) return ISING_ERR_ARG;
+    int rc = check_params(p);
+    if (rc) return rc;
+    if ((size_t)p->n_step * 8 * (size_t)p->d > kNoAllocMaxThresholds) return ISING_ERR_SCRATCH_LIMIT;
+    const jz::Geom g = make_geom(p->d, p->L, p->L_t);
+    if (jz::traj_smem_bytes(g) > jz::kMaxSmemPerCta) return ISING_ERR_UNSUPPORTED;
+    if (!is_device_ptr(work_int_out)) return ISING_ERR_ARG;
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) {
+        cudaGetLastError();
+        return ISING_ERR_CUDA;
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    void* base = nullptr;
+    if ((rc = noalloc_scratch_address(device, &base))) return rc;
+    uint32_t* d_tcut = (uint32_t*)((unsigned char*)base + kNoAllocJobBytes);
+
+    jz::JobDesc J{};
+    J.l = p->l;
+    J.n_step = p->n_step;
+    J.n_sweep = p->n_sweep;
+    J.n_therm = p->n_therm;
+    J.dir = p->direction;
+    J.n_traj = p->n_traj;
+    J.traj0 = p->traj0;
+    J.cta0 = 0;
+    build_tables(*p, J.tb, g_noalloc_host_tcut, 0);
+    J.tcut = d_tcut;
+    J.w_out = (long long*)work_int_out;
+    J.spins_out = nullptr;
+    const size_t n_tcut = (size_t)p->n_step * 8 * p->d;
+    // pageable sources: each copy returns once its bytes are staged, so the
+    // host buffers may be reused as soon as the call returns
+    if ((rc = cuda_err(cudaMemcpyAsync(d_tcut, g_noalloc_host_tcut.data(),
+                                       n_tcut * sizeof(uint32_t), cudaMemcpyHostToDevice, st))))
+        return rc;
+    if ((rc = cuda_err(cudaMemcpyAsync(base, &J, sizeof J, cudaMemcpyHostToDevice, st))))
+        return rc;
+    const jz::PhiloxKeys K = key_schedule(p->seed);
+    return cuda_err(jz::launch_traj(p->d, g, K, (const jz::JobDesc*)base, 1, p->n_traj,
+                                    threads_for(g), st));
+}
