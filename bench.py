@@ -53,6 +53,15 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--traj-per-l", type=int, default=None,
+                    help="override the trajectories per transformation (small profiling cases)")
+    ap.add_argument("--n-step", type=int, default=None,
+                    help="override the protocol steps N (small profiling cases)")
+    ap.add_argument("--probe", action="store_true",
+                    help="print the integer-issue probe rates as JSON and exit")
+    ap.add_argument("--plain", type=int, default=0,
+                    help="also time the plain one-lattice-per-launch baseline on this many "
+                         "trajectories of the middle l")
     return ap.parse_args()
 
 
@@ -61,11 +70,33 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def workload_for(config: int, rank: int):
+def workload_for(config: int, rank: int, traj_per_l=None, n_step=None):
     w = wl.CONFIGS[config]()
+    if traj_per_l:
+        w.jobs = [j.with_(n_traj=traj_per_l) for j in w.jobs]
+        w.name += f"_traj{traj_per_l}"
+    if n_step:
+        w.jobs = [j.with_(n_step=n_step) for j in w.jobs]
+        w.name += f"_N{n_step}"
     # weak scaling: rank r owns trajectories [r n, (r+1) n) of every job
     w.jobs = [j.with_(traj0=rank * j.n_traj) for j in w.jobs]
     return w
+
+
+def run_probe():
+    import torch
+    from paper_2304_03311_gb300 import build as jzbuild
+    jzbuild.build()
+    import paper_2304_03311_gb300 as jz
+    dev = torch.cuda.current_device()
+    sampler = ClockSampler(dev)
+    sampler.start()
+    names = ["lop3_chain", "imad_chain", "imad_lop3_iadd3_mix", "philox_blocks"]
+    rates = {n: jz.ising_probe(dev, k) for k, n in enumerate(names)}
+    clocks = sampler.stop()
+    rates["philox_update_ceiling"] = 4 * rates["philox_blocks"]
+    print(json.dumps({"probe": rates, "units": "thread-instr/s (chains), blocks/s (philox), "
+                      "updates/s (ceiling)", "clocks": clocks}), flush=True)
 
 
 def config_block(w, config, world):
@@ -203,7 +234,7 @@ def run_ours(args):
         dist.barrier()
     import paper_2304_03311_gb300 as jz
 
-    w = workload_for(args.config, rank)
+    w = workload_for(args.config, rank, args.traj_per_l, args.n_step)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
     ctx = jz.ising_replica_init(local_rank, 0, stream.cuda_stream)
@@ -308,7 +339,7 @@ def run_ours(args):
     table_bytes = sum(j.n_step * 8 * j.d * 4 + 96 for j in w.jobs)
     h2d = table_bytes + sum(8 * j.n_traj * world for j in w.jobs)
     d2h = sum(8 * j.n_traj for j in w.jobs) + 24 * len(w.jobs)
-    e2e = {"value": updates_step / (e2e_s / e2e_steps), "unit": UNIT,
+    e2e = {"value": updates_step / (e2e_s / e2e_steps) if e2e_steps else None, "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
 
     d = w.jobs[0].d
@@ -321,6 +352,25 @@ def run_ours(args):
                 "traffic": traffic_from_profile(src_hash),
                 "ops_per_update": N_ALG[d], "kernel_ms": kernel_ms,
                 "peak_basis": "152 SMs x 128 int lanes/clk x 2070 MHz (derived)"}
+
+    plain = None
+    if args.plain > 0:
+        j = w.jobs[len(w.jobs) // 2].with_(n_traj=args.plain)
+        pw = torch.empty(j.n_traj, dtype=torch.int64, device=dev)
+        pp = jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj, j.seed,
+                            n_therm=j.n_therm, direction=j.direction, traj0=j.traj0)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        jz.jarzynski_run_plain(ctx, pp, pw)
+        jz.ising_sync(ctx)
+        dt = time.perf_counter() - t0
+        # same trajectories from the fused kernel: identical bits, so equal error
+        fw = torch.empty_like(pw)
+        jz.jarzynski_run_ex(ctx, pp, fw)
+        jz.ising_sync(ctx)
+        plain = {"value": j.updates / dt, "unit": UNIT, "sample": f"{j.n_traj} trajectories "
+                 f"of l = {j.l}", "bit_identical_to_fused": bool(torch.equal(pw, fw)),
+                 "speedup_of_fused": value / (j.updates / dt)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -337,6 +387,7 @@ def run_ours(args):
                 "trajectories_per_s": traj_rate,
                 "c_function_err_max": max(e for _, e in cfun) if cfun else None,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "plain_gpu_baseline": plain,
                 "gpu_launches": args.steps * (n_groups + len(w.jobs)),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
@@ -352,7 +403,7 @@ def run_reference(args):
     import oracle
     oracle.build()
     threads = oracle.max_threads()
-    w = workload_for(args.config, 0)
+    w = workload_for(args.config, 0, args.traj_per_l, args.n_step)
     jobs = w.jobs[:: max(1, len(w.jobs) // 2)][:2]
     n_per = threads
 
@@ -388,7 +439,9 @@ def run_reference(args):
 
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.probe:
+        run_probe()
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

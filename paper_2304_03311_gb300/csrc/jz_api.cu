@@ -177,11 +177,18 @@ void build_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcu
     }
 }
 
+// CTA size G * L_y * TS: each thread owns one (word, y) column of every TS-th
+// time slice.  TS <= L_t, preferably even (a thread's row parity is then the
+// same for all its slices), with about 256 threads and at most 512.
 int threads_for(const jz::Geom& g)
 {
-    int items = g.NR * g.G;
-    int t = ((items + 31) / 32) * 32;
-    return t > 256 ? 256 : t;
+    const int col = g.G * g.Ly;
+    int ts = 256 / col;
+    if (ts < 1) ts = 1;
+    if (ts > 1 && (ts & 1)) ts -= 1;
+    if (ts > g.Lt) ts = g.Lt;
+    while (ts > 1 && col * ts > 512) --ts;
+    return col * ts;
 }
 
 int cuda_err(cudaError_t e)
@@ -198,7 +205,8 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
 {
     const jz_params& p0 = jobs[idx[0]];
     const jz::Geom g = make_geom(p0.d, p0.L, p0.L_t);
-    if (jz::traj_smem_bytes(g) > jz::kMaxSmemPerCta) return ISING_ERR_UNSUPPORTED;
+    if (jz::traj_smem_bytes(g) > jz::kMaxSmemPerCta || threads_for(g) > 512)
+        return ISING_ERR_UNSUPPORTED;
     const int n_jobs = (int)idx.size();
     const int per = 8 * p0.d;
     const int V = 2 * p0.L_t * g.Ly * p0.L;
@@ -598,7 +606,8 @@ extern "C" int jarzynski_run_noalloc(const jz_params* p, int64_t* work_int_out, 
     if (rc) return rc;
     if ((size_t)p->n_step * 8 * (size_t)p->d > kNoAllocMaxThresholds) return ISING_ERR_SCRATCH_LIMIT;
     const jz::Geom g = make_geom(p->d, p->L, p->L_t);
-    if (jz::traj_smem_bytes(g) > jz::kMaxSmemPerCta) return ISING_ERR_UNSUPPORTED;
+    if (jz::traj_smem_bytes(g) > jz::kMaxSmemPerCta || threads_for(g) > 512)
+        return ISING_ERR_UNSUPPORTED;
     if (!is_device_ptr(work_int_out)) return ISING_ERR_ARG;
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess) {

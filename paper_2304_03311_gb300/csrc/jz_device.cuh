@@ -81,6 +81,30 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
     return make_uint4(c0, c1, c2, c3);
 }
 
+// The same block with round 0's product M1 * c2 supplied (hi1, lo1): counter
+// word 2 is the trajectory index, fixed for a whole trajectory.
+__device__ __forceinline__ uint4 philox_r0(uint32_t c0, uint32_t c1, uint32_t hi1, uint32_t lo1,
+                                           uint32_t c3, const PhiloxKeys& K)
+{
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * c0;
+    c0 = hi1 ^ c1 ^ K.k0[0];
+    uint32_t c2 = (uint32_t)(p0 >> 32) ^ c3 ^ K.k1[0];
+    c1 = lo1;
+    c3 = (uint32_t)p0;
+#pragma unroll
+    for (int i = 1; i < 10; ++i) {
+        const uint64_t q0 = (uint64_t)kPhiloxM0 * c0;
+        const uint64_t q1 = (uint64_t)kPhiloxM1 * c2;
+        const uint32_t n0 = (uint32_t)(q1 >> 32) ^ c1 ^ K.k0[i];
+        const uint32_t n2 = (uint32_t)(q0 >> 32) ^ c3 ^ K.k1[i];
+        c1 = (uint32_t)q1;
+        c3 = (uint32_t)q0;
+        c0 = n0;
+        c2 = n2;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
 __device__ __forceinline__ uint32_t word_of(const uint4& u, int j)
 {
     return j == 0 ? u.x : j == 1 ? u.y : j == 2 ? u.z : u.w;
