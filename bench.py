@@ -49,7 +49,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", type=int, choices=[1, 2, 3], default=2)
+    ap.add_argument("--config", type=int, choices=[1, 2, 3, 4], default=2)
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -57,6 +57,10 @@ def parse_args():
                     help="override the trajectories per transformation (small profiling cases)")
     ap.add_argument("--n-step", type=int, default=None,
                     help="override the protocol steps N (small profiling cases)")
+    ap.add_argument("--threads", type=int, default=0,
+                    help="fix the trajectory kernel's CTA size (0 = library default)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the (untimed) CTA-size autotuning per lattice shape")
     ap.add_argument("--probe", action="store_true",
                     help="print the integer-issue probe rates as JSON and exit")
     ap.add_argument("--plain", type=int, default=0,
@@ -79,7 +83,7 @@ def workload_for(config: int, rank: int, traj_per_l=None, n_step=None):
         w.jobs = [j.with_(n_step=n_step) for j in w.jobs]
         w.name += f"_N{n_step}"
     # weak scaling: rank r owns trajectories [r n, (r+1) n) of every job
-    w.jobs = [j.with_(traj0=rank * j.n_traj) for j in w.jobs]
+    w.jobs = [j.with_(traj0=j.traj0 + rank * j.n_traj) for j in w.jobs]
     return w
 
 
@@ -102,6 +106,16 @@ def run_probe():
 def config_block(w, config, world):
     j0 = w.jobs[0]
     ls = [j.l for j in w.jobs]
+    if len({(j.d, j.L, j.L_t) for j in w.jobs}) > 1:
+        shapes = sorted({(j.d, j.L, j.L_t) for j in w.jobs})
+        return {"workload": w.name, "jobs": len(w.jobs),
+                "shapes": [f"{d}D L={L} L_t={Lt}" for d, L, Lt in shapes],
+                "trajectories": w.trajectories * world, "spin_updates": w.updates * world,
+                "n_step": f"{min(j.n_step for j in w.jobs)}-{max(j.n_step for j in w.jobs)}",
+                "n_therm": j0.n_therm, "replicas": 2, "launch": "one persistent CUDA-graph launch",
+                "l2": "flushed between steps (512 MiB write)",
+                "parallelism": f"trajectory shards x{world}" if world > 1 else "single GPU",
+                "source_config": config}
     return {"workload": w.name, "d": j0.d, "L": j0.L, "L_t": j0.L_t, "beta": j0.beta,
             "l": f"{min(ls)}-{max(ls)}" if len(ls) > 1 else ls[0],
             "n_step": j0.n_step, "n_sweep": j0.n_sweep, "n_therm": j0.n_therm,
@@ -244,6 +258,24 @@ def run_ours(args):
               for j in w.jobs]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     n_groups = len({(j.d, j.L, j.L_t, j.seed) for j in w.jobs})
+    tuned = {}
+    plan = None
+    est = None
+    if args.config == 4:
+        # uneven batch: one persistent launch + batched estimator, one CUDA graph
+        est = torch.zeros(3 * len(w.jobs), dtype=torch.float64, device=dev)
+        plan = jz.jz_plan_create(ctx, params, outs, est, args.threads)
+        cta, grid, n_items = jz.jz_plan_info(plan)
+        tuned = {"persistent_cta": cta, "grid": grid, "work_items": n_items}
+        n_groups = 1
+    else:
+        for shape, j in {(j.d, j.L, j.L_t): j for j in w.jobs}.items():
+            if args.threads:
+                jz.ising_set_threads(ctx, *shape, args.threads)
+                tuned[str(shape)] = args.threads
+            elif not args.no_autotune:
+                p = params[w.jobs.index(j)]
+                tuned[str(shape)] = jz.ising_autotune(ctx, p)
 
     def estimate(buffers, gathered_world):
         res = []
@@ -258,8 +290,14 @@ def run_ours(args):
         k1 = torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
             k0.record(stream)
-            jz.jarzynski_run_batch(ctx, params, outs)
+            if plan is not None:
+                jz.jz_plan_launch(plan)
+            else:
+                jz.jarzynski_run_batch(ctx, params, outs)
             k1.record(stream)
+            if plan is not None and world == 1:
+                e = est.cpu().numpy().reshape(-1, 3)
+                return (k0, k1), c_function_errors(w, [(r[1], r[2]) for r in e])
             bufs = outs
             if world > 1:
                 bufs = []
@@ -377,6 +415,8 @@ def run_ours(args):
         rate, trate, cores, sample = cpu_oracle_rate(w, args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
                "trajectories_per_s": trate}
+    if plan is not None:
+        jz.jz_plan_free(plan)
     jz.ising_replica_free(ctx)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -387,8 +427,8 @@ def run_ours(args):
                 "trajectories_per_s": traj_rate,
                 "c_function_err_max": max(e for _, e in cfun) if cfun else None,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "plain_gpu_baseline": plain,
-                "gpu_launches": args.steps * (n_groups + len(w.jobs)),
+                "plain_gpu_baseline": plain, "cta_threads": tuned or "default",
+                "gpu_launches": args.steps * ((2 if plan is not None else n_groups + len(w.jobs))),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:

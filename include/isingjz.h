@@ -137,6 +137,35 @@ int jarzynski_run_ex(ising_ctx* ctx, const jz_params* p, int64_t* work_int_out,
 int jarzynski_run_batch(ising_ctx* ctx, const jz_params* jobs, int n_jobs,
                         int64_t* const* work_outs);
 
+/* Uneven batches (section 3 protocol for every job; lattices of different
+ * d, L, L_t and any l) as ONE persistent launch, captured with the batched
+ * FP64 estimator into a CUDA graph that jz_plan_launch replays.
+ *   jobs, n_jobs  the transformations; all must share one seed
+ *   work_outs     n_jobs caller-owned DEVICE buffers, jobs[j].n_traj int64 each
+ *   est_out       caller-owned DEVICE buffer of 3 n_jobs doubles (nullable):
+ *                 per job ln <e^-W>, Delta S_2 and its jackknife error, as
+ *                 estimator_reduce with 32 blocks
+ *   cta_threads   CTA size of the persistent kernel (0 = autotune: each of
+ *                 256, 288, 384, 512 is timed on a reduced copy of the batch)
+ * The plan keeps its own device tables (charged to the context's budget) and
+ * records the pointers it was given: they must stay valid while it is used.
+ * Each job's results are bit-identical to running it alone with
+ * jarzynski_run_ex.  Errors: as jarzynski_run_ex; ISING_ERR_ARG if seeds
+ * differ or an output is host memory. */
+typedef struct jz_plan jz_plan;
+int jz_plan_create(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const* work_outs,
+                   double* est_out, int cta_threads, jz_plan** out);
+
+/* Enqueues one replay of the plan's graph on the context's stream (counter
+ * reset, persistent kernel, batched estimator); use ising_sync to wait. */
+int jz_plan_launch(jz_plan* plan);
+
+/* Chosen launch shape of a plan: CTA size, grid size, work items. */
+int jz_plan_info(const jz_plan* plan, int* cta_threads, int* grid, int* n_items);
+
+/* Releases the plan (waits for its queued replays). */
+void jz_plan_free(jz_plan* plan);
+
 /* The plain GPU form of the same computation, kept as the comparison baseline:
  * one trajectory per launch sequence, one launch per half-sweep, spins in
  * global memory (section 3 protocol, Appendix A work; same random stream and
@@ -184,6 +213,22 @@ int jarzynski_run_noalloc(const jz_params* p, int64_t* work_int_out, void* cuda_
 int estimator_reduce(ising_ctx* ctx, const int64_t* work_int, int n_traj, double beta,
                      int n_step, int direction, int n_jack_bins, double* log_ratio,
                      double* delta_S2, double* delta_S2_err);
+
+/* Launch-shape control; the paper has no counterpart.  Fixes the CTA size the
+ * context uses for lattices of shape (d, L, L_t): threads = ceil(L/8) * L_y * TS
+ * with 1 <= TS <= L_t (each thread owns one spin-word column of every TS-th
+ * time slice), at most 512; threads = 0 restores the default choice.
+ * Results do not depend on it.  Errors: ISING_ERR_ARG. */
+int ising_set_threads(ising_ctx* ctx, int d, int L, int L_t, int threads);
+
+/* Autotuner; the paper has no counterpart.  Times every admissible CTA size
+ * (TS a power of two up to L_t, and the default) on a short sample of the
+ * transformation p -- same shape, coupling and l, n_therm = 16, N = 16,
+ * n_sweep = 1, min(p->n_traj, 4864) trajectories -- keeps the fastest for p's
+ * shape in the context (as ising_set_threads would) and writes it to
+ * *threads (nullable).  Synchronises the context's stream.
+ * Errors: as jarzynski_run_ex. */
+int ising_autotune(ising_ctx* ctx, const jz_params* p, int* threads);
 
 /* Measurement utility; the paper has no counterpart.  Runs an integer-issue
  * probe on `device` over all SMs at full occupancy and writes its rate:

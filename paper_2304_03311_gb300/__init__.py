@@ -90,6 +90,14 @@ def load():
                                             P(ctypes.c_double), P(ctypes.c_double)]),
         "ising_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "ising_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]),
+        "ising_set_threads": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int]),
+        "ising_autotune": (ctypes.c_int, [vp, P(JzParams), P(ctypes.c_int)]),
+        "jz_plan_create": (ctypes.c_int, [vp, P(JzParams), ctypes.c_int, P(vp), vp, ctypes.c_int,
+                                          P(vp)]),
+        "jz_plan_launch": (ctypes.c_int, [vp]),
+        "jz_plan_info": (ctypes.c_int, [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]),
+        "jz_plan_free": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -201,3 +209,45 @@ def ising_probe(device: int, kind: int) -> float:
     r = ctypes.c_double()
     _check(load().ising_probe(int(device), int(kind), ctypes.byref(r)), "ising_probe")
     return r.value
+
+
+def ising_set_threads(ctx, d: int, L: int, L_t: int, threads: int) -> None:
+    """Fix the CTA size for lattices of shape (d, L, L_t) (0 = default)."""
+    _check(load().ising_set_threads(ctx, int(d), int(L), int(L_t), int(threads)),
+           "ising_set_threads")
+
+
+def ising_autotune(ctx, params: JzParams) -> int:
+    """Time the admissible CTA sizes on a short sample of `params`, keep the
+    fastest for its shape in the context, and return it."""
+    t = ctypes.c_int()
+    _check(load().ising_autotune(ctx, ctypes.byref(params), ctypes.byref(t)), "ising_autotune")
+    return t.value
+
+
+def jz_plan_create(ctx, params_list, work_outs, est_out=None, cta_threads: int = 0):
+    """Persistent-launch plan for an uneven batch (see include/isingjz.h);
+    work_outs and est_out must be device memory.  Returns the plan handle."""
+    n = len(params_list)
+    arr = (JzParams * n)(*params_list)
+    outs = (ctypes.c_void_p * n)(*[_ptr(w) for w in work_outs])
+    plan = ctypes.c_void_p()
+    _check(load().jz_plan_create(ctx, arr, n, outs, _ptr(est_out), int(cta_threads),
+                                 ctypes.byref(plan)), "jz_plan_create")
+    return plan.value
+
+
+def jz_plan_launch(plan) -> None:
+    _check(load().jz_plan_launch(plan), "jz_plan_launch")
+
+
+def jz_plan_info(plan):
+    """(CTA size, grid size, work items) of a plan."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().jz_plan_info(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "jz_plan_info")
+    return a.value, b.value, c.value
+
+
+def jz_plan_free(plan) -> None:
+    load().jz_plan_free(plan)

@@ -2,6 +2,7 @@
 // threshold tables, device buffers, launch grouping, estimator.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -27,6 +28,7 @@ cudaError_t plain_trajectory(int D, const Geom& g, const PhiloxKeys& K, int l, i
                              long long* w, cudaStream_t st);
 constexpr int kMaxJackBlocksHost = 64;
 constexpr size_t kMaxSmemPerCta = 227 * 1024;
+constexpr int kMaxTeamsHost = 64;   // teams per CTA of the persistent kernel
 }  // namespace jz
 
 // Grow-only device buffer charged against the context's HBM budget.
@@ -44,6 +46,7 @@ struct ising_ctx {
     DevBuf tcut, jobs, work, spins, est_in, est_out;
     std::vector<uint32_t> h_tcut;
     std::vector<jz::JobDesc> h_jobs;
+    std::map<std::tuple<int, int, int>, int> threads;   // per-shape CTA size (tuned)
 };
 
 static_assert(sizeof(jz_params) == 64, "jz_params layout is part of the ABI");
@@ -191,6 +194,22 @@ int threads_for(const jz::Geom& g)
     return col * ts;
 }
 
+// A CTA size is admissible for g iff it is G * L_y * TS with 1 <= TS <= L_t
+// and at most 512 threads.
+bool threads_ok(const jz::Geom& g, int threads)
+{
+    const int col = g.G * g.Ly;
+    return threads > 0 && threads <= 512 && threads % col == 0 && threads / col <= g.Lt;
+}
+
+// The context's CTA size for this shape: the tuned / fixed one, else the default.
+int ctx_threads(const ising_ctx* ctx, int d, const jz::Geom& g)
+{
+    auto it = ctx->threads.find(std::make_tuple(d, g.L, g.Lt));
+    if (it != ctx->threads.end() && threads_ok(g, it->second)) return it->second;
+    return threads_for(g);
+}
+
 int cuda_err(cudaError_t e)
 {
     if (e == cudaSuccess) return ISING_OK;
@@ -265,7 +284,7 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
         return rc;
     const jz::PhiloxKeys K = key_schedule(p0.seed);
     if ((rc = cuda_err(jz::launch_traj(p0.d, g, K, (const jz::JobDesc*)ctx->jobs.ptr, n_jobs,
-                                       n_cta, threads_for(g), st))))
+                                       n_cta, ctx_threads(ctx, p0.d, g), st))))
         return rc;
     if (!outs_on_device || (n_spin_traj && !spins_on_device)) {
         long long c = 0, so = 0;
@@ -424,6 +443,74 @@ int jarzynski_run(ising_ctx* ctx, int d, int L, int L_t, double beta, int l, int
     p.n_traj = n_traj;
     p.seed = seed;
     return jarzynski_run_ex(ctx, &p, work_int_out, nullptr);
+}
+
+int ising_set_threads(ising_ctx* ctx, int d, int L, int L_t, int threads)
+{
+    if (!ctx || (d != 2 && d != 3) || L < 2 || L_t < 2 || (L & 1) || (L_t & 1))
+        return ISING_ERR_ARG;
+    const auto key = std::make_tuple(d, L, L_t);
+    if (threads == 0) {
+        ctx->threads.erase(key);
+        return ISING_OK;
+    }
+    if (!threads_ok(make_geom(d, L, L_t), threads)) return ISING_ERR_ARG;
+    ctx->threads[key] = threads;
+    return ISING_OK;
+}
+
+int ising_autotune(ising_ctx* ctx, const jz_params* p, int* threads)
+{
+    if (!ctx || !p) return ISING_ERR_ARG;
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
+    const jz::Geom g = make_geom(p->d, p->L, p->L_t);
+    if (jz::traj_smem_bytes(g) > jz::kMaxSmemPerCta || threads_for(g) > 512)
+        return ISING_ERR_UNSUPPORTED;
+    jz_params s = *p;
+    s.n_therm = 16;
+    s.n_step = 16;
+    s.n_sweep = 1;
+    s.n_traj = p->n_traj < 4864 ? p->n_traj : 4864;
+    s.traj0 = 0;
+    if ((rc = ensure(ctx, ctx->est_in, (size_t)s.n_traj * sizeof(long long)))) return rc;
+    int64_t* out = (int64_t*)ctx->est_in.ptr;
+    std::vector<int> cands;
+    const int col = g.G * g.Ly;
+    for (int ts = 1; ts <= g.Lt && col * ts <= 512; ts *= 2) cands.push_back(col * ts);
+    if (std::find(cands.begin(), cands.end(), threads_for(g)) == cands.end())
+        cands.push_back(threads_for(g));
+    const auto key = std::make_tuple(p->d, p->L, p->L_t);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return ISING_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return ISING_ERR_CUDA;
+    }
+    int best = threads_for(g);
+    float best_ms = 1e30f;
+    int64_t* outs[1] = {out};
+    for (int t : cands) {
+        ctx->threads[key] = t;
+        if ((rc = run_jobs(ctx, &s, 1, outs, nullptr))) break;           // warm-up
+        cudaEventRecord(e0, ctx->stream);
+        if ((rc = run_jobs(ctx, &s, 1, outs, nullptr))) break;
+        cudaEventRecord(e1, ctx->stream);
+        if ((rc = cuda_err(cudaEventSynchronize(e1)))) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->threads[key] = best;
+    if (rc) return rc;
+    if (threads) *threads = best;
+    return ISING_OK;
 }
 
 int jarzynski_run_batch(ising_ctx* ctx, const jz_params* jobs, int n_jobs,
@@ -645,3 +732,308 @@ extern "C" int jarzynski_run_noalloc(const jz_params* p, int64_t* work_int_out, 
     return cuda_err(jz::launch_traj(p->d, g, K, (const jz::JobDesc*)base, 1, p->n_traj,
                                     threads_for(g), st));
 }
+
+// --------------------------------------------------- persistent batch plans --
+namespace jz {
+cudaError_t persistent_prepare(size_t smem, int threads, int* blocks_per_sm);
+cudaError_t launch_persistent(const BatchJob* jobs, const int2* items, int n_items,
+                              unsigned int* counter, const PhiloxKeys& K, int grid, int threads,
+                              size_t smem, cudaStream_t st);
+cudaError_t launch_estimator_batch(const EstJob* jobs, int n_jobs, double* out, cudaStream_t st);
+}  // namespace jz
+
+struct jz_plan {
+    ising_ctx* ctx = nullptr;
+    int n_jobs = 0, n_items = 0, threads = 0, grid = 0;
+    size_t smem = 0;
+    jz::PhiloxKeys K{};
+    DevBuf jobs, items, tcut, counter, est_jobs;
+    double* est_out = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void plan_release(jz_plan* pl)
+{
+    if (!pl) return;
+    ising_ctx* ctx = pl->ctx;
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    for (DevBuf* b : {&pl->jobs, &pl->items, &pl->tcut, &pl->counter, &pl->est_jobs})
+        if (b->ptr) {
+            cudaFree(b->ptr);
+            ctx->used -= b->bytes;
+        }
+    delete pl;
+}
+
+// Team size of one job inside a CTA of `cta` threads: G * L_y * TS with the
+// most threads in use (teams * team size), ties to even TS; teams <= 64.
+void team_shape(const jz::Geom& g, int cta, int* team_threads, int* teams)
+{
+    const int col = g.G * g.Ly;
+    int best_t = col, best_use = -1;
+    for (int ts = 1; ts <= g.Lt && col * ts <= cta; ++ts) {
+        const int tt = col * ts;
+        int nt = cta / tt;
+        if (nt > jz::kMaxTeamsHost) nt = jz::kMaxTeamsHost;
+        const int use = nt * tt;
+        if (use > best_use || (use == best_use && (ts & 1) == 0)) {
+            best_use = use;
+            best_t = tt;
+        }
+    }
+    *team_threads = best_t;
+    int nt = cta / best_t;
+    *teams = nt > jz::kMaxTeamsHost ? jz::kMaxTeamsHost : nt;
+}
+
+// Builds (not captures) a plan for a fixed CTA size.
+int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const* work_outs,
+               double* est_out, int cta, jz_plan** out)
+{
+    jz_plan* pl = new (std::nothrow) jz_plan();
+    if (!pl) return ISING_ERR_NOMEM;
+    pl->ctx = ctx;
+    pl->n_jobs = n_jobs;
+    pl->threads = cta;
+    pl->est_out = est_out;
+    pl->K = key_schedule(jobs[0].seed);
+    std::vector<jz::BatchJob> bj(n_jobs);
+    std::vector<uint32_t> tcut;
+    std::vector<size_t> toff(n_jobs);
+    std::vector<std::pair<double, int2>> items;
+    size_t smem = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        const jz_params& p = jobs[j];
+        jz::BatchJob& B = bj[j];
+        B.g = make_geom(p.d, p.L, p.L_t);
+        B.D = p.d;
+        B.fast = (B.g.Lh % 4) == 0;
+        team_shape(B.g, cta, &B.team_threads, &B.teams);
+        B.lattice_words = 2 * B.g.NR * B.g.G;
+        if (B.g.G * B.g.Ly > cta) {
+            plan_release(pl);
+            return ISING_ERR_UNSUPPORTED;
+        }
+        while (B.teams > 1 && (size_t)B.teams * B.lattice_words * 4 > jz::kMaxSmemPerCta)
+            --B.teams;
+        const size_t sm = (size_t)B.teams * B.lattice_words * 4;
+        if (sm > jz::kMaxSmemPerCta) {
+            plan_release(pl);
+            return ISING_ERR_UNSUPPORTED;
+        }
+        smem = std::max(smem, sm);
+        toff[j] = tcut.size();
+        tcut.resize(tcut.size() + (size_t)p.n_step * 8 * p.d);
+        jz::JobDesc& J = B.J;
+        J.l = p.l;
+        J.n_step = p.n_step;
+        J.n_sweep = p.n_sweep;
+        J.n_therm = p.n_therm;
+        J.dir = p.direction;
+        J.n_traj = p.n_traj;
+        J.traj0 = p.traj0;
+        J.cta0 = 0;
+        build_tables(p, J.tb, tcut, toff[j]);
+        J.w_out = (long long*)work_outs[j];
+        J.spins_out = nullptr;
+        const double per_traj = (double)(2 * p.L_t * B.g.Ly * p.L) *
+                                ((double)p.n_therm + (double)p.n_step * p.n_sweep);
+        for (int lo = 0; lo < p.n_traj; lo += B.teams) {
+            const int cnt = std::min(B.teams, p.n_traj - lo);
+            items.push_back({per_traj * cnt, make_int2(j, lo)});
+        }
+    }
+    // largest items first
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<double, int2>& a, const std::pair<double, int2>& b) {
+                         return a.first > b.first;
+                     });
+    pl->n_items = (int)items.size();
+    pl->smem = smem;
+    int rc;
+    if ((rc = ensure(ctx, pl->tcut, tcut.size() * sizeof(uint32_t))) ||
+        (rc = ensure(ctx, pl->jobs, bj.size() * sizeof(jz::BatchJob))) ||
+        (rc = ensure(ctx, pl->items, items.size() * sizeof(int2))) ||
+        (rc = ensure(ctx, pl->counter, sizeof(unsigned int))) ||
+        (rc = ensure(ctx, pl->est_jobs, (size_t)n_jobs * sizeof(jz::EstJob)))) {
+        plan_release(pl);
+        return rc;
+    }
+    uint32_t* d_tcut = (uint32_t*)pl->tcut.ptr;
+    for (int j = 0; j < n_jobs; ++j) bj[j].J.tcut = d_tcut + toff[j];
+    std::vector<int2> it(items.size());
+    for (size_t i = 0; i < items.size(); ++i) it[i] = items[i].second;
+    std::vector<jz::EstJob> ej(n_jobs);
+    for (int j = 0; j < n_jobs; ++j) {
+        ej[j].w = (const long long*)work_outs[j];
+        ej[j].n = jobs[j].n_traj;
+        ej[j].direction = jobs[j].direction;
+        ej[j].n_blocks = std::min(32, jobs[j].n_traj);
+        ej[j].scale = jobs[j].beta / (double)jobs[j].n_step;
+    }
+    cudaStream_t st = ctx->stream;
+    if ((rc = cuda_err(cudaMemcpyAsync(pl->tcut.ptr, tcut.data(), tcut.size() * sizeof(uint32_t),
+                                       cudaMemcpyHostToDevice, st))) ||
+        (rc = cuda_err(cudaMemcpyAsync(pl->jobs.ptr, bj.data(), bj.size() * sizeof(jz::BatchJob),
+                                       cudaMemcpyHostToDevice, st))) ||
+        (rc = cuda_err(cudaMemcpyAsync(pl->items.ptr, it.data(), it.size() * sizeof(int2),
+                                       cudaMemcpyHostToDevice, st))) ||
+        (rc = cuda_err(cudaMemcpyAsync(pl->est_jobs.ptr, ej.data(), ej.size() * sizeof(jz::EstJob),
+                                       cudaMemcpyHostToDevice, st))) ||
+        (rc = cuda_err(cudaStreamSynchronize(st)))) {
+        plan_release(pl);
+        return rc;
+    }
+    int per_sm = 0;
+    cudaDeviceProp prop;
+    if ((rc = cuda_err(jz::persistent_prepare(smem, cta, &per_sm))) ||
+        (rc = cuda_err(cudaGetDeviceProperties(&prop, ctx->device)))) {
+        plan_release(pl);
+        return rc;
+    }
+    if (per_sm < 1) {
+        plan_release(pl);
+        return ISING_ERR_UNSUPPORTED;
+    }
+    pl->grid = std::min(per_sm * prop.multiProcessorCount, pl->n_items);
+    *out = pl;
+    return ISING_OK;
+}
+
+// Enqueues the plan's work directly (no graph): counter reset, kernel, estimator.
+int plan_enqueue(jz_plan* pl)
+{
+    cudaStream_t st = pl->ctx->stream;
+    int rc;
+    if ((rc = cuda_err(cudaMemsetAsync(pl->counter.ptr, 0, sizeof(unsigned int), st)))) return rc;
+    if ((rc = cuda_err(jz::launch_persistent((const jz::BatchJob*)pl->jobs.ptr,
+                                             (const int2*)pl->items.ptr, pl->n_items,
+                                             (unsigned int*)pl->counter.ptr, pl->K, pl->grid,
+                                             pl->threads, pl->smem, st))))
+        return rc;
+    if (pl->est_out)
+        return cuda_err(jz::launch_estimator_batch((const jz::EstJob*)pl->est_jobs.ptr, pl->n_jobs,
+                                                   pl->est_out, st));
+    return ISING_OK;
+}
+
+int plan_capture(jz_plan* pl)
+{
+    cudaStream_t st = pl->ctx->stream;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return ISING_ERR_CUDA;
+    }
+    const int rc = plan_enqueue(pl);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (rc || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc ? rc : ISING_ERR_CUDA;
+    }
+    pl->graph = graph;
+    if (cudaGraphInstantiate(&pl->exec, graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        pl->exec = nullptr;
+        return ISING_ERR_CUDA;
+    }
+    return ISING_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int jz_plan_create(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const* work_outs,
+                   double* est_out, int cta_threads, jz_plan** out)
+{
+    if (!ctx || !jobs || n_jobs < 1 || !work_outs || !out) return ISING_ERR_ARG;
+    *out = nullptr;
+    if (cta_threads != 0 && (cta_threads < 32 || cta_threads > 512 || cta_threads % 32))
+        return ISING_ERR_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
+    for (int j = 0; j < n_jobs; ++j) {
+        const int rc = check_params(&jobs[j]);
+        if (rc) return rc;
+        if (jobs[j].seed != jobs[0].seed || !work_outs[j] || !is_device_ptr(work_outs[j]))
+            return ISING_ERR_ARG;
+    }
+    if (est_out && !is_device_ptr(est_out)) return ISING_ERR_ARG;
+    int rc;
+    int cta = cta_threads;
+    if (cta == 0) {
+        // autotune on a reduced copy: 1/16 of the trajectories, 8 + 8 sweeps
+        std::vector<jz_params> small(jobs, jobs + n_jobs);
+        for (auto& p : small) {
+            p.n_traj = std::max(1, p.n_traj / 16);
+            p.n_therm = 8;
+            p.n_step = 8;
+            p.n_sweep = 1;
+        }
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+            return ISING_ERR_CUDA;
+        float best_ms = 1e30f;
+        for (int cand : {256, 288, 384, 512}) {
+            jz_plan* pl = nullptr;
+            if (plan_build(ctx, small.data(), n_jobs, work_outs, nullptr, cand, &pl)) continue;
+            float ms = 1e30f;
+            if (!plan_enqueue(pl)) {
+                cudaEventRecord(e0, ctx->stream);
+                if (!plan_enqueue(pl)) {
+                    cudaEventRecord(e1, ctx->stream);
+                    if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+                }
+            }
+            cudaStreamSynchronize(ctx->stream);
+            cudaGetLastError();
+            plan_release(pl);
+            if (ms < best_ms) {
+                best_ms = ms;
+                cta = cand;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (cta == 0) return ISING_ERR_UNSUPPORTED;
+    }
+    jz_plan* pl = nullptr;
+    if ((rc = plan_build(ctx, jobs, n_jobs, work_outs, est_out, cta, &pl))) return rc;
+    if ((rc = plan_capture(pl))) {
+        plan_release(pl);
+        return rc;
+    }
+    *out = pl;
+    return ISING_OK;
+}
+
+int jz_plan_launch(jz_plan* plan)
+{
+    if (!plan || !plan->exec) return ISING_ERR_ARG;
+    if (cudaSetDevice(plan->ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
+    return cuda_err(cudaGraphLaunch(plan->exec, plan->ctx->stream));
+}
+
+int jz_plan_info(const jz_plan* plan, int* cta_threads, int* grid, int* n_items)
+{
+    if (!plan) return ISING_ERR_ARG;
+    if (cta_threads) *cta_threads = plan->threads;
+    if (grid) *grid = plan->grid;
+    if (n_items) *n_items = plan->n_items;
+    return ISING_OK;
+}
+
+void jz_plan_free(jz_plan* plan)
+{
+    if (!plan) return;
+    cudaSetDevice(plan->ctx->device);
+    cudaStreamSynchronize(plan->ctx->stream);
+    plan_release(plan);
+}
+
+}  // extern "C"

@@ -57,6 +57,25 @@ struct JobDesc {
     int8_t* spins_out;      // [n_traj][V] final spins (+-1) or nullptr
 };
 
+// One job of a persistent batch launch.
+struct BatchJob {
+    JobDesc J;            // thresholds, outputs, trajectory range
+    Geom g;
+    int D, fast;
+    int team_threads;     // G * L_y * TS threads run one trajectory
+    int teams;            // trajectories per work item (teams per CTA)
+    int lattice_words;    // 2 * NR * G spin words per team
+};
+
+// One job of the batched estimator.
+struct EstJob {
+    const long long* w;   // n work values W_int
+    int n;
+    int direction;
+    int n_blocks;         // jackknife blocks, <= 64 and <= n
+    double scale;         // beta / N
+};
+
 // q = n / d for n * d < 2^32, with magic = ceil(2^32 / d) (d > 1).
 __device__ __forceinline__ uint32_t div_magic(uint32_t n, uint32_t d, uint32_t magic)
 {

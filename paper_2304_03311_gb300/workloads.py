@@ -87,7 +87,9 @@ def config4(seed: int = 0) -> Workload:
     """Uneven batch: 2D L in {32,48,64,96,128}, 3D L in {8,12,16,24}, L_t = L,
     critical beta, every l in [1, L/2]; per item n_traj in {1024..8192} and
     N in {500..4000} drawn log-uniformly (powers of two grid) from
-    numpy.random.default_rng(seed); 1 sweep per step."""
+    numpy.random.default_rng(seed); 1 sweep per step.  All jobs use Philox
+    seed 0 (one persistent launch shares one key; the counter's l, direction
+    and trajectory words keep the streams of different jobs apart)."""
     rng = np.random.default_rng(seed)
     jobs = []
     shapes = [(2, L) for L in (32, 48, 64, 96, 128)] + [(3, L) for L in (8, 12, 16, 24)]
@@ -96,7 +98,8 @@ def config4(seed: int = 0) -> Workload:
         for l in range(1, L // 2 + 1):
             n_traj = int(2 ** rng.integers(10, 14))          # 1024 .. 8192
             n_step = int(500 * 2 ** rng.integers(0, 4))       # 500 .. 4000
-            jobs.append(Job(d, L, L, beta, l, n_step, 1, n_traj, seed=1000 + i))
+            # distinct trajectory ranges per shape keep the shapes' streams apart
+            jobs.append(Job(d, L, L, beta, l, n_step, 1, n_traj, seed=0, traj0=i << 24))
     return Workload("uneven_batch_2d_3d", jobs)
 
 

@@ -113,6 +113,32 @@ def test_plain_baseline_is_bit_exact(ctx, job):
     np.testing.assert_array_equal(s.cpu().numpy().reshape(job.n_traj, -1), So)
 
 
+@pytest.mark.parametrize("job", [SMALL[0], SMALL[1], SMALL[8], SMALL[9]],
+                         ids=["2d", "2d_ragged", "3d", "3d_ragged_rev"])
+def test_cta_size_does_not_change_results(job):
+    """Every admissible CTA size, and the autotuner's choice, give the same bits."""
+    c = jz.ising_replica_init(0, 0, None)
+    try:
+        ref, _ = gpu_run(c, job, spins=False)
+        col = ((job.L // 2 + 3) // 4) * (job.L if job.d == 3 else 1)
+        ts = 1
+        while ts <= job.L_t and col * ts <= 512:
+            jz.ising_set_threads(c, job.d, job.L, job.L_t, col * ts)
+            W, _ = gpu_run(c, job, spins=False)
+            np.testing.assert_array_equal(W, ref)
+            ts *= 2
+        with pytest.raises(jz.IsingError):
+            jz.ising_set_threads(c, job.d, job.L, job.L_t, col * (job.L_t + 1))
+        p = jz.make_params(job.d, job.L, job.L_t, job.beta, job.l, job.n_step, job.n_sweep,
+                           job.n_traj, job.seed, n_therm=job.n_therm, direction=job.direction)
+        best = jz.ising_autotune(c, p)
+        assert best % col == 0 and 1 <= best // col <= job.L_t
+        W, _ = gpu_run(c, job, spins=False)
+        np.testing.assert_array_equal(W, ref)
+    finally:
+        jz.ising_replica_free(c)
+
+
 def test_host_and_device_outputs_agree(ctx):
     job = SMALL[1]
     Wd, Sd = gpu_run(ctx, job, on_device=True)
