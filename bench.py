@@ -49,7 +49,12 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", type=int, choices=[1, 2, 3, 4], default=2)
+    ap.add_argument("--config", type=int, choices=[1, 2, 3, 4, 5], default=2)
+    ap.add_argument("--serve-jobs", type=int, default=200, help="served stream: jobs")
+    ap.add_argument("--rate", type=float, default=50.0, help="served stream: arrivals per second")
+    ap.add_argument("--inflight", type=int, default=16, help="served stream: stream slots")
+    ap.add_argument("--serve-budget-mb", type=int, default=4096,
+                    help="served stream: admission budget (MiB)")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -435,6 +440,57 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------ serving -------
+def run_serve(args):
+    """Served stream: jobs arrive as a Poisson process and are submitted to the
+    continuous-batching server at their arrival times; reports sustained spin
+    updates/s over the makespan and p50 / p99 latency (submit -> result)."""
+    import torch
+    from paper_2304_03311_gb300 import build as jzbuild
+    jzbuild.build()
+    import paper_2304_03311_gb300 as jz
+
+    arrivals = wl.config5(n_jobs=args.serve_jobs, rate=args.rate)
+    ctx = jz.ising_replica_init(0, 0, None)
+    server = jz.jz_server_create(ctx, args.serve_budget_mb << 20, args.inflight)
+    mk = lambda j: jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj,
+                                  j.seed, n_therm=j.n_therm, direction=j.direction,
+                                  traj0=j.traj0)
+    # warm-up: one small job per dimension through the same server
+    for j in (wl.Job(2, 32, 32, wl.BETA_C_2D, 3, 20, 1, 64), wl.Job(3, 8, 8, wl.BETA_C_3D, 2, 20, 1, 64)):
+        jz.jz_wait(server, jz.jz_submit(server, mk(j)))
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    t0 = time.perf_counter()
+    ids = []
+    for t_arr, j in arrivals:
+        delay = t0 + t_arr - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        ids.append(jz.jz_submit(server, mk(j)))
+    results = [jz.jz_wait(server, i, 7200.0) for i in ids]
+    clocks = sampler.stop()
+    jz.jz_server_free(server)
+    jz.ising_replica_free(ctx)
+    bad = [r.status for r in results if r.status != 0]
+    lat = sorted(r.done_s - r.submit_s for r in results)
+    makespan = max(r.done_s for r in results) - min(r.submit_s for r in results)
+    updates = sum(r.updates for r in results)
+    pct = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
+    line = {"metric": METRIC, "value": updates / makespan, "unit": UNIT, "n_gpus": 1,
+            "steps": 1, "warmup": 1, "ms_per_step": makespan * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (Philox hot starts; no dataset)",
+            "config": {"workload": f"served_stream_poisson{args.rate:g}_jobs{len(ids)}",
+                       "inflight_slots": args.inflight, "hbm_budget_mb": args.serve_budget_mb,
+                       "source_config": 5},
+            "latency_s": {"p50": pct(0.50), "p99": pct(0.99), "max": lat[-1]},
+            "trajectories_per_s": sum(j.n_traj for _, j in arrivals) / makespan,
+            "jobs_failed": len(bad), "makespan_s": makespan, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------- reference arm -----
 def run_reference(args):
     rank, world, _ = dist_env()
@@ -483,6 +539,8 @@ def main():
         run_probe()
     elif args.impl == "reference":
         run_reference(args)
+    elif args.config == 5:
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -166,6 +166,56 @@ int jz_plan_info(const jz_plan* plan, int* cta_threads, int* grid, int* n_items)
 /* Releases the plan (waits for its queued replays). */
 void jz_plan_free(jz_plan* plan);
 
+/* ---------------------------------------------------------------- serving --
+ * A continuous-batching server for c-function jobs (each job one
+ * transformation of section 3, estimated as in estimator_reduce).  A host
+ * thread admits submitted jobs in arrival order whenever a stream slot is free
+ * and the job's device memory (thresholds, work array, estimator output) fits
+ * the server's HBM budget, launches it on its slot's stream -- so jobs that
+ * arrive while others run overlap on the device -- and, when its completion
+ * event fires, copies the result back and frees the slot for the next job.
+ * A job's lattice and random state stay in one CTA's shared memory for its
+ * whole protocol.  Results are bit-identical to running the job alone. */
+typedef struct jz_server jz_server;
+
+typedef struct jz_result {
+    int status;                 /* ISING_OK or the job's error code          */
+    double log_ratio;           /* ln <e^-W>                                 */
+    double delta_S2;            /* Delta S_2 of the transformation           */
+    double delta_S2_err;        /* jackknife error (32 blocks)               */
+    double submit_s, start_s, done_s;   /* server clock (s): submitted,
+                                           launched, completion observed     */
+    long long updates;          /* spin updates the job performed            */
+} jz_result;
+
+/* Creates a server on the context's device.
+ *   hbm_budget_bytes  admission budget for the jobs' device memory (> 0)
+ *   max_inflight      jobs on the device at once (1..64), one stream each
+ * The context must outlive the server and is used only for its device and its
+ * autotuned CTA sizes.  Errors: ISING_ERR_ARG, ISING_ERR_CUDA, ISING_ERR_NOMEM. */
+int jz_server_create(ising_ctx* ctx, size_t hbm_budget_bytes, int max_inflight,
+                     jz_server** out);
+
+/* Queues a job (parameters are copied); returns its id in *job_id.  Invalid
+ * parameters are reported at once; a job that can never fit the budget
+ * finishes with status ISING_ERR_NOMEM. */
+int jz_submit(jz_server* s, const jz_params* p, uint64_t* job_id);
+
+/* ISING_OK and *out filled when the job is finished; ISING_ERR_PENDING while
+ * it is queued or running; ISING_ERR_NOT_FOUND for an unknown id. */
+int jz_poll(jz_server* s, uint64_t job_id, jz_result* out);
+
+/* As jz_poll, but waits up to timeout_s seconds; ISING_ERR_TIMEOUT when the
+ * job is still unfinished then (the job keeps running). */
+int jz_wait(jz_server* s, uint64_t job_id, double timeout_s, jz_result* out);
+
+/* Copies a finished job's W_int (n_traj entries) to host memory work_out. */
+int jz_server_work(jz_server* s, uint64_t job_id, int64_t* work_out);
+
+/* Stops admitting, waits for the jobs on the device, drops queued ones and
+ * releases the server. */
+void jz_server_free(jz_server* s);
+
 /* The plain GPU form of the same computation, kept as the comparison baseline:
  * one trajectory per launch sequence, one launch per half-sweep, spins in
  * global memory (section 3 protocol, Appendix A work; same random stream and

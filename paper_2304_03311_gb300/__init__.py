@@ -49,6 +49,15 @@ class JzParams(ctypes.Structure):
     ]
 
 
+class JzResult(ctypes.Structure):
+    """Mirror of ``jz_result`` in include/isingjz.h."""
+    _fields_ = [
+        ("status", ctypes.c_int), ("log_ratio", ctypes.c_double), ("delta_S2", ctypes.c_double),
+        ("delta_S2_err", ctypes.c_double), ("submit_s", ctypes.c_double),
+        ("start_s", ctypes.c_double), ("done_s", ctypes.c_double), ("updates", ctypes.c_longlong),
+    ]
+
+
 class IsingError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
@@ -98,6 +107,12 @@ def load():
         "jz_plan_launch": (ctypes.c_int, [vp]),
         "jz_plan_info": (ctypes.c_int, [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]),
         "jz_plan_free": (None, [vp]),
+        "jz_server_create": (ctypes.c_int, [vp, ctypes.c_size_t, ctypes.c_int, P(vp)]),
+        "jz_submit": (ctypes.c_int, [vp, P(JzParams), P(ctypes.c_uint64)]),
+        "jz_poll": (ctypes.c_int, [vp, ctypes.c_uint64, P(JzResult)]),
+        "jz_wait": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_double, P(JzResult)]),
+        "jz_server_work": (ctypes.c_int, [vp, ctypes.c_uint64, vp]),
+        "jz_server_free": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -251,3 +266,40 @@ def jz_plan_info(plan):
 
 def jz_plan_free(plan) -> None:
     load().jz_plan_free(plan)
+
+
+def jz_server_create(ctx, hbm_budget_bytes: int, max_inflight: int):
+    s = ctypes.c_void_p()
+    _check(load().jz_server_create(ctx, int(hbm_budget_bytes), int(max_inflight),
+                                   ctypes.byref(s)), "jz_server_create")
+    return s.value
+
+
+def jz_submit(server, params: JzParams) -> int:
+    jid = ctypes.c_uint64()
+    _check(load().jz_submit(server, ctypes.byref(params), ctypes.byref(jid)), "jz_submit")
+    return jid.value
+
+
+def jz_poll(server, job_id: int):
+    """The job's JzResult, or None while it is pending."""
+    r = JzResult()
+    rc = load().jz_poll(server, int(job_id), ctypes.byref(r))
+    if rc == ISING_ERR_PENDING:
+        return None
+    _check(rc, "jz_poll")
+    return r
+
+
+def jz_wait(server, job_id: int, timeout_s: float = 3600.0) -> JzResult:
+    r = JzResult()
+    _check(load().jz_wait(server, int(job_id), float(timeout_s), ctypes.byref(r)), "jz_wait")
+    return r
+
+
+def jz_server_work(server, job_id: int, work_out) -> None:
+    _check(load().jz_server_work(server, int(job_id), _ptr(work_out)), "jz_server_work")
+
+
+def jz_server_free(server) -> None:
+    load().jz_server_free(server)

@@ -15,43 +15,11 @@
 #include "../../include/isingjz.h"
 #include "jz_device.cuh"
 
-namespace jz {
-size_t traj_smem_bytes(const Geom& g);
-cudaError_t launch_traj(int D, const Geom& g, const PhiloxKeys& K, const JobDesc* jobs,
-                        int n_jobs, long long n_cta, int threads, cudaStream_t st);
-cudaError_t launch_estimator(const long long* w_int, int n, double scale, int direction,
-                             int n_blocks, double* out, cudaStream_t st);
-double run_probe(int kind, int device);
-cudaError_t plain_trajectory(int D, const Geom& g, const PhiloxKeys& K, int l, int dir,
-                             int n_step, int n_sweep, int n_therm, uint32_t traj,
-                             const uint32_t tb[4], const uint32_t* tcut, int8_t* s,
-                             long long* w, cudaStream_t st);
-constexpr int kMaxJackBlocksHost = 64;
-constexpr size_t kMaxSmemPerCta = 227 * 1024;
-constexpr int kMaxTeamsHost = 64;   // teams per CTA of the persistent kernel
-}  // namespace jz
-
-// Grow-only device buffer charged against the context's HBM budget.
-struct DevBuf {
-    void* ptr = nullptr;
-    size_t bytes = 0;
-};
-
-struct ising_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    size_t budget = 0;   // 0 = unlimited
-    size_t used = 0;
-    DevBuf tcut, jobs, work, spins, est_in, est_out;
-    std::vector<uint32_t> h_tcut;
-    std::vector<jz::JobDesc> h_jobs;
-    std::map<std::tuple<int, int, int>, int> threads;   // per-shape CTA size (tuned)
-};
+#include "jz_host.h"
 
 static_assert(sizeof(jz_params) == 64, "jz_params layout is part of the ABI");
 
-namespace {
+namespace jzh {
 
 int ensure(ising_ctx* ctx, DevBuf& b, size_t bytes)
 {
@@ -358,7 +326,9 @@ int run_jobs(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const* 
     return ISING_OK;
 }
 
-}  // namespace
+}  // namespace jzh
+
+using namespace jzh;
 
 extern "C" {
 

@@ -136,12 +136,21 @@ estimator_batch_kernel(const EstJob* __restrict__ jobs, double* __restrict__ out
 
 // ------------------------------------------------------------------ launchers --
 // The attribute is set to the per-CTA maximum (not this plan's size) so that
-// graphs captured for larger plans stay launchable after smaller ones.
+// graphs captured for larger plans stay launchable after smaller ones; the
+// kernel's static shared memory comes out of the same opt-in limit.
 cudaError_t persistent_prepare(size_t smem, int threads, int* blocks_per_sm)
 {
-    cudaError_t e = cudaFuncSetAttribute(persistent_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         227 * 1024);
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, persistent_kernel);
+    if (e != cudaSuccess) return e;
+    const int max_dyn = optin - (int)fa.sharedSizeBytes;
+    if ((long long)smem > max_dyn) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             max_dyn);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, persistent_kernel,
                                                           threads, smem);

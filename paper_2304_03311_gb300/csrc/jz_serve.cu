@@ -1,0 +1,353 @@
+// jz_serve.cu -- continuous-batching server for c-function jobs.
+//
+// One host worker thread owns the device side.  It admits queued jobs in
+// arrival order while a stream slot is free and the job's device memory fits
+// the budget, launches each admitted job on its slot's stream (the job's
+// trajectories, then its estimator, then the copies of the results into
+// pinned host memory), and polls the slots' completion events; a finished slot
+// immediately takes the next queued job, so jobs arriving while others run are
+// overlapped on the device.  Device memory is allocated stream-ordered
+// (cudaMallocAsync / cudaFreeAsync on the slot's stream), so admitting and
+// retiring jobs never synchronises the device.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "jz_host.h"
+
+using namespace jzh;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Job {
+    jz_params p{};
+    size_t need = 0;          // device bytes while running
+    bool done = false;
+    jz_result res{};
+    std::vector<int64_t> work;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    uint64_t job = 0;
+    std::vector<uint32_t> tcut;        // host table build area
+    uint32_t* h_tcut = nullptr;        // pinned staging
+    size_t h_tcut_cap = 0;             // words
+    jz::JobDesc* h_desc = nullptr;     // pinned
+    double* h_est = nullptr;           // pinned, 3 doubles
+    int64_t* h_work = nullptr;         // pinned
+    size_t h_work_cap = 0;             // entries
+};
+
+size_t job_bytes(const jz_params& p)
+{
+    const size_t tcut = (size_t)p.n_step * 8 * p.d * sizeof(uint32_t);
+    return ((tcut + 255) & ~(size_t)255) + 256 + (size_t)p.n_traj * sizeof(int64_t) + 256;
+}
+
+int grow_pinned(void** p, size_t* cap, size_t want, size_t elem)
+{
+    if (want <= *cap) return ISING_OK;
+    if (*p) cudaFreeHost(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (cudaMallocHost(p, want * elem) != cudaSuccess) {
+        cudaGetLastError();
+        return ISING_ERR_NOMEM;
+    }
+    *cap = want;
+    return ISING_OK;
+}
+
+}  // namespace
+
+struct jz_server {
+    ising_ctx* ctx = nullptr;
+    size_t budget = 0, used = 0;
+    std::vector<Slot> slots;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<uint64_t> queue;
+    std::map<uint64_t, std::unique_ptr<Job>> jobs;
+    uint64_t next_id = 1;
+    bool stop = false;
+    std::thread worker;
+    Clock::time_point t0;
+
+    double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+    void run();
+    int launch(Slot& s, Job& j);
+};
+
+// Enqueues one job on its slot's stream.  Called without the lock; the job
+// record is stable (held by unique_ptr) and not touched by other threads
+// while it is running.
+int jz_server::launch(Slot& s, Job& j)
+{
+    const jz_params& p = j.p;
+    const jz::Geom g = make_geom(p.d, p.L, p.L_t);
+    const size_t n_tcut = (size_t)p.n_step * 8 * p.d;
+    int rc;
+    if ((rc = grow_pinned((void**)&s.h_tcut, &s.h_tcut_cap, n_tcut, sizeof(uint32_t))) ||
+        (rc = grow_pinned((void**)&s.h_work, &s.h_work_cap, (size_t)p.n_traj, sizeof(int64_t))))
+        return rc;
+    s.tcut.assign(n_tcut, 0);
+    jz::JobDesc& J = *s.h_desc;
+    std::memset(&J, 0, sizeof J);
+    build_tables(p, J.tb, s.tcut, 0);
+    std::memcpy(s.h_tcut, s.tcut.data(), n_tcut * sizeof(uint32_t));
+    char* d = nullptr;
+    if ((rc = cuda_err(cudaMallocAsync((void**)&d, j.need, s.stream)))) return rc;
+    const size_t tcut_bytes = (n_tcut * sizeof(uint32_t) + 255) & ~(size_t)255;
+    uint32_t* d_tcut = (uint32_t*)d;
+    jz::JobDesc* d_desc = (jz::JobDesc*)(d + tcut_bytes);
+    long long* d_work = (long long*)(d + tcut_bytes + 256);
+    double* d_est = (double*)(d + tcut_bytes + 256 + (size_t)p.n_traj * sizeof(int64_t));
+    J.l = p.l;
+    J.n_step = p.n_step;
+    J.n_sweep = p.n_sweep;
+    J.n_therm = p.n_therm;
+    J.dir = p.direction;
+    J.n_traj = p.n_traj;
+    J.traj0 = p.traj0;
+    J.cta0 = 0;
+    J.tcut = d_tcut;
+    J.w_out = d_work;
+    J.spins_out = nullptr;
+    const jz::PhiloxKeys K = key_schedule(p.seed);
+    const int B = p.n_traj < 32 ? p.n_traj : 32;
+    if ((rc = cuda_err(cudaMemcpyAsync(d_tcut, s.h_tcut, n_tcut * sizeof(uint32_t),
+                                       cudaMemcpyHostToDevice, s.stream))) ||
+        (rc = cuda_err(cudaMemcpyAsync(d_desc, s.h_desc, sizeof(jz::JobDesc),
+                                       cudaMemcpyHostToDevice, s.stream))) ||
+        (rc = cuda_err(jz::launch_traj(p.d, g, K, d_desc, 1, p.n_traj, ctx_threads(ctx, p.d, g),
+                                       s.stream))) ||
+        (rc = cuda_err(jz::launch_estimator(d_work, p.n_traj, p.beta / (double)p.n_step,
+                                            p.direction, B, d_est, s.stream))) ||
+        (rc = cuda_err(cudaMemcpyAsync(s.h_est, d_est, 3 * sizeof(double),
+                                       cudaMemcpyDeviceToHost, s.stream))) ||
+        (rc = cuda_err(cudaMemcpyAsync(s.h_work, d_work, (size_t)p.n_traj * sizeof(int64_t),
+                                       cudaMemcpyDeviceToHost, s.stream)))) {
+        cudaFreeAsync(d, s.stream);
+        return rc;
+    }
+    cudaFreeAsync(d, s.stream);
+    return cuda_err(cudaEventRecord(s.done, s.stream));
+}
+
+void jz_server::run()
+{
+    cudaSetDevice(ctx->device);
+    std::unique_lock<std::mutex> lk(mu);
+    for (;;) {
+        bool any_busy = false;
+        // retire finished jobs
+        for (Slot& s : slots) {
+            if (!s.busy) continue;
+            const cudaError_t e = cudaEventQuery(s.done);
+            if (e == cudaErrorNotReady) {
+                any_busy = true;
+                continue;
+            }
+            Job& j = *jobs[s.job];
+            if (e == cudaSuccess) {
+                j.res.status = ISING_OK;
+                j.res.log_ratio = s.h_est[0];
+                j.res.delta_S2 = s.h_est[1];
+                j.res.delta_S2_err = s.h_est[2];
+                j.work.assign(s.h_work, s.h_work + j.p.n_traj);
+            } else {
+                cudaGetLastError();
+                j.res.status = ISING_ERR_CUDA;
+            }
+            j.res.done_s = now();
+            j.done = true;
+            used -= j.need;
+            s.busy = false;
+            cv_done.notify_all();
+        }
+        // admit in arrival order while a slot and the budget allow
+        while (!queue.empty() && !stop) {
+            Job& j = *jobs[queue.front()];
+            if (j.need > budget) {
+                j.res.status = ISING_ERR_NOMEM;
+                j.res.start_s = j.res.done_s = now();
+                j.done = true;
+                queue.pop_front();
+                cv_done.notify_all();
+                continue;
+            }
+            Slot* free_slot = nullptr;
+            for (Slot& s : slots)
+                if (!s.busy) {
+                    free_slot = &s;
+                    break;
+                }
+            if (!free_slot || used + j.need > budget) break;
+            const uint64_t id = queue.front();
+            queue.pop_front();
+            used += j.need;
+            free_slot->busy = true;
+            free_slot->job = id;
+            j.res.start_s = now();
+            lk.unlock();
+            const int rc = launch(*free_slot, j);
+            lk.lock();
+            if (rc) {
+                cudaStreamSynchronize(free_slot->stream);
+                cudaGetLastError();
+                j.res.status = rc;
+                j.res.done_s = now();
+                j.done = true;
+                used -= j.need;
+                free_slot->busy = false;
+                cv_done.notify_all();
+            } else {
+                any_busy = true;
+            }
+        }
+        if (stop && !any_busy) break;
+        if (any_busy)
+            cv_work.wait_for(lk, std::chrono::microseconds(50));
+        else
+            cv_work.wait(lk, [&] { return stop || !queue.empty(); });
+    }
+}
+
+extern "C" {
+
+int jz_server_create(ising_ctx* ctx, size_t hbm_budget_bytes, int max_inflight, jz_server** out)
+{
+    if (!ctx || !out || hbm_budget_bytes == 0 || max_inflight < 1 || max_inflight > 64)
+        return ISING_ERR_ARG;
+    *out = nullptr;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
+    std::unique_ptr<jz_server> s(new (std::nothrow) jz_server());
+    if (!s) return ISING_ERR_NOMEM;
+    s->ctx = ctx;
+    s->budget = hbm_budget_bytes;
+    s->slots.resize(max_inflight);
+    for (Slot& sl : s->slots) {
+        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMallocHost((void**)&sl.h_desc, sizeof(jz::JobDesc)) != cudaSuccess ||
+            cudaMallocHost((void**)&sl.h_est, 4 * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            for (Slot& t : s->slots) {
+                if (t.stream) cudaStreamDestroy(t.stream);
+                if (t.done) cudaEventDestroy(t.done);
+                if (t.h_desc) cudaFreeHost(t.h_desc);
+                if (t.h_est) cudaFreeHost(t.h_est);
+            }
+            return ISING_ERR_CUDA;
+        }
+    }
+    s->t0 = Clock::now();
+    jz_server* raw = s.release();
+    raw->worker = std::thread([raw] { raw->run(); });
+    *out = raw;
+    return ISING_OK;
+}
+
+int jz_submit(jz_server* s, const jz_params* p, uint64_t* job_id)
+{
+    if (!s || !p || !job_id) return ISING_ERR_ARG;
+    int rc = check_params(p);
+    if (rc) return rc;
+    const jz::Geom g = make_geom(p->d, p->L, p->L_t);
+    if (jz::traj_smem_bytes(g) > jz::kMaxSmemPerCta || threads_for(g) > 512)
+        return ISING_ERR_UNSUPPORTED;
+    std::unique_ptr<Job> j(new (std::nothrow) Job());
+    if (!j) return ISING_ERR_NOMEM;
+    j->p = *p;
+    j->need = job_bytes(*p);
+    j->res.status = ISING_ERR_PENDING;
+    j->res.updates = (long long)p->n_traj * (2LL * p->L_t * g.Ly * p->L) *
+                     ((long long)p->n_therm + (long long)p->n_step * p->n_sweep);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) return ISING_ERR_ARG;
+        const uint64_t id = s->next_id++;
+        j->res.submit_s = s->now();
+        s->jobs[id] = std::move(j);
+        s->queue.push_back(id);
+        *job_id = id;
+    }
+    s->cv_work.notify_one();
+    return ISING_OK;
+}
+
+int jz_poll(jz_server* s, uint64_t job_id, jz_result* out)
+{
+    if (!s || !out) return ISING_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return ISING_ERR_NOT_FOUND;
+    if (!it->second->done) return ISING_ERR_PENDING;
+    *out = it->second->res;
+    return ISING_OK;
+}
+
+int jz_wait(jz_server* s, uint64_t job_id, double timeout_s, jz_result* out)
+{
+    if (!s || !out || !(timeout_s >= 0)) return ISING_ERR_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return ISING_ERR_NOT_FOUND;
+    Job* j = it->second.get();
+    const auto limit = std::chrono::duration<double>(timeout_s);
+    if (!s->cv_done.wait_for(lk, std::chrono::duration_cast<Clock::duration>(limit),
+                             [&] { return j->done; }))
+        return ISING_ERR_TIMEOUT;
+    *out = j->res;
+    return ISING_OK;
+}
+
+int jz_server_work(jz_server* s, uint64_t job_id, int64_t* work_out)
+{
+    if (!s || !work_out) return ISING_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return ISING_ERR_NOT_FOUND;
+    if (!it->second->done) return ISING_ERR_PENDING;
+    if (it->second->res.status != ISING_OK) return it->second->res.status;
+    std::memcpy(work_out, it->second->work.data(), it->second->work.size() * sizeof(int64_t));
+    return ISING_OK;
+}
+
+void jz_server_free(jz_server* s)
+{
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        s->queue.clear();
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    cudaSetDevice(s->ctx->device);
+    for (Slot& t : s->slots) {
+        cudaStreamSynchronize(t.stream);
+        cudaStreamDestroy(t.stream);
+        cudaEventDestroy(t.done);
+        if (t.h_desc) cudaFreeHost(t.h_desc);
+        if (t.h_est) cudaFreeHost(t.h_est);
+        if (t.h_tcut) cudaFreeHost(t.h_tcut);
+        if (t.h_work) cudaFreeHost(t.h_work);
+    }
+    delete s;
+}
+
+}  // extern "C"
