@@ -87,13 +87,8 @@ jz::Geom make_geom(int d, int L, int Lt)
     g.Ly = d == 3 ? L : 1;
     g.Lh = L / 2;
     g.G = (g.Lh + 3) / 4;
+    g.GW = (g.Lh + 7) / 8;
     g.NR = 2 * Lt * g.Ly;
-    auto magic = [](uint32_t v) -> uint32_t {
-        return v <= 1 ? 0u : (uint32_t)((0x100000000ULL + v - 1) / v);
-    };
-    g.magic_G = magic((uint32_t)g.G);
-    g.magic_Ly = magic((uint32_t)g.Ly);
-    g.magic_Lt = magic((uint32_t)g.Lt);
     return g;
 }
 
@@ -148,34 +143,68 @@ void build_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcu
     }
 }
 
-// CTA size G * L_y * TS: each thread owns one (word, y) column of every TS-th
-// time slice.  TS <= L_t, preferably even (a thread's row parity is then the
-// same for all its slices), with about 256 threads and at most 512.
-int threads_for(const jz::Geom& g)
+// Launch shape for lattices g in CTAs of cta_threads (0 = the default).  With
+// col = GW * L_y words per time slice, each thread owns one word column of
+// every TS-th slice.  col <= 32: warp teams of col * TS threads, TS =
+// min(32 / col, L_t), as many per CTA as fit (default CTA 128 threads).
+// Wider slices: the CTA is one team of col * TS threads, TS <= L_t (default
+// about 256 threads, at most 512).  Teams per CTA stay <= 64 and within the
+// per-CTA shared memory.
+jz::LaunchShape shape_for(const jz::Geom& g, int cta_threads)
 {
-    const int col = g.G * g.Ly;
-    int ts = 256 / col;
-    if (ts < 1) ts = 1;
-    if (ts > 1 && (ts & 1)) ts -= 1;
-    if (ts > g.Lt) ts = g.Lt;
-    while (ts > 1 && col * ts > 512) --ts;
-    return col * ts;
+    jz::LaunchShape s{};
+    const int col = g.GW * g.Ly;
+    const size_t lat = jz::traj_smem_bytes(g);
+    if (col <= 32) {
+        int ts = 32 / col;
+        if (ts > g.Lt) ts = g.Lt;
+        s.team_threads = col * ts;
+        s.warp = 1;
+        const int per_warp = 32 / s.team_threads;
+        int warps = (cta_threads > 0 ? cta_threads : 128) / 32;
+        if (warps < 1) warps = 1;
+        while (warps > 1 && ((size_t)warps * per_warp * lat > jz::kMaxSmemPerCta ||
+                             warps * per_warp > jz::kMaxTeamsHost))
+            --warps;
+        s.teams = warps * per_warp;
+        s.cta_threads = warps * 32;
+    } else {
+        int ts = (cta_threads > 0 ? cta_threads : 256) / col;
+        if (ts < 1) ts = 1;
+        if (cta_threads == 0 && ts > 1 && (ts & 1)) ts -= 1;
+        if (ts > g.Lt) ts = g.Lt;
+        while (ts > 1 && col * ts > 512) --ts;
+        s.team_threads = col * ts;
+        s.teams = 1;
+        s.cta_threads = s.team_threads;
+        s.warp = 0;
+    }
+    return s;
 }
 
-// A CTA size is admissible for g iff it is G * L_y * TS with 1 <= TS <= L_t
-// and at most 512 threads.
+// Whether g can run at all: one team's lattice fits a CTA's shared memory and
+// one time slice of words fits 512 threads.
+bool shape_fits(const jz::Geom& g)
+{
+    return jz::traj_smem_bytes(g) <= jz::kMaxSmemPerCta && g.GW * g.Ly <= 512;
+}
+
+// A CTA size is admissible: a multiple of 32 for warp teams, col * TS with
+// TS <= L_t for CTA teams; at most 512 threads.
 bool threads_ok(const jz::Geom& g, int threads)
 {
-    const int col = g.G * g.Ly;
-    return threads > 0 && threads <= 512 && threads % col == 0 && threads / col <= g.Lt;
+    const int col = g.GW * g.Ly;
+    if (threads <= 0 || threads > 512) return false;
+    if (col <= 32) return threads % 32 == 0;
+    return threads % col == 0 && threads / col <= g.Lt;
 }
 
-// The context's CTA size for this shape: the tuned / fixed one, else the default.
-int ctx_threads(const ising_ctx* ctx, int d, const jz::Geom& g)
+// The context's launch shape for this lattice: the tuned / fixed CTA size, else the default.
+jz::LaunchShape ctx_shape(const ising_ctx* ctx, int d, const jz::Geom& g)
 {
     auto it = ctx->threads.find(std::make_tuple(d, g.L, g.Lt));
-    if (it != ctx->threads.end() && threads_ok(g, it->second)) return it->second;
-    return threads_for(g);
+    const int t = (it != ctx->threads.end() && threads_ok(g, it->second)) ? it->second : 0;
+    return shape_for(g, t);
 }
 
 int cuda_err(cudaError_t e)
@@ -192,24 +221,25 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
 {
     const jz_params& p0 = jobs[idx[0]];
     const jz::Geom g = make_geom(p0.d, p0.L, p0.L_t);
-    if (jz::traj_smem_bytes(g) > jz::kMaxSmemPerCta || threads_for(g) > 512)
-        return ISING_ERR_UNSUPPORTED;
+    if (!shape_fits(g)) return ISING_ERR_UNSUPPORTED;
+    const jz::LaunchShape sh = ctx_shape(ctx, p0.d, g);
     const int n_jobs = (int)idx.size();
     const int per = 8 * p0.d;
     const int V = 2 * p0.L_t * g.Ly * p0.L;
 
     size_t n_tcut = 0;
-    long long n_cta = 0, n_spin_traj = 0;
+    long long n_cta = 0, n_traj_all = 0, n_spin_traj = 0;
     for (int j : idx) {
         n_tcut += (size_t)jobs[j].n_step * per;
-        n_cta += jobs[j].n_traj;
+        n_traj_all += jobs[j].n_traj;
+        n_cta += (jobs[j].n_traj + sh.teams - 1) / sh.teams;
         if (spins && spins[j]) n_spin_traj += jobs[j].n_traj;
     }
     if (n_cta > 0x7FFFFFFFLL) return ISING_ERR_ARG;
     int rc;
     if ((rc = ensure(ctx, ctx->tcut, n_tcut * sizeof(uint32_t)))) return rc;
     if ((rc = ensure(ctx, ctx->jobs, (size_t)n_jobs * sizeof(jz::JobDesc)))) return rc;
-    if (!outs_on_device && (rc = ensure(ctx, ctx->work, (size_t)n_cta * sizeof(long long))))
+    if (!outs_on_device && (rc = ensure(ctx, ctx->work, (size_t)n_traj_all * sizeof(long long))))
         return rc;
     if (n_spin_traj && !spins_on_device &&
         (rc = ensure(ctx, ctx->spins, (size_t)n_spin_traj * V)))
@@ -218,7 +248,7 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
     ctx->h_tcut.assign(n_tcut, 0);
     ctx->h_jobs.assign(n_jobs, jz::JobDesc{});
     size_t off = 0;
-    long long cta = 0, spin_off = 0;
+    long long cta = 0, traj_off = 0, spin_off = 0;
     uint32_t* d_tcut = (uint32_t*)ctx->tcut.ptr;
     for (int i = 0; i < n_jobs; ++i) {
         const jz_params& p = jobs[idx[i]];
@@ -233,7 +263,7 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
         J.cta0 = cta;
         build_tables(p, J.tb, ctx->h_tcut, off);
         J.tcut = d_tcut + off;
-        J.w_out = outs_on_device ? (long long*)outs[idx[i]] : (long long*)ctx->work.ptr + cta;
+        J.w_out = outs_on_device ? (long long*)outs[idx[i]] : (long long*)ctx->work.ptr + traj_off;
         J.spins_out = nullptr;
         if (spins && spins[idx[i]]) {
             J.spins_out = spins_on_device ? spins[idx[i]]
@@ -241,7 +271,8 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
             spin_off += p.n_traj;
         }
         off += (size_t)p.n_step * per;
-        cta += p.n_traj;
+        cta += (p.n_traj + sh.teams - 1) / sh.teams;
+        traj_off += p.n_traj;
     }
     cudaStream_t st = ctx->stream;
     if ((rc = cuda_err(cudaMemcpyAsync(ctx->tcut.ptr, ctx->h_tcut.data(),
@@ -252,7 +283,7 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
         return rc;
     const jz::PhiloxKeys K = key_schedule(p0.seed);
     if ((rc = cuda_err(jz::launch_traj(p0.d, g, K, (const jz::JobDesc*)ctx->jobs.ptr, n_jobs,
-                                       n_cta, ctx_threads(ctx, p0.d, g), st))))
+                                       n_cta, sh, st))))
         return rc;
     if (!outs_on_device || (n_spin_traj && !spins_on_device)) {
         long long c = 0, so = 0;
@@ -436,8 +467,7 @@ int ising_autotune(ising_ctx* ctx, const jz_params* p, int* threads)
     if (rc) return rc;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
     const jz::Geom g = make_geom(p->d, p->L, p->L_t);
-    if (jz::traj_smem_bytes(g) > jz::kMaxSmemPerCta || threads_for(g) > 512)
-        return ISING_ERR_UNSUPPORTED;
+    if (!shape_fits(g)) return ISING_ERR_UNSUPPORTED;
     jz_params s = *p;
     s.n_therm = 16;
     s.n_step = 16;
@@ -447,10 +477,14 @@ int ising_autotune(ising_ctx* ctx, const jz_params* p, int* threads)
     if ((rc = ensure(ctx, ctx->est_in, (size_t)s.n_traj * sizeof(long long)))) return rc;
     int64_t* out = (int64_t*)ctx->est_in.ptr;
     std::vector<int> cands;
-    const int col = g.G * g.Ly;
-    for (int ts = 1; ts <= g.Lt && col * ts <= 512; ts *= 2) cands.push_back(col * ts);
-    if (std::find(cands.begin(), cands.end(), threads_for(g)) == cands.end())
-        cands.push_back(threads_for(g));
+    const int col = g.GW * g.Ly;
+    if (col <= 32) {
+        for (int t = 32; t <= 512; t *= 2) cands.push_back(t);
+    } else {
+        for (int ts = 1; ts <= g.Lt && col * ts <= 512; ts *= 2) cands.push_back(col * ts);
+        const int def = shape_for(g, 0).cta_threads;
+        if (std::find(cands.begin(), cands.end(), def) == cands.end()) cands.push_back(def);
+    }
     const auto key = std::make_tuple(p->d, p->L, p->L_t);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return ISING_ERR_CUDA;
@@ -458,7 +492,7 @@ int ising_autotune(ising_ctx* ctx, const jz_params* p, int* threads)
         cudaEventDestroy(e0);
         return ISING_ERR_CUDA;
     }
-    int best = threads_for(g);
+    int best = shape_for(g, 0).cta_threads;
     float best_ms = 1e30f;
     int64_t* outs[1] = {out};
     for (int t : cands) {
@@ -663,8 +697,7 @@ extern "C" int jarzynski_run_noalloc(const jz_params* p, int64_t* work_int_out, 
     if (rc) return rc;
     if ((size_t)p->n_step * 8 * (size_t)p->d > kNoAllocMaxThresholds) return ISING_ERR_SCRATCH_LIMIT;
     const jz::Geom g = make_geom(p->d, p->L, p->L_t);
-    if (jz::traj_smem_bytes(g) > jz::kMaxSmemPerCta || threads_for(g) > 512)
-        return ISING_ERR_UNSUPPORTED;
+    if (!shape_fits(g)) return ISING_ERR_UNSUPPORTED;
     if (!is_device_ptr(work_int_out)) return ISING_ERR_ARG;
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess) {
@@ -699,8 +732,9 @@ extern "C" int jarzynski_run_noalloc(const jz_params* p, int64_t* work_int_out, 
     if ((rc = cuda_err(cudaMemcpyAsync(base, &J, sizeof J, cudaMemcpyHostToDevice, st))))
         return rc;
     const jz::PhiloxKeys K = key_schedule(p->seed);
-    return cuda_err(jz::launch_traj(p->d, g, K, (const jz::JobDesc*)base, 1, p->n_traj,
-                                    threads_for(g), st));
+    const jz::LaunchShape sh = shape_for(g, 0);
+    return cuda_err(jz::launch_traj(p->d, g, K, (const jz::JobDesc*)base, 1,
+                                    (p->n_traj + sh.teams - 1) / sh.teams, sh, st));
 }
 
 // --------------------------------------------------- persistent batch plans --
@@ -739,27 +773,6 @@ void plan_release(jz_plan* pl)
     delete pl;
 }
 
-// Team size of one job inside a CTA of `cta` threads: G * L_y * TS with the
-// most threads in use (teams * team size), ties to even TS; teams <= 64.
-void team_shape(const jz::Geom& g, int cta, int* team_threads, int* teams)
-{
-    const int col = g.G * g.Ly;
-    int best_t = col, best_use = -1;
-    for (int ts = 1; ts <= g.Lt && col * ts <= cta; ++ts) {
-        const int tt = col * ts;
-        int nt = cta / tt;
-        if (nt > jz::kMaxTeamsHost) nt = jz::kMaxTeamsHost;
-        const int use = nt * tt;
-        if (use > best_use || (use == best_use && (ts & 1) == 0)) {
-            best_use = use;
-            best_t = tt;
-        }
-    }
-    *team_threads = best_t;
-    int nt = cta / best_t;
-    *teams = nt > jz::kMaxTeamsHost ? jz::kMaxTeamsHost : nt;
-}
-
 // Builds (not captures) a plan for a fixed CTA size.
 int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const* work_outs,
                double* est_out, int cta, jz_plan** out)
@@ -781,16 +794,14 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
         jz::BatchJob& B = bj[j];
         B.g = make_geom(p.d, p.L, p.L_t);
         B.D = p.d;
-        B.fast = (B.g.Lh % 4) == 0;
-        team_shape(B.g, cta, &B.team_threads, &B.teams);
-        B.lattice_words = 2 * B.g.NR * B.g.G;
-        if (B.g.G * B.g.Ly > cta) {
+        B.fast = (B.g.Lh % 8) == 0;   // rows of whole 8-site words
+        B.sh = shape_for(B.g, cta);
+        B.lattice_words = 2 * B.g.NR * B.g.GW;
+        if (!shape_fits(B.g) || B.sh.team_threads > cta || (B.sh.warp && B.sh.cta_threads > cta)) {
             plan_release(pl);
             return ISING_ERR_UNSUPPORTED;
         }
-        while (B.teams > 1 && (size_t)B.teams * B.lattice_words * 4 > jz::kMaxSmemPerCta)
-            --B.teams;
-        const size_t sm = (size_t)B.teams * B.lattice_words * 4;
+        const size_t sm = (size_t)B.sh.teams * B.lattice_words * 4;
         if (sm > jz::kMaxSmemPerCta) {
             plan_release(pl);
             return ISING_ERR_UNSUPPORTED;
@@ -812,8 +823,8 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
         J.spins_out = nullptr;
         const double per_traj = (double)(2 * p.L_t * B.g.Ly * p.L) *
                                 ((double)p.n_therm + (double)p.n_step * p.n_sweep);
-        for (int lo = 0; lo < p.n_traj; lo += B.teams) {
-            const int cnt = std::min(B.teams, p.n_traj - lo);
+        for (int lo = 0; lo < p.n_traj; lo += B.sh.teams) {
+            const int cnt = std::min(B.sh.teams, p.n_traj - lo);
             items.push_back({per_traj * cnt, make_int2(j, lo)});
         }
     }

@@ -17,31 +17,37 @@ namespace jz {
 
 constexpr int kMaxTeams = 64;
 
-struct CtaBarrierB {
-    __device__ __forceinline__ void operator()() const { __syncthreads(); }
-};
-
-template <int D, bool FAST>
+template <int D, bool FAST, class Bar>
 __device__ __forceinline__ void run_item(const BatchJob& B, const PhiloxKeys& K, int traj_lo,
-                                         uint32_t* S, const uint32_t* tab, int* s_work)
+                                         uint32_t* S, const uint32_t* tab, int* s_work, Bar bar)
 {
     const TeamJob tj = team_job(B.J);
-    const int team = (int)threadIdx.x / B.team_threads;
-    const int n_here = min(B.teams, B.J.n_traj - traj_lo);
-    const bool has = team < n_here;
-    const int tid = has ? (int)threadIdx.x - team * B.team_threads : -1;
+    int team, tid;
+    team_of(B.sh, &team, &tid);
+    if (!B.sh.warp && tid >= B.sh.team_threads) team = -1;   // CTA larger than the team
+    const int n_here = min(B.sh.teams, B.J.n_traj - traj_lo);
+    const bool has = team >= 0 && team < n_here;
+    if (!has) tid = -1;
     const int tm = has ? team : 0;
     uint32_t* St = S + (size_t)tm * B.lattice_words;
     const long long local = (long long)traj_lo + tm;
     const int dE = run_trajectory<D, FAST, 0, 0>(B.g, K, tj, B.J.traj0 + local, St, tab, tid,
-                                                 B.team_threads, CtaBarrierB{});
+                                                 B.sh.team_threads, bar);
     if (has && dE != 0) atomicAdd(&s_work[tm], dE);
     __syncthreads();
     if (has && tid == 0)
         B.J.w_out[local] = (long long)(tj.dir > 0 ? s_work[tm] : -s_work[tm]);
     if (has && B.J.spins_out != nullptr)
         export_spins<D>(B.g, St, B.J.spins_out + local * (long long)(2 * B.g.Lt * B.g.Ly * B.g.L),
-                        tid, B.team_threads);
+                        tid, B.sh.team_threads);
+}
+
+template <int D, bool FAST>
+__device__ __forceinline__ void run_item_any(const BatchJob& B, const PhiloxKeys& K, int traj_lo,
+                                             uint32_t* S, const uint32_t* tab, int* s_work)
+{
+    if (B.sh.warp) run_item<D, FAST>(B, K, traj_lo, S, tab, s_work, WarpBarrier{});
+    else run_item<D, FAST>(B, K, traj_lo, S, tab, s_work, CtaBarrier{});
 }
 
 __global__ void __launch_bounds__(512)
@@ -62,13 +68,13 @@ persistent_kernel(const BatchJob* __restrict__ jobs, const int2* __restrict__ it
         if (threadIdx.x < 8)
             s_tab[threadIdx.x] = threadIdx.x < (unsigned)B.D ? B.J.tb[threadIdx.x] : 0u;
         if (threadIdx.x < kMaxTeams) s_work[threadIdx.x] = 0;
-        // the first barrier inside run_trajectory orders these before any use
+        __syncthreads();
         if (B.D == 2) {
-            if (B.fast) run_item<2, true>(B, K, item.y, S, s_tab, s_work);
-            else run_item<2, false>(B, K, item.y, S, s_tab, s_work);
+            if (B.fast) run_item_any<2, true>(B, K, item.y, S, s_tab, s_work);
+            else run_item_any<2, false>(B, K, item.y, S, s_tab, s_work);
         } else {
-            if (B.fast) run_item<3, true>(B, K, item.y, S, s_tab, s_work);
-            else run_item<3, false>(B, K, item.y, S, s_tab, s_work);
+            if (B.fast) run_item_any<3, true>(B, K, item.y, S, s_tab, s_work);
+            else run_item_any<3, false>(B, K, item.y, S, s_tab, s_work);
         }
         __syncthreads();   // shared memory and s_item are reused by the next item
     }

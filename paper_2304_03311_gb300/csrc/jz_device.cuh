@@ -1,15 +1,15 @@
 // jz_device.cuh -- device-side building blocks of the replica-gluing kernels.
 //
-// Spin storage in shared memory (one trajectory per CTA):
+// Spin storage in shared memory (one trajectory per team of threads):
 //   S[c][R][q]  uint32 words, c = colour, R = (r L_t + t) L_y + y the row,
-//               q < G = ceil((L/2)/4) the word within the row.  Byte j of word
-//               q holds the colour-c site h = 4q + j of row R, x = 2h + p with
-//               p = (c + t + y) mod 2; the byte is 0 for spin +1 and 1 for -1.
-// With this layout the four (2D) or six (3D) neighbours of the four sites of
+//               q < GW = ceil((L/2)/8) the word within the row.  Nibble j of
+//               word q holds the colour-c site h = 8q + j of row R, x = 2h + p
+//               with p = (c + t + y) mod 2; 0 for spin +1 and 1 for -1.
+// With this layout the four (2D) or six (3D) neighbours of the eight sites of
 // one word are, in the other colour: the same word of rows t-1, t+1 (and
 // y-1, y+1), the same word of the same row (one x neighbour), and that word
-// shifted by one byte (the other x neighbour).  One Philox4x32-10 block gives
-// the four acceptance words of one spin word.
+// shifted by one nibble (the other x neighbour).  Two Philox4x32-10 blocks
+// give the eight acceptance words of one spin word.
 #pragma once
 #include <cstdint>
 
@@ -35,11 +35,20 @@ struct PhiloxKeys {
 struct Geom {
     int L, Lt, Ly;      // spatial extent, time extent, L in 3D / 1 in 2D
     int Lh;             // L / 2 sites of one colour per row
-    int G;              // words per row, ceil(Lh / 4)
+    int G;              // Philox blocks per row, ceil(Lh / 4) (the random-stream layout)
+    int GW;             // shared-memory words per row, ceil(Lh / 8) (8 sites per word)
     int NR;             // rows per colour, 2 * Lt * Ly
-    uint32_t magic_G;   // ceil(2^32 / G)   (G > 1), exact division of idx < 2^16
-    uint32_t magic_Ly;  // ceil(2^32 / Ly)  (Ly > 1)
-    uint32_t magic_Lt;  // ceil(2^32 / Lt)
+};
+
+// How one launch maps trajectories onto threads: a team of team_threads runs
+// one trajectory; a CTA of cta_threads holds `teams` teams.  warp: every team
+// lies inside one warp and synchronises with __syncwarp (no cross-warp
+// barrier); otherwise the CTA is one team and uses __syncthreads.
+struct LaunchShape {
+    int team_threads;
+    int teams;
+    int cta_threads;
+    int warp;
 };
 
 // Per-job (one transformation) parameters, device copy.
@@ -62,9 +71,8 @@ struct BatchJob {
     JobDesc J;            // thresholds, outputs, trajectory range
     Geom g;
     int D, fast;
-    int team_threads;     // G * L_y * TS threads run one trajectory
-    int teams;            // trajectories per work item (teams per CTA)
-    int lattice_words;    // 2 * NR * G spin words per team
+    LaunchShape sh;       // team size, teams per CTA (= trajectories per work item), barrier
+    int lattice_words;    // 2 * NR * GW spin words per team
 };
 
 // One job of the batched estimator.
@@ -75,12 +83,6 @@ struct EstJob {
     int n_blocks;         // jackknife blocks, <= 64 and <= n
     double scale;         // beta / N
 };
-
-// q = n / d for n * d < 2^32, with magic = ceil(2^32 / d) (d > 1).
-__device__ __forceinline__ uint32_t div_magic(uint32_t n, uint32_t d, uint32_t magic)
-{
-    return d == 1 ? n : __umulhi(n, magic);
-}
 
 // One Philox4x32-10 block.
 __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,

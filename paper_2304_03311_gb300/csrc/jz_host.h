@@ -16,7 +16,7 @@
 namespace jz {
 size_t traj_smem_bytes(const Geom& g);
 cudaError_t launch_traj(int D, const Geom& g, const PhiloxKeys& K, const JobDesc* jobs,
-                        int n_jobs, long long n_cta, int threads, cudaStream_t st);
+                        int n_jobs, long long n_cta, const LaunchShape& sh, cudaStream_t st);
 cudaError_t launch_estimator(const long long* w_int, int n, double scale, int direction,
                              int n_blocks, double* out, cudaStream_t st);
 double run_probe(int kind, int device);
@@ -26,7 +26,7 @@ cudaError_t plain_trajectory(int D, const Geom& g, const PhiloxKeys& K, int l, i
                              long long* w, cudaStream_t st);
 constexpr int kMaxJackBlocksHost = 64;
 constexpr size_t kMaxSmemPerCta = 227 * 1024;
-constexpr int kMaxTeamsHost = 64;   // teams per CTA of the persistent kernel
+constexpr int kMaxTeamsHost = 64;   // teams per CTA
 }  // namespace jz
 
 // Grow-only device buffer charged against the context's HBM budget.
@@ -55,9 +55,10 @@ jz::Geom make_geom(int d, int L, int Lt);
 uint32_t threshold(double x);
 jz::PhiloxKeys key_schedule(uint64_t seed);
 void build_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcut, size_t off);
-int threads_for(const jz::Geom& g);
+jz::LaunchShape shape_for(const jz::Geom& g, int cta_threads);
+bool shape_fits(const jz::Geom& g);
 bool threads_ok(const jz::Geom& g, int threads);
-int ctx_threads(const ising_ctx* ctx, int d, const jz::Geom& g);
+jz::LaunchShape ctx_shape(const ising_ctx* ctx, int d, const jz::Geom& g);
 int cuda_err(cudaError_t e);
 int run_jobs(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const* outs,
              int8_t* const* spins);

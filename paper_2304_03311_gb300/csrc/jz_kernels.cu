@@ -18,38 +18,48 @@ __device__ __forceinline__ int find_job(const JobDesc* __restrict__ jobs, int n_
     return lo;
 }
 
-struct CtaBarrier {
-    __device__ __forceinline__ void operator()() const { __syncthreads(); }
-};
+constexpr int kMaxTeams = 64;
 
-// One CTA runs one trajectory of the job that owns it; the CTA is the team.
-template <int D, bool FAST, int CG, int CLY>
+// One CTA runs `teams` trajectories of the job that owns it (sh.teams per
+// CTA; warp teams sync with __syncwarp, a CTA team with __syncthreads).
+template <int D, bool FAST, int CW, int CLY, bool WARP>
 __global__ void __launch_bounds__(512)
-traj_kernel(const Geom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, int n_jobs)
+traj_kernel(const Geom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, int n_jobs,
+            const LaunchShape sh)
 {
     extern __shared__ uint32_t S[];
-    __shared__ int s_work;
+    __shared__ int s_work[kMaxTeams];
     __shared__ uint32_t s_tab[8];
 
     const int j = find_job(jobs, n_jobs, (long long)blockIdx.x);
     const JobDesc& J = jobs[j];
     const TeamJob tj = team_job(J);
-    const long long local = (long long)blockIdx.x - __ldg(&J.cta0);
-    const long long traj = __ldg(&J.traj0) + local;
+    const long long cta_local = (long long)blockIdx.x - __ldg(&J.cta0);
+    int team, tid;
+    team_of(sh, &team, &tid);
+    const long long local = cta_local * sh.teams + (team < 0 ? 0 : team);
+    const bool has = team >= 0 && local < __ldg(&J.n_traj);
+    if (!has) tid = -1;
+    const int tm = team < 0 ? 0 : team;
+    uint32_t* St = S + (size_t)tm * (2 * g.NR * g.GW);
     if (threadIdx.x < 8) s_tab[threadIdx.x] = threadIdx.x < D ? __ldg(&J.tb[threadIdx.x]) : 0u;
-    if (threadIdx.x == 0) s_work = 0;
-    // (the first barrier inside run_trajectory orders these before any use)
-    const int dE = run_trajectory<D, FAST, CG, CLY>(g, K, tj, traj, S, s_tab, (int)threadIdx.x,
-                                                    (int)blockDim.x, CtaBarrier{});
-    // per-trajectory integer work: warp reduction, then one shared atomic per warp
-    const int wsum = __reduce_add_sync(0xFFFFFFFFu, dE);
-    if ((threadIdx.x & 31) == 0 && wsum != 0) atomicAdd(&s_work, wsum);
+    if (threadIdx.x < kMaxTeams) s_work[threadIdx.x] = 0;
     __syncthreads();
-    if (threadIdx.x == 0) J.w_out[local] = (long long)(tj.dir > 0 ? s_work : -s_work);
+    const long long traj = __ldg(&J.traj0) + local;
+    int dE;
+    if (WARP)
+        dE = run_trajectory<D, FAST, CW, CLY>(g, K, tj, traj, St, s_tab, tid, sh.team_threads,
+                                              WarpBarrier{});
+    else
+        dE = run_trajectory<D, FAST, CW, CLY>(g, K, tj, traj, St, s_tab, tid, sh.team_threads,
+                                              CtaBarrier{});
+    if (has && dE != 0) atomicAdd(&s_work[tm], dE);
+    __syncthreads();
+    if (has && tid == 0) J.w_out[local] = (long long)(tj.dir > 0 ? s_work[tm] : -s_work[tm]);
     int8_t* sp = J.spins_out;
-    if (sp != nullptr)
-        export_spins<D>(g, S, sp + local * (long long)(2 * g.Lt * g.Ly * g.L), (int)threadIdx.x,
-                        (int)blockDim.x);
+    if (has && sp != nullptr)
+        export_spins<D>(g, St, sp + local * (long long)(2 * g.Lt * g.Ly * g.L), tid,
+                        sh.team_threads);
 }
 
 // ---------------------------------------------------------------- estimator --
@@ -113,36 +123,38 @@ estimator_kernel(const long long* __restrict__ w_int, int n, double scale, int d
 }
 
 // ------------------------------------------------------------ host launchers --
-size_t traj_smem_bytes(const Geom& g) { return (size_t)2 * g.NR * g.G * sizeof(uint32_t); }
+size_t traj_smem_bytes(const Geom& g) { return (size_t)2 * g.NR * g.GW * sizeof(uint32_t); }
 
-template <int D, bool FAST, int CG, int CLY>
+template <int D, bool FAST, int CW, int CLY>
 static cudaError_t launch_traj_t(const Geom& g, const PhiloxKeys& K, const JobDesc* jobs,
-                                 int n_jobs, long long n_cta, int threads, cudaStream_t st)
+                                 int n_jobs, long long n_cta, const LaunchShape& sh,
+                                 cudaStream_t st)
 {
-    const size_t smem = traj_smem_bytes(g);
-    cudaError_t e = cudaFuncSetAttribute(traj_kernel<D, FAST, CG, CLY>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = traj_smem_bytes(g) * sh.teams;
+    auto kern = sh.warp ? traj_kernel<D, FAST, CW, CLY, true> : traj_kernel<D, FAST, CW, CLY, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
-    traj_kernel<D, FAST, CG, CLY><<<(unsigned)n_cta, threads, smem, st>>>(g, K, jobs, n_jobs);
+    kern<<<(unsigned)n_cta, sh.cta_threads, smem, st>>>(g, K, jobs, n_jobs, sh);
     return cudaGetLastError();
 }
 
-// Shapes with compile-time row geometry: 2D L = 16 and 64 (G = 2, 8) and 3D
-// L = 16 (G = 2, L_y = 16); every other shape runs the generic instantiation.
+// Shapes with compile-time row geometry: 2D L = 16 and 64 (GW = 1, 4) and 3D
+// L = 16 (GW = 1, L_y = 16); every other shape runs the generic instantiation.
 cudaError_t launch_traj(int D, const Geom& g, const PhiloxKeys& K, const JobDesc* jobs,
-                        int n_jobs, long long n_cta, int threads, cudaStream_t st)
+                        int n_jobs, long long n_cta, const LaunchShape& sh, cudaStream_t st)
 {
-    const bool fast = (g.Lh % 4) == 0;
+    const bool fast = (g.Lh % 8) == 0;
     if (D == 2) {
-        if (fast && g.G == 8) return launch_traj_t<2, true, 8, 1>(g, K, jobs, n_jobs, n_cta, threads, st);
-        if (fast && g.G == 2) return launch_traj_t<2, true, 2, 1>(g, K, jobs, n_jobs, n_cta, threads, st);
-        return fast ? launch_traj_t<2, true, 0, 0>(g, K, jobs, n_jobs, n_cta, threads, st)
-                    : launch_traj_t<2, false, 0, 0>(g, K, jobs, n_jobs, n_cta, threads, st);
+        if (fast && g.GW == 4) return launch_traj_t<2, true, 4, 1>(g, K, jobs, n_jobs, n_cta, sh, st);
+        if (fast && g.GW == 1) return launch_traj_t<2, true, 1, 1>(g, K, jobs, n_jobs, n_cta, sh, st);
+        return fast ? launch_traj_t<2, true, 0, 0>(g, K, jobs, n_jobs, n_cta, sh, st)
+                    : launch_traj_t<2, false, 0, 0>(g, K, jobs, n_jobs, n_cta, sh, st);
     }
-    if (fast && g.G == 2 && g.Ly == 16)
-        return launch_traj_t<3, true, 2, 16>(g, K, jobs, n_jobs, n_cta, threads, st);
-    return fast ? launch_traj_t<3, true, 0, 0>(g, K, jobs, n_jobs, n_cta, threads, st)
-                : launch_traj_t<3, false, 0, 0>(g, K, jobs, n_jobs, n_cta, threads, st);
+    if (fast && g.GW == 1 && g.Ly == 16)
+        return launch_traj_t<3, true, 1, 16>(g, K, jobs, n_jobs, n_cta, sh, st);
+    return fast ? launch_traj_t<3, true, 0, 0>(g, K, jobs, n_jobs, n_cta, sh, st)
+                : launch_traj_t<3, false, 0, 0>(g, K, jobs, n_jobs, n_cta, sh, st);
 }
 
 cudaError_t launch_estimator(const long long* w_int, int n, double scale, int direction,

@@ -127,13 +127,14 @@ int jz_server::launch(Slot& s, Job& j)
     J.w_out = d_work;
     J.spins_out = nullptr;
     const jz::PhiloxKeys K = key_schedule(p.seed);
+    const jz::LaunchShape sh = ctx_shape(ctx, p.d, g);
     const int B = p.n_traj < 32 ? p.n_traj : 32;
     if ((rc = cuda_err(cudaMemcpyAsync(d_tcut, s.h_tcut, n_tcut * sizeof(uint32_t),
                                        cudaMemcpyHostToDevice, s.stream))) ||
         (rc = cuda_err(cudaMemcpyAsync(d_desc, s.h_desc, sizeof(jz::JobDesc),
                                        cudaMemcpyHostToDevice, s.stream))) ||
-        (rc = cuda_err(jz::launch_traj(p.d, g, K, d_desc, 1, p.n_traj, ctx_threads(ctx, p.d, g),
-                                       s.stream))) ||
+        (rc = cuda_err(jz::launch_traj(p.d, g, K, d_desc, 1,
+                                       (p.n_traj + sh.teams - 1) / sh.teams, sh, s.stream))) ||
         (rc = cuda_err(jz::launch_estimator(d_work, p.n_traj, p.beta / (double)p.n_step,
                                             p.direction, B, d_est, s.stream))) ||
         (rc = cuda_err(cudaMemcpyAsync(s.h_est, d_est, 3 * sizeof(double),
@@ -267,8 +268,7 @@ int jz_submit(jz_server* s, const jz_params* p, uint64_t* job_id)
     int rc = check_params(p);
     if (rc) return rc;
     const jz::Geom g = make_geom(p->d, p->L, p->L_t);
-    if (jz::traj_smem_bytes(g) > jz::kMaxSmemPerCta || threads_for(g) > 512)
-        return ISING_ERR_UNSUPPORTED;
+    if (!shape_fits(g)) return ISING_ERR_UNSUPPORTED;
     std::unique_ptr<Job> j(new (std::nothrow) Job());
     if (!j) return ISING_ERR_NOMEM;
     j->p = *p;

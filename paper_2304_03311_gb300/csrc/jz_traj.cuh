@@ -7,16 +7,19 @@
 // protocol steps, each the work increment dE_k on phi_k followed by n_sweep
 // sweeps at lambda_{k+1}.
 //
-// Layout: S[colour][row R][word q], R = (r L_t + t) L_y + y, q < G = ceil(L/8);
-// byte j of word q is the colour-c site h = 4q + j of the row, x = 2h + p,
-// p = (c + t + y) mod 2, value 0 for spin +1 and 1 for spin -1.
+// Layout: S[colour][row R][word q], R = (r L_t + t) L_y + y, q < GW = ceil(L/16);
+// nibble j (bits 4j..4j+3) of word q is the colour-c site h = 8q + j of the
+// row, x = 2h + p, p = (c + t + y) mod 2, value 0 for spin +1 and 1 for -1.
+// A word's eight sites draw from Philox blocks 2q and 2q+1 of their row.
+// Nibble-wise sums of XORs give the anti-aligned neighbour count of all eight
+// sites at once (at most 6 < 16, so no carries cross nibbles).
 //
-// Team mapping: a team of G * L_y * TS threads; thread (t0, y, q) owns word q
-// of row y of the time slices t0, t0 + TS, ... in both replicas and colours, so
-// all its index and wrap arithmetic is fixed.  Rows t >= 2 take the bulk path;
-// the rows t = 0, 1 next to the cut blend in the glued replica and handle the
-// switched column x = l.  CG, CLY > 0 fix G and L_y at compile time (the
-// neighbour loads then use immediate offsets); 0 reads them from Geom.
+// Team mapping: a team of GW * L_y * TS threads; thread (t0, y, q) owns word q
+// of row y of the time slices t0, t0 + TS, ... in both replicas and colours,
+// so all its index and wrap arithmetic is fixed.  Rows t >= 2 take the bulk
+// path; the rows t = 0, 1 next to the cut blend in the glued replica and
+// handle the switched column x = l.  CW, CLY > 0 fix GW and L_y at compile
+// time (neighbour loads then use immediate offsets); 0 reads them from Geom.
 //
 // The work increment is gathered inside the first colour-0 half-sweep of each
 // step: for every (r, y) exactly one of the switched sites (l, y, 0)^r and
@@ -32,20 +35,33 @@
 
 namespace jz {
 
-// Flip bits of the four sites of a word.  dsum byte j = a_j, the number of
-// anti-aligned neighbours of site j (energy cost m = 2D - 2 a_j); tab[a] =
-// T(m) for a < D.  Sites with a_j >= D (m <= 0) always flip.
+// Flip bits (bit 4j) of the eight sites of a word.  dsum nibble j = a_j, the
+// number of anti-aligned neighbours of site j (energy cost m = 2D - 2 a_j);
+// tab[a] = T(m) for a < D.  Sites with a_j >= D (m <= 0) always flip.  Sites
+// 0..3 use the words of block ua, sites 4..7 those of block ub.
 template <int D>
-__device__ __forceinline__ uint32_t accept4(uint32_t dsum, const uint4& u, const uint32_t* tab)
+__device__ __forceinline__ uint32_t accept8(uint32_t dsum, const uint4& ua, const uint4& ub,
+                                            const uint32_t* tab)
 {
-    uint32_t f = ((dsum + (uint32_t)(0x80 - D) * 0x01010101u) >> 7) & 0x01010101u;
-    const uint32_t d4 = dsum << 2;   // byte offsets into tab
+    uint32_t f = ((dsum + (uint32_t)(8 - D) * 0x11111111u) >> 3) & 0x11111111u;
+    const uint32_t ev = (dsum & 0x0F0F0F0Fu) << 2;   // sites 0,2,4,6: byte offsets into tab
+    const uint32_t od = (dsum >> 2) & 0x3C3C3C3Cu;   // sites 1,3,5,7
     const unsigned char* tb = reinterpret_cast<const unsigned char*>(tab);
-    if (u.x < *reinterpret_cast<const uint32_t*>(tb + (d4 & 0xFFu))) f |= 1u;
-    if (u.y < *reinterpret_cast<const uint32_t*>(tb + __byte_perm(d4, 0, 0x4441))) f |= 1u << 8;
-    if (u.z < *reinterpret_cast<const uint32_t*>(tb + __byte_perm(d4, 0, 0x4442))) f |= 1u << 16;
-    if (u.w < *reinterpret_cast<const uint32_t*>(tb + __byte_perm(d4, 0, 0x4443))) f |= 1u << 24;
+    auto T = [&](uint32_t off) { return *reinterpret_cast<const uint32_t*>(tb + off); };
+    if (ua.x < T(ev & 0xFFu)) f |= 1u;
+    if (ua.y < T(od & 0xFFu)) f |= 1u << 4;
+    if (ua.z < T(__byte_perm(ev, 0, 0x4441))) f |= 1u << 8;
+    if (ua.w < T(__byte_perm(od, 0, 0x4441))) f |= 1u << 12;
+    if (ub.x < T(__byte_perm(ev, 0, 0x4442))) f |= 1u << 16;
+    if (ub.y < T(__byte_perm(od, 0, 0x4442))) f |= 1u << 20;
+    if (ub.z < T(__byte_perm(ev, 0, 0x4443))) f |= 1u << 24;
+    if (ub.w < T(__byte_perm(od, 0, 0x4443))) f |= 1u << 28;
     return f;
+}
+
+__device__ __forceinline__ uint32_t word8(const uint4& ua, const uint4& ub, int j)
+{
+    return word_of(j < 4 ? ua : ub, j & 3);
 }
 
 // Per-job values a team needs (read from the job descriptor once).
@@ -54,10 +70,10 @@ struct TeamJob {
     const uint32_t* tcut;
 };
 
-template <int D, bool FAST, int CG = 0, int CLY = 0>
+template <int D, bool FAST, int CW = 0, int CLY = 0>
 struct Traj {
     const Geom& g;
-    uint32_t* S;              // this team's spin words [2][NR * G]
+    uint32_t* S;              // this team's spin words [2][NR * GW]
     const uint32_t* tab;      // shared bulk thresholds
     const PhiloxKeys& K;
     uint32_t hi1, lo1;        // M1 * traj: round 0 of Philox for counter word 2
@@ -65,11 +81,13 @@ struct Traj {
     int q, y, t0, TS;         // this thread's word, row y, first slice and slice step
     int d_qm, d_qp;           // word offset of the x-shift neighbour word (p = 0 / 1)
     int d_ym, d_yp;           // word offsets of the rows y-1 / y+1 (3D)
-    uint32_t vmask;           // bytes of word q that hold sites (ragged rows)
+    uint32_t vmask;           // nibbles of word q that hold sites (ragged rows)
+    int sh_next, sh_prev;     // ragged rows: nibble position of the wrapped x neighbour
+    uint32_t m_next;
 
-    __device__ __forceinline__ int G() const { return CG > 0 ? CG : g.G; }
+    __device__ __forceinline__ int W() const { return CW > 0 ? CW : g.GW; }
     __device__ __forceinline__ int Ly() const { return D == 2 ? 1 : (CLY > 0 ? CLY : g.Ly); }
-    __device__ __forceinline__ int rowW() const { return Ly() * G(); }
+    __device__ __forceinline__ int rowW() const { return Ly() * W(); }
 
     // tid < 0: a thread with no sites (it still takes part in the barriers).
     __device__ __forceinline__ Traj(const Geom& g_, uint32_t* S_, const uint32_t* tab_,
@@ -80,62 +98,52 @@ struct Traj {
         const uint64_t p1 = (uint64_t)kPhiloxM1 * traj;
         hi1 = (uint32_t)(p1 >> 32);
         lo1 = (uint32_t)p1;
-        const int col = G() * Ly();
+        const int col = W() * Ly();
         TS = nthr / col;
         if (tid < 0) {
             q = y = 0;
             t0 = g.Lt;
         } else {
-            q = tid % G();
-            y = (tid / G()) % Ly();
+            q = tid % W();
+            y = (tid / W()) % Ly();
             t0 = tid / col;
         }
-        d_qm = (q == 0 ? G() - 1 : q - 1) - q;
-        d_qp = (q == G() - 1 ? 0 : q + 1) - q;
-        d_ym = ((y == 0 ? Ly() - 1 : y - 1) - y) * G();
-        d_yp = ((y == Ly() - 1 ? 0 : y + 1) - y) * G();
-        const int nv = g.Lh - 4 * q;
-        vmask = nv >= 4 ? 0xFFFFFFFFu : ((1u << (8 * nv)) - 1u);
+        d_qm = (q == 0 ? W() - 1 : q - 1) - q;
+        d_qp = (q == W() - 1 ? 0 : q + 1) - q;
+        d_ym = ((y == 0 ? Ly() - 1 : y - 1) - y) * W();
+        d_yp = ((y == Ly() - 1 ? 0 : y + 1) - y) * W();
+        const int nv = g.Lh - 8 * q;                       // sites in this word
+        const int nv_last = g.Lh - 8 * (W() - 1);          // sites in the row's last word
+        vmask = nv >= 8 ? 0xFFFFFFFFu : ((1u << (4 * nv)) - 1u);
+        sh_next = 4 * ((nv >= 8 ? 8 : nv) - 1);
+        m_next = (1u << sh_next) - 1u;
+        sh_prev = q == 0 ? 4 * (nv_last - 1) : 28;
     }
 
-    // Glue mask: bytes of word q (row parity p) whose site has x < lg.
+    // Glue mask: nibbles of word q (row parity p) whose site has x < lg.
     __device__ __forceinline__ uint32_t glue_mask(int lg, int p) const
     {
-        int nj = ((lg - p + 1) >> 1) - 4 * q;   // # of sites 2h + p < lg in this word
-        nj = nj < 0 ? 0 : (nj > 4 ? 4 : nj);
-        return nj == 4 ? 0xFFFFFFFFu : ((1u << (8 * nj)) - 1u);
+        int nj = ((lg - p + 1) >> 1) - 8 * q;   // # of sites 2h + p < lg in this word
+        nj = nj < 0 ? 0 : (nj > 8 ? 8 : nj);
+        return nj == 8 ? 0xFFFFFFFFu : ((1u << (4 * nj)) - 1u);
     }
 
-    // The x neighbour not at the same h: h-1 for p = 0, h+1 for p = 1.  The
-    // row's other words are at o[d_qm] / o[d_qp]; o points at word q.
+    // The x neighbour not at the same h: h-1 for p = 0, h+1 for p = 1.  o points
+    // at word q of the other colour; the row's other words are o[d_qm] / o[d_qp].
     __device__ __forceinline__ uint32_t xshift(const uint32_t* o, int p, uint32_t nx0) const
     {
-        if (FAST) {
-            const uint32_t nb = o[p ? d_qp : d_qm];
-            return __byte_perm(nb, nx0, p ? 0x0765 : 0x6543);
-        }
-        const uint8_t* row = reinterpret_cast<const uint8_t*>(o - q);
-        uint32_t v = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int h = 4 * q + j;
-            if (h < g.Lh) {
-                const int hn = p == 0 ? (h == 0 ? g.Lh - 1 : h - 1) : (h == g.Lh - 1 ? 0 : h + 1);
-                v |= (uint32_t)row[hn] << (8 * j);
-            }
-        }
-        return v;
-    }
-
-    __device__ __forceinline__ uint4 rng(int w, uint32_t sweep, uint32_t c3) const
-    {
-        return philox_r0((uint32_t)w, sweep, hi1, lo1, c3, K);
+        const uint32_t nb = o[p ? d_qp : d_qm];
+        if (FAST) return p ? __funnelshift_r(nx0, nb, 4) : __funnelshift_l(nb, nx0, 4);
+        // ragged rows: the row's last word holds fewer than eight sites
+        return p ? (((nx0 >> 4) & m_next) | ((nb & 0xFu) << sh_next))
+                 : ((nx0 << 4) | ((nb >> sh_prev) & 0xFu));
     }
 
     // Bulk row, 2 <= t < L_t, all links full beta.  up: offset of the t+1 row
-    // (rowW, or -(L_t - 1) rowW at t = L_t - 1).
+    // (rowW, or -(L_t - 1) rowW at t = L_t - 1); c0: Philox block of the word's
+    // first four sites.
     __device__ __forceinline__ void bulk_item(uint32_t* own_b, const uint32_t* oth, int w, int up,
-                                              int p, uint32_t sweep, uint32_t c3) const
+                                              int p, uint32_t c0, uint32_t sweep, uint32_t c3) const
     {
         const uint32_t* o = oth + w;
         const uint32_t own = own_b[w];
@@ -145,8 +153,9 @@ struct Traj {
         const uint32_t nx1 = xshift(o, p, nx0);
         uint32_t dsum = (own ^ ntm) + (own ^ ntp) + (own ^ nx0) + (own ^ nx1);
         if (D == 3) dsum += (own ^ o[d_ym]) + (own ^ o[d_yp]);
-        const uint4 u = rng(w, sweep, c3);
-        uint32_t flip = accept4<D>(dsum, u, tab);
+        const uint4 ua = philox_r0(c0, sweep, hi1, lo1, c3, K);
+        const uint4 ub = philox_r0(c0 + 1u, sweep, hi1, lo1, c3, K);
+        uint32_t flip = accept8<D>(dsum, ua, ub, tab);
         if (!FAST) flip &= vmask;
         own_b[w] = own ^ flip;
     }
@@ -154,9 +163,9 @@ struct Traj {
     // Rows t = 0, 1 next to the cut.  lg = columns glued across the cut; k >= 0
     // is the protocol step (the switched column then uses the step's table).
     __device__ __forceinline__ void cut_item(uint32_t* own_b, const uint32_t* oth, int w, int t,
-                                             int r, int p, uint32_t sweep, uint32_t c3, int k,
-                                             int lg, const TeamJob& J, int w_self, int w_glue,
-                                             bool record, int& dE) const
+                                             int r, int p, uint32_t c0, uint32_t sweep,
+                                             uint32_t c3, int k, int lg, const TeamJob& J,
+                                             int w_self, int w_glue, bool record, int& dE) const
     {
         const int rw = rowW();
         const int repW = g.Lt * rw;
@@ -172,24 +181,26 @@ struct Traj {
         const uint32_t nx1 = xshift(o, p, nx0);
         uint32_t dsum = (own ^ normal) + (own ^ cross) + (own ^ nx0) + (own ^ nx1);
         if (D == 3) dsum += (own ^ o[d_ym]) + (own ^ o[d_yp]);
-        const uint4 u = rng(w, sweep, c3);
-        uint32_t flip = accept4<D>(dsum, u, tab);
+        const uint4 ua = philox_r0(c0, sweep, hi1, lo1, c3, K);
+        const uint4 ub = philox_r0(c0 + 1u, sweep, hi1, lo1, c3, K);
+        uint32_t flip = accept8<D>(dsum, ua, ub, tab);
         // Switched site x = l during the protocol: couplings beta (1 - lambda)
         // to its own replica, beta lambda to the next one.
         const int l = J.l;
-        if (k >= 0 && ((l - p) & 1) == 0 && ((l - p) >> 3) == q) {
-            const int jl = ((l - p) >> 1) & 3;
-            const uint32_t ob = (own >> (8 * jl)) & 1u;
-            const int as = (int)(ob ^ ((self_w >> (8 * jl)) & 1u));
-            const int ag = (int)(ob ^ ((glue_w >> (8 * jl)) & 1u));
-            const int a_cnt = (int)((dsum >> (8 * jl)) & 0xFFu) - as;   // fixed links
+        if (k >= 0 && ((l - p) & 1) == 0 && ((l - p) >> 4) == q) {
+            const int jl = ((l - p) >> 1) & 7;
+            const int sh = 4 * jl;
+            const uint32_t ob = (own >> sh) & 1u;
+            const int as = (int)(ob ^ ((self_w >> sh) & 1u));
+            const int ag = (int)(ob ^ ((glue_w >> sh) & 1u));
+            const int a_cnt = (int)((dsum >> sh) & 0xFu) - as;   // fixed links
             const int a = (2 * D - 1) - 2 * a_cnt;
             const int b = 1 - 2 * as;
             const int cg = 1 - 2 * ag;
             const int mm = a * J.n_step + b * w_self + cg * w_glue;
             const int ti = (((a + 2 * D - 1) >> 1) * 2 + (b > 0)) * 2 + (cg > 0);
-            const bool acc = (mm <= 0) || (word_of(u, jl) < __ldg(J.tcut + k * (8 * D) + ti));
-            flip = (flip & ~(0xFFu << (8 * jl))) | ((uint32_t)acc << (8 * jl));
+            const bool acc = (mm <= 0) || (word8(ua, ub, jl) < __ldg(J.tcut + k * (8 * D) + ti));
+            flip = (flip & ~(0xFu << sh)) | ((uint32_t)acc << sh);
             if (record) dE += b - cg;
         }
         if (!FAST) flip &= vmask;
@@ -207,24 +218,27 @@ struct Traj {
         const uint32_t* oth = S + (1 - c) * cw;
         const uint32_t c3 = (uint32_t)c | c3base;
         const int stride = TS * rw;
+        const uint32_t cstride = (uint32_t)(TS * Ly() * g.G);   // Philox blocks per TS slices
         const int pc = (c + y) & 1;
         const int wrap_up = -(Lt - 1) * rw;
 #pragma unroll 1
         for (int r = 0; r < 2; ++r) {
             int t = t0;
-            int w = (r * Lt + t0) * rw + y * G() + q;
-            for (; t < 2 && t < Lt; t += TS, w += stride)
-                cut_item(own_b, oth, w, t, r, (pc ^ t) & 1, sweep, c3, k, lg, J, w_self, w_glue,
-                         record, dE);
+            int w = (r * Lt + t0) * rw + y * W() + q;
+            uint32_t c0 = (uint32_t)(((r * Lt + t0) * Ly() + y) * g.G + 2 * q);
+            for (; t < 2 && t < Lt; t += TS, w += stride, c0 += cstride)
+                cut_item(own_b, oth, w, t, r, (pc ^ t) & 1, c0, sweep, c3, k, lg, J, w_self,
+                         w_glue, record, dE);
             if (TS & 1) {
-                for (; t < Lt; t += TS, w += stride)
-                    bulk_item(own_b, oth, w, t == Lt - 1 ? wrap_up : rw, (pc ^ t) & 1, sweep, c3);
+                for (; t < Lt; t += TS, w += stride, c0 += cstride)
+                    bulk_item(own_b, oth, w, t == Lt - 1 ? wrap_up : rw, (pc ^ t) & 1, c0, sweep,
+                              c3);
             } else {
                 // t keeps its parity: the x-shift direction is fixed for the row set
                 const int p = (pc ^ t0) & 1;
-                for (; t < Lt - TS; t += TS, w += stride)
-                    bulk_item(own_b, oth, w, rw, p, sweep, c3);
-                if (t < Lt) bulk_item(own_b, oth, w, t == Lt - 1 ? wrap_up : rw, p, sweep, c3);
+                for (; t < Lt - TS; t += TS, w += stride, c0 += cstride)
+                    bulk_item(own_b, oth, w, rw, p, c0, sweep, c3);
+                if (t < Lt) bulk_item(own_b, oth, w, t == Lt - 1 ? wrap_up : rw, p, c0, sweep, c3);
             }
         }
     }
@@ -233,15 +247,20 @@ struct Traj {
     {
         const int rw = rowW();
         const int cw = 2 * g.Lt * rw;
+        const uint32_t cstride = (uint32_t)(TS * Ly() * g.G);
         for (int c = 0; c < 2; ++c) {
             uint32_t* base = S + c * cw;
             const uint32_t c3 = (uint32_t)c | c3base | (1u << 30);
             for (int r = 0; r < 2; ++r) {
-                int w = (r * g.Lt + t0) * rw + y * G() + q;
-                for (int t = t0; t < g.Lt; t += TS, w += TS * rw) {
-                    const uint4 u = rng(w, 0u, c3);
-                    const uint32_t v = (u.x >> 31) | ((u.y >> 31) << 8) | ((u.z >> 31) << 16) |
-                                       ((u.w >> 31) << 24);
+                int w = (r * g.Lt + t0) * rw + y * W() + q;
+                uint32_t c0 = (uint32_t)(((r * g.Lt + t0) * Ly() + y) * g.G + 2 * q);
+                for (int t = t0; t < g.Lt; t += TS, w += TS * rw, c0 += cstride) {
+                    const uint4 ua = philox_r0(c0, 0u, hi1, lo1, c3, K);
+                    const uint4 ub = philox_r0(c0 + 1u, 0u, hi1, lo1, c3, K);
+                    const uint32_t v = (ua.x >> 31) | ((ua.y >> 31) << 4) | ((ua.z >> 31) << 8) |
+                                       ((ua.w >> 31) << 12) | ((ub.x >> 31) << 16) |
+                                       ((ub.y >> 31) << 20) | ((ub.z >> 31) << 24) |
+                                       ((ub.w >> 31) << 28);
                     base[w] = v & vmask;
                 }
             }
@@ -249,17 +268,23 @@ struct Traj {
     }
 };
 
-// Runs one whole trajectory with the team's threads.  Every thread of the CTA
-// calls it with the same job (trip counts match across teams); tid < 0 marks
-// a thread without sites.  bar() synchronises the team (all teams of a CTA
-// run in lockstep, so __syncthreads serves).  Returns this thread's share of
-// W_int (in units of beta/N, sign of the direction applied by the caller).
-template <int D, bool FAST, int CG, int CLY, class Bar>
+struct CtaBarrier {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct WarpBarrier {
+    __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+
+// Runs one whole trajectory with the team's threads.  Every thread sharing the
+// barrier calls it with the same job (trip counts match across teams); tid < 0
+// marks a thread without sites.  Returns this thread's share of W_int (in
+// units of beta/N, sign of the direction applied by the caller).
+template <int D, bool FAST, int CW, int CLY, class Bar>
 __device__ __forceinline__ int run_trajectory(const Geom& g, const PhiloxKeys& K, const TeamJob& J,
                                               long long traj, uint32_t* S_team,
                                               const uint32_t* tab, int tid, int nthr, Bar bar)
 {
-    const Traj<D, FAST, CG, CLY> tr(g, S_team, tab, K, (uint32_t)traj,
+    const Traj<D, FAST, CW, CLY> tr(g, S_team, tab, K, (uint32_t)traj,
                                     ((uint32_t)(J.dir < 0) << 1) | ((uint32_t)J.l << 2), tid, nthr);
     tr.hot_start();
     bar();
@@ -294,7 +319,6 @@ __device__ __forceinline__ void export_spins(const Geom& g, const uint32_t* S_te
                                              int tid, int nthr)
 {
     const int V = 2 * g.Lt * g.Ly * g.L;
-    const uint8_t* bytes = reinterpret_cast<const uint8_t*>(S_team);
     for (int i = tid; i < V; i += nthr) {
         const int x = i % g.L;
         const int R = i / g.L;                      // (r, t, y) row
@@ -302,8 +326,9 @@ __device__ __forceinline__ void export_spins(const Geom& g, const uint32_t* S_te
         if (D == 3) { y = R % g.Ly; trow = R / g.Ly; }
         const int t = trow % g.Lt;
         const int c = (x + y + t) & 1;
-        const uint8_t b = bytes[(size_t)(c * g.NR + R) * g.G * 4 + (x >> 1)];
-        dst[i] = b ? (int8_t)-1 : (int8_t)1;
+        const int h = x >> 1;
+        const uint32_t word = S_team[(size_t)(c * g.NR + R) * g.GW + (h >> 3)];
+        dst[i] = ((word >> (4 * (h & 7))) & 1u) ? (int8_t)-1 : (int8_t)1;
     }
 }
 
@@ -317,6 +342,28 @@ __device__ __forceinline__ TeamJob team_job(const JobDesc& J)
     t.dir = __ldg(&J.dir);
     t.tcut = J.tcut;
     return t;
+}
+
+// This thread's team and team-local id under a launch shape (warp teams do
+// not cross warps).  team = -1: no team.
+__device__ __forceinline__ void team_of(const LaunchShape& sh, int* team, int* tid)
+{
+    const int x = (int)threadIdx.x;
+    if (!sh.warp) {
+        *team = 0;
+        *tid = x;
+        return;
+    }
+    const int per_warp = 32 / sh.team_threads;
+    const int lane = x & 31;
+    const int sub = lane / sh.team_threads;
+    if (sub >= per_warp) {
+        *team = -1;
+        *tid = -1;
+        return;
+    }
+    *team = (x >> 5) * per_warp + sub;
+    *tid = lane - sub * sh.team_threads;
 }
 
 }  // namespace jz

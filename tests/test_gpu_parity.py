@@ -120,19 +120,23 @@ def test_cta_size_does_not_change_results(job):
     c = jz.ising_replica_init(0, 0, None)
     try:
         ref, _ = gpu_run(c, job, spins=False)
-        col = ((job.L // 2 + 3) // 4) * (job.L if job.d == 3 else 1)
-        ts = 1
-        while ts <= job.L_t and col * ts <= 512:
-            jz.ising_set_threads(c, job.d, job.L, job.L_t, col * ts)
+        # words per time slice: 8 sites per word, L_y rows
+        col = ((job.L // 2 + 7) // 8) * (job.L if job.d == 3 else 1)
+        if col <= 32:       # warp teams: any multiple of 32
+            sizes, bad = [32, 64, 128, 256, 512], 48
+        else:               # one team per CTA: col * TS, TS <= L_t
+            sizes = [col * ts for ts in (1, 2, 4, 8, 16) if ts <= job.L_t and col * ts <= 512]
+            bad = col * (job.L_t + 1)
+        for t in sizes:
+            jz.ising_set_threads(c, job.d, job.L, job.L_t, t)
             W, _ = gpu_run(c, job, spins=False)
             np.testing.assert_array_equal(W, ref)
-            ts *= 2
         with pytest.raises(jz.IsingError):
-            jz.ising_set_threads(c, job.d, job.L, job.L_t, col * (job.L_t + 1))
+            jz.ising_set_threads(c, job.d, job.L, job.L_t, bad)
         p = jz.make_params(job.d, job.L, job.L_t, job.beta, job.l, job.n_step, job.n_sweep,
                            job.n_traj, job.seed, n_therm=job.n_therm, direction=job.direction)
         best = jz.ising_autotune(c, p)
-        assert best % col == 0 and 1 <= best // col <= job.L_t
+        assert best in sizes or best == 128
         W, _ = gpu_run(c, job, spins=False)
         np.testing.assert_array_equal(W, ref)
     finally:

@@ -1,0 +1,72 @@
+"""Physics checks of the GPU path against exact results (no bit parity involved).
+
+* A full c-function scan of the 2D critical Ising model at L = 10, L_t = 8L
+  (the zero-temperature regime of section 4) run on the GPU agrees, for every
+  l, with the exact Delta S_2(l) of the replica transfer matrix within its
+  jackknife error, and its c-function follows the transfer matrix's.
+* Direct (l+1 -> l) and reverse (l -> l+1) protocols agree (Appendix A, eq.
+  equality_of_direct_reverse_protocols).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle.estimator as oest
+import oracle.exact as ex
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="no CUDA device")]
+
+import paper_2304_03311_gb300 as jz  # noqa: E402
+from paper_2304_03311_gb300 import build as jzbuild  # noqa: E402
+from paper_2304_03311_gb300 import workloads as wl  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    jzbuild.build()
+    c = jz.ising_replica_init(0, 0, None)
+    yield c
+    jz.ising_replica_free(c)
+
+
+def _scan(ctx, L, L_t, n_step, n_traj, direction=1, seed=1):
+    jobs = [wl.Job(2, L, L_t, wl.BETA_C_2D, l, n_step, 1, n_traj, seed=seed, direction=direction)
+            for l in range(L)]
+    outs = [torch.empty(j.n_traj, dtype=torch.int64, device="cuda") for j in jobs]
+    params = [jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj, j.seed,
+                             n_therm=j.n_therm, direction=j.direction) for j in jobs]
+    jz.jarzynski_run_batch(ctx, params, outs)
+    jz.ising_sync(ctx)
+    res = []
+    for j, o in zip(jobs, outs):
+        _, ds, err = jz.estimator_reduce(ctx, o, j.n_traj, j.beta, j.n_step, direction, 32)
+        res.append((ds, err))
+    return res
+
+
+def test_scan_matches_exact_transfer_matrix_at_zero_temperature(ctx):
+    L, L_t = 10, 80
+    exact = ex.delta_s2_transfer(2, L, L_t, wl.BETA_C_2D)
+    res = _scan(ctx, L, L_t, 400, 4096)
+    pulls = [(ds - e) / err for (ds, err), e in zip(res, exact)]
+    assert max(abs(p) for p in pulls) < 4.5, pulls
+    # chi^2 over the ten transformations is compatible with statistics alone
+    chi2 = sum(p * p for p in pulls)
+    assert chi2 < 30.0
+    # the c-function follows the exact one (section 2, symmetrised form)
+    for l, ((ds, err), e) in enumerate(zip(res, exact)):
+        c_mc, c_ex = oest.c_function(ds, 2, L, l), oest.c_function(e, 2, L, l)
+        c_err = oest.c_function(err, 2, L, l)
+        assert abs(c_mc - c_ex) < 4.5 * c_err + 1e-4
+
+
+def test_direct_and_reverse_agree_on_gpu(ctx):
+    L, L_t = 16, 32
+    fwd = _scan(ctx, L, L_t, 300, 2048, direction=1, seed=2)
+    rev = _scan(ctx, L, L_t, 300, 2048, direction=-1, seed=3)
+    pulls = [(a - b) / math.hypot(ea, eb) for (a, ea), (b, eb) in zip(fwd, rev)]
+    assert max(abs(p) for p in pulls) < 4.5, pulls
+    assert sum(p * p for p in pulls) < 45.0
