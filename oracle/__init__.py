@@ -83,6 +83,14 @@ def _declare(lib):
                                          ctypes.c_int]
     lib.oracle_max_threads.restype = ctypes.c_int
     lib.oracle_max_threads.argtypes = []
+    lib.oracle_run_update.restype = ctypes.c_int
+    lib.oracle_run_update.argtypes = [
+        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+        ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_longlong, ctypes.c_int,
+        ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.oracle_bond_threshold.restype = ctypes.c_uint32
+    lib.oracle_bond_threshold.argtypes = [ctypes.c_double]
 
 
 def philox4x32_10(ctr, key):
@@ -107,10 +115,16 @@ def max_threads() -> int:
     return int(_load().oracle_max_threads())
 
 
+def bond_threshold(x: float) -> int:
+    """Swendsen-Wang bond threshold floor(2^32 (1 - e^-x)), x = 2K."""
+    return int(_load().oracle_bond_threshold(x))
+
+
 def run(d, L, L_t, beta, l, n_step, n_sweep, n_traj, seed, *, n_therm=1000,
-        direction=1, traj0=0, n_threads=0, want_spins=False, lib=None):
+        direction=1, traj0=0, n_threads=0, want_spins=False, lib=None, update=0):
     """Run trajectories traj0..traj0+n_traj-1 of the transformation l -> l+1
-    (direction=+1) or l+1 -> l (direction=-1).
+    (direction=+1) or l+1 -> l (direction=-1); update 0 = checkerboard
+    Metropolis, 1 = Swendsen-Wang clusters.
 
     Returns (W_int int64[n_traj], spins int8[n_traj, 2, L_t, L_y, L] or None).
     Follows section 3 (replica geometry and linear protocol) and Appendix A
@@ -120,11 +134,11 @@ def run(d, L, L_t, beta, l, n_step, n_sweep, n_traj, seed, *, n_therm=1000,
     work = np.zeros(n_traj, dtype=np.int64)
     L_y = L if d == 3 else 1
     spins = np.zeros((n_traj, 2, L_t, L_y, L), dtype=np.int8) if want_spins else None
-    rc = lib.oracle_run(int(d), int(L), int(L_t), float(beta), int(l), int(n_step),
-                        int(n_sweep), int(n_therm), int(direction),
-                        int(seed) & 0xFFFFFFFFFFFFFFFF, int(traj0), int(n_traj),
-                        int(n_threads), work.ctypes.data,
-                        spins.ctypes.data if spins is not None else None)
+    rc = lib.oracle_run_update(int(d), int(L), int(L_t), float(beta), int(l), int(n_step),
+                               int(n_sweep), int(n_therm), int(direction), int(update),
+                               int(seed) & 0xFFFFFFFFFFFFFFFF, int(traj0), int(n_traj),
+                               int(n_threads), work.ctypes.data,
+                               spins.ctypes.data if spins is not None else None)
     if rc != 0:
         raise ValueError("oracle_run rejected its arguments")
     return work, spins

@@ -22,6 +22,7 @@ import math
 from dataclasses import dataclass
 
 import numpy as np
+from scipy import sparse
 
 N_REPLICA = 2
 
@@ -361,4 +362,143 @@ def exact_path_measure(d, L, L_t, l, beta, n_step, n_sweep, n_therm, *, directio
         F = G
         for _ in range(n_sweep):
             F = dyn.sweep(F, k)
+    return np.arange(-wmax, wmax + 1), F
+
+
+# ----------------------------------------------- exact Swendsen-Wang kernel --
+def _bond_prob(x: float, quantised: bool) -> float:
+    """Swendsen-Wang bond probability 1 - e^{-x} (x = 2K) between equal spins;
+    quantised: floor(2^32 (1 - e^{-x})) / 2^32, saturated at 1 - 2^-32."""
+    if quantised:
+        return min(int(math.floor(math.ldexp(-math.expm1(-x), 32))), 2 ** 32 - 1) / 2.0 ** 32
+    return -math.expm1(-x)
+
+
+class _SWDynamics:
+    """Exact Swendsen-Wang transition matrices of a tiny replica lattice
+    (Swendsen and Wang 1987, the update of the paper's GPU code, section 3):
+    every link of coupling K between equal spins is a bond with probability
+    1 - e^{-2K}; each cluster of bonded sites flips with probability 1/2.
+    T[s, s'] = sum over bond sets B of P(B | s) 2^{-nc(B)} [s' = s with some
+    clusters of B flipped], computed by enumerating all bond sets."""
+
+    def __init__(self, d, L, L_t, l, beta, n_step, direction, quantised):
+        self.beta, self.N, self.dir, self.quantised = beta, n_step, direction, quantised
+        self.links = replica_links(d, L, L_t, l)
+        self.V = self.links.n_sites
+        if self.V > 10:
+            raise ValueError("exact Swendsen-Wang kernel needs V <= 10")
+        lk = self.links
+        self.pairs = np.concatenate([lk.full, lk.self_, lk.glue])
+        self.kind = np.array([0] * len(lk.full) + [1] * len(lk.self_) + [2] * len(lk.glue))
+        self.sigma = _spins_of_states(self.V).astype(np.int64)
+        self.aligned = (self.sigma[:, self.pairs[:, 0]] == self.sigma[:, self.pairs[:, 1]])
+        self._cache = {}
+
+    def _x(self, kind, k):
+        """x = 2K of a link class at protocol step k (None: thermalisation)."""
+        b = self.beta
+        if kind == 0:
+            return 2.0 * b
+        if k is None:   # start geometry: forward self-linked, reverse glued
+            full = (kind == 1) == (self.dir > 0)
+            return 2.0 * b if full else 0.0
+        kp = k + 1
+        w_self = self.N - kp if self.dir > 0 else kp
+        w_glue = kp if self.dir > 0 else self.N - kp
+        w = w_self if kind == 1 else w_glue
+        return (2.0 * b * float(w)) / float(self.N)
+
+    def kernel(self, k):
+        if k in self._cache:
+            return self._cache[k]
+        p = np.array([_bond_prob(self._x(kd, k), self.quantised) for kd in self.kind])
+        live = np.nonzero(p > 0)[0]
+        pairs, pl = self.pairs[live], p[live]
+        nl, n_states, V = len(live), 1 << self.V, self.V
+        aligned = self.aligned[:, live]
+        # every bond set B of the live links: membership and cluster labels
+        # (label = smallest site index of the component, by V rounds of min
+        # propagation along the bonds of B)
+        subsets = np.arange(1 << nl, dtype=np.int64)
+        inB = ((subsets[:, None] >> np.arange(nl)[None, :]) & 1).astype(bool)
+        lab = np.tile(np.arange(V), (1 << nl, 1))
+        for _ in range(V):
+            for e in range(nl):
+                i, j = pairs[e]
+                m = np.minimum(lab[:, i], lab[:, j])
+                sel = inB[:, e]
+                lab[sel, i] = m[sel]
+                lab[sel, j] = m[sel]
+        parts, pid = np.unique(lab, axis=0, return_inverse=True)
+        pid = pid.reshape(-1)
+        # P(B | s) = prod_{e in B} [aligned_e(s)] p_e * prod_{e not in B} (1 - [aligned_e(s)] p_e);
+        # W[partition, s] = sum of P(B | s) over the bond sets B with that partition
+        log_p = np.log(pl)
+        log_q = np.log1p(-(aligned * pl[None, :])).T                    # (links, states)
+        unequal = (~aligned).astype(np.float64).T                         # (links, states)
+        W = np.zeros((len(parts), n_states))
+        chunk = 16384
+        for lo in range(0, 1 << nl, chunk):
+            b = inB[lo:lo + chunk].astype(np.float64)
+            prob = np.exp((b @ log_p)[:, None] + (1.0 - b) @ log_q)
+            prob[(b @ unequal) > 0] = 0.0                                 # a bond between unequal spins
+            ind = sparse.csr_matrix((np.ones(len(b)), (pid[lo:lo + chunk], np.arange(len(b)))),
+                                    shape=(len(parts), len(b)))
+            W += ind @ prob
+        T = np.zeros((n_states, n_states))
+        s_idx = np.arange(n_states)
+        for q, row in enumerate(parts):
+            roots = np.unique(row)
+            masks = np.array([sum(1 << i for i in range(V) if row[i] == r) for r in roots])
+            nc = len(masks)
+            sel = (np.arange(1 << nc)[:, None] >> np.arange(nc)[None, :]) & 1
+            flips = np.bitwise_or.reduce(sel * masks[None, :], axis=1)
+            T[s_idx[:, None], s_idx[:, None] ^ flips[None, :]] += W[q][:, None] / (1 << nc)
+        self._cache[k] = T
+        return T
+
+    def work_increment(self):
+        e = _bond_sums(self.sigma, self.links.self_) - _bond_sums(self.sigma, self.links.glue)
+        return e if self.dir > 0 else -e
+
+    def energy(self, lam):
+        lk = self.links
+        return -(_bond_sums(self.sigma, lk.full) + (1 - lam) * _bond_sums(self.sigma, lk.self_)
+                 + lam * _bond_sums(self.sigma, lk.glue))
+
+
+def exact_path_measure_sw(d, L, L_t, l, beta, n_step, n_sweep, n_therm, *, direction=1,
+                          quantised=True, start="hot"):
+    """Exact joint law of (W_int, final state) of the non-equilibrium dynamics
+    with Swendsen-Wang updates (same protocol as exact_path_measure: work
+    before each update, update at lambda_{k+1}).  Returns (w_values, F)."""
+    dyn = _SWDynamics(d, L, L_t, l, beta, n_step, direction, quantised)
+    n_states = 1 << dyn.V
+    lam0 = 0.0 if direction > 0 else 1.0
+    if start == "hot":
+        f = np.full(n_states, 1.0 / n_states)
+        T0 = dyn.kernel(None)
+        for _ in range(n_therm):
+            f = f @ T0
+    else:
+        e = -beta * dyn.energy(lam0)
+        w = np.exp(e - e.max())
+        f = w / w.sum()
+    de = dyn.work_increment()
+    wmax = int(np.max(np.abs(de))) * n_step
+    F = np.zeros((2 * wmax + 1, n_states))
+    F[wmax] = f
+    for k in range(n_step):
+        G = np.zeros_like(F)
+        for dv in np.unique(de):
+            sel = de == dv
+            if dv >= 0:
+                G[dv:, sel] += F[:F.shape[0] - dv, sel]
+            else:
+                G[:dv, sel] += F[-dv:, sel]
+        F = G
+        Tk = dyn.kernel(k)
+        for _ in range(n_sweep):
+            F = F @ Tk
     return np.arange(-wmax, wmax + 1), F

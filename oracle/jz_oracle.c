@@ -64,7 +64,13 @@
  *   1 update of step k at lambda_k      2 work taken after the sweeps
  *   3 region A not glued                4 forward start geometry glued at x = l
  *   5 one spatial link dropped          6 sign of the work flipped
- *   7 Boltzmann factor exp(-beta m)     */
+ *   7 Boltzmann factor exp(-beta m)
+ * and, in the Swendsen-Wang update:
+ *   8 bond probability e^-x instead of 1 - e^-x
+ *   9 switched bonds of step k at lambda_k
+ *  10 each site flips on its own draw instead of its cluster's
+ *  11 bonds also between unequal spins
+ *  12 glued links of region A stay inside one replica */
 #ifndef ORACLE_MUTANT
 #define ORACLE_MUTANT 0
 #endif
@@ -105,6 +111,18 @@ static uint32_t quantise(double x)
     double v = floor(ldexp(exp(-x), 32));
     return v >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)v;
 }
+
+/* Swendsen-Wang bond probability p = 1 - e^-x for a link of coupling K,
+ * x = 2K (Swendsen and Wang, PRL 58 (1987) 86, the paper's ref. for its
+ * cluster update), quantised the same way: a bond between equal spins is
+ * active iff u < floor(2^32 (1 - e^-x)), saturated at 2^32 - 1. */
+static uint32_t quantise_bond(double x)
+{
+    double v = floor(ldexp(ORACLE_MUTANT == 8 ? exp(-x) : -expm1(-x), 32));
+    return v >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)v;
+}
+
+uint32_t oracle_bond_threshold(double x) { return quantise_bond(x); }
 
 uint32_t oracle_threshold_bulk(double beta, int m)
 {
@@ -193,9 +211,12 @@ typedef struct {
     geom_t g;
     double beta;
     int n_step, n_sweep, n_therm;
+    int update;           /* 0 checkerboard Metropolis, 1 Swendsen-Wang */
     uint32_t key[2];
     uint32_t bulk_T[8];   /* indexed by m/2 for m = 2, 4, ..., 2d */
     const uint32_t *cut_T; /* [n_step][table], see cut_index() */
+    uint32_t bond_full;   /* Swendsen-Wang bond threshold of a full-beta link */
+    const uint32_t *bond_self, *bond_glue; /* [n_step] switched links at lambda_{k+1} */
 } run_t;
 
 /* The switched-site table of one step is indexed by a (odd, |a| <= 2d-1), b, c. */
@@ -268,6 +289,99 @@ static void sweep(const run_t *R, int8_t *s, long long traj, int sweep_index, in
     }
 }
 
+/* ---------------------------------------------------- Swendsen-Wang update --
+ * One cluster update of the replica lattice at protocol step k (k < 0:
+ * thermalisation at the start geometry), the update the paper's GPU code uses
+ * (section 3, GPU paragraph).  Every link with coupling K > 0 between equal
+ * spins becomes a bond with probability 1 - e^{-2K}; the clusters of bonded
+ * sites are flipped independently with probability 1/2.  Bit-level
+ * conventions (shared with the CUDA path only as this written contract):
+ *   bonds   the links leaving site i (natural index ((r L_t + t) L_y + y) L + x)
+ *           towards +x, +t in the same replica, +y and +t into replica r+1 use
+ *           words 0, 1, 2, 3 of Philox block (i, s, traj, dir<<1 | l<<2 | 2<<30);
+ *   flips   a cluster's representative is its smallest site index; the
+ *           cluster flips iff the top bit of word 0 of Philox block
+ *           (root, s, traj, dir<<1 | l<<2 | 3<<30) is set. */
+static int uf_find(int *parent, int a)
+{
+    while (parent[a] != a) a = parent[a];
+    return a;
+}
+
+/* joins the clusters of a and b; the smaller root stays the root */
+static void uf_union(int *parent, int a, int b)
+{
+    int ra = uf_find(parent, a), rb = uf_find(parent, b);
+    if (ra == rb) return;
+    if (ra < rb) parent[rb] = ra; else parent[ra] = rb;
+}
+
+static uint32_t philox_word(const run_t *R, uint32_t c0, uint32_t sweep, long long traj,
+                            uint32_t phase, int word)
+{
+    const geom_t *g = &R->g;
+    uint32_t ctr[4], out[4];
+    ctr[0] = c0;
+    ctr[1] = sweep;
+    ctr[2] = (uint32_t)traj;
+    ctr[3] = ((uint32_t)(g->dir < 0) << 1) | ((uint32_t)g->l << 2) | (phase << 30);
+    oracle_philox4x32_10(ctr, R->key, out);
+    return out[word];
+}
+
+static void sw_sweep(const run_t *R, int8_t *s, int *parent, long long traj, int sweep_index,
+                     int k)
+{
+    const geom_t *g = &R->g;
+    const int V = 2 * g->Lt * g->Ly * g->L;
+    const int protocol = k >= 0;
+    for (int i = 0; i < V; ++i) parent[i] = i;
+    for (int r = 0; r < g->n; ++r)
+    for (int t = 0; t < g->Lt; ++t)
+    for (int y = 0; y < g->Ly; ++y)
+    for (int x = 0; x < g->L; ++x) {
+        int i = site_of(g, r, t, y, x);
+        /* partners and thresholds of the four forward links */
+        int j[4] = {-1, -1, -1, -1};
+        uint32_t T[4] = {0, 0, 0, 0};
+        j[0] = site_of(g, r, t, y, wrap(x + 1, g->L));
+        T[0] = R->bond_full;
+        if (g->d == 3) {
+            j[2] = site_of(g, r, t, wrap(y + 1, g->Ly), x);
+            T[2] = R->bond_full;
+        }
+        int tn = wrap(t + 1, g->Lt);
+        if (t != 0) {
+            j[1] = site_of(g, r, tn, y, x);
+            T[1] = R->bond_full;
+        } else {
+            int self_site = site_of(g, r, tn, y, x);
+            int glue_site = site_of(g, wrap(r + 1, g->n), tn, y, x);
+            if (x > g->l) {
+                j[1] = self_site; T[1] = R->bond_full;
+            } else if (x < g->l) {
+                j[3] = ORACLE_MUTANT == 12 ? self_site : glue_site; T[3] = R->bond_full;
+            } else if (!protocol) {
+                if (g->dir > 0) { j[1] = self_site; T[1] = R->bond_full; }
+                else { j[3] = glue_site; T[3] = R->bond_full; }
+            } else {
+                j[1] = self_site; T[1] = R->bond_self[k];
+                j[3] = glue_site; T[3] = R->bond_glue[k];
+            }
+        }
+        for (int w = 0; w < 4; ++w) {
+            if (j[w] < 0 || (s[i] != s[j[w]] && ORACLE_MUTANT != 11)) continue;
+            if (philox_word(R, (uint32_t)i, (uint32_t)sweep_index, traj, 2, w) < T[w])
+                uf_union(parent, i, j[w]);
+        }
+    }
+    for (int i = 0; i < V; ++i) {
+        int root = ORACLE_MUTANT == 10 ? i : uf_find(parent, i);
+        if (philox_word(R, (uint32_t)root, (uint32_t)sweep_index, traj, 3, 0) >> 31)
+            s[i] = (int8_t)(-s[i]);
+    }
+}
+
 /* dE_k = H_{lambda_{k+1}} - H_{lambda_k} on the current configuration, in
  * units of beta / N (Appendix A, eq. work_in_one_MC_step). */
 static long long work_increment(const run_t *R, const int8_t *s)
@@ -296,15 +410,22 @@ static void hot_start(const run_t *R, int8_t *s, long long traj)
     }
 }
 
-static long long run_trajectory(const run_t *R, long long traj, int8_t *s)
+static void update(const run_t *R, int8_t *s, int *parent, long long traj, int sweep_index,
+                   int k)
+{
+    if (R->update == 1) sw_sweep(R, s, parent, traj, sweep_index, k);
+    else sweep(R, s, traj, sweep_index, k);
+}
+
+static long long run_trajectory(const run_t *R, long long traj, int8_t *s, int *parent)
 {
     hot_start(R, s, traj);
-    for (int i = 0; i < R->n_therm; ++i) sweep(R, s, traj, i, -1);
+    for (int i = 0; i < R->n_therm; ++i) update(R, s, parent, traj, i, -1);
     long long w = 0;
     for (int k = 0; k < R->n_step; ++k) {
         if (ORACLE_MUTANT != 2) w += work_increment(R, s);
         for (int i = 0; i < R->n_sweep; ++i)
-            sweep(R, s, traj, R->n_therm + k * R->n_sweep + i, k);
+            update(R, s, parent, traj, R->n_therm + k * R->n_sweep + i, k);
         if (ORACLE_MUTANT == 2) w += work_increment(R, s);
     }
     return w;
@@ -317,11 +438,12 @@ static long long run_trajectory(const run_t *R, long long traj, int8_t *s)
  * trajectory as int8 +-1 in the natural order [traj][r][t][y][x].
  * n_threads > 0 sets the OpenMP thread count (trajectories are independent, so
  * the result does not depend on it).  Returns 0, or -1 on bad arguments. */
-int oracle_run(int d, int L, int Lt, double beta, int l, int n_step, int n_sweep,
-               int n_therm, int dir, uint64_t seed, long long traj0, int n_traj,
-               int n_threads, long long *work_out, int8_t *spins_out)
+int oracle_run_update(int d, int L, int Lt, double beta, int l, int n_step, int n_sweep,
+                      int n_therm, int dir, int upd, uint64_t seed, long long traj0, int n_traj,
+                      int n_threads, long long *work_out, int8_t *spins_out)
 {
     if ((d != 2 && d != 3) || L < 2 || Lt < 2 || (L & 1) || (Lt & 1)) return -1;
+    if (upd != 0 && upd != 1) return -1;
     if (l < 0 || l >= L || n_step < 1 || n_sweep < 0 || n_therm < 0) return -1;
     if (dir != 1 && dir != -1) return -1;
     run_t R;
@@ -347,6 +469,21 @@ int oracle_run(int d, int L, int Lt, double beta, int l, int n_step, int n_sweep
         }
     }
     R.cut_T = cut;
+    /* Swendsen-Wang bond thresholds: full links x = 2 beta, switched links at
+     * step k: x = (2 beta w)/N with w = w_self or w_glue of lambda_{k+1} */
+    R.update = upd;
+    R.bond_full = quantise_bond(2.0 * beta);
+    uint32_t *bonds = (uint32_t *)malloc(sizeof(uint32_t) * 2 * (size_t)n_step);
+    if (!bonds) { free(cut); return -1; }
+    for (int k = 0; k < n_step; ++k) {
+        long long kp = ORACLE_MUTANT == 9 ? k : k + 1;
+        long long w_self = dir > 0 ? n_step - kp : kp;
+        long long w_glue = dir > 0 ? kp : n_step - kp;
+        bonds[k] = quantise_bond((2.0 * beta * (double)w_self) / (double)n_step);
+        bonds[n_step + k] = quantise_bond((2.0 * beta * (double)w_glue) / (double)n_step);
+    }
+    R.bond_self = bonds;
+    R.bond_glue = bonds + n_step;
     int V = 2 * L * Lt * R.g.Ly;
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
@@ -357,20 +494,32 @@ int oracle_run(int d, int L, int Lt, double beta, int l, int n_step, int n_sweep
 #pragma omp parallel
     {
         int8_t *s = (int8_t *)malloc((size_t)V);
-        if (!s) {
+        int *parent = (int *)malloc(sizeof(int) * (size_t)V);
+        if (!s || !parent) {
 #pragma omp atomic write
             failed = 1;
         }
 #pragma omp for schedule(dynamic, 1)
         for (int i = 0; i < n_traj; ++i) {
-            if (!s) continue;
-            work_out[i] = run_trajectory(&R, traj0 + i, s);
+            if (!s || !parent) continue;
+            work_out[i] = run_trajectory(&R, traj0 + i, s, parent);
             if (spins_out) memcpy(spins_out + (size_t)i * V, s, (size_t)V);
         }
         free(s);
+        free(parent);
     }
     free(cut);
+    free(bonds);
     return failed ? -1 : 0;
+}
+
+/* The Metropolis form (update 0) of oracle_run_update. */
+int oracle_run(int d, int L, int Lt, double beta, int l, int n_step, int n_sweep,
+               int n_therm, int dir, uint64_t seed, long long traj0, int n_traj,
+               int n_threads, long long *work_out, int8_t *spins_out)
+{
+    return oracle_run_update(d, L, Lt, beta, l, n_step, n_sweep, n_therm, dir, 0, seed, traj0,
+                             n_traj, n_threads, work_out, spins_out);
 }
 
 /* Number of OpenMP threads a parallel region would use (1 without OpenMP). */
