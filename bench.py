@@ -39,6 +39,11 @@ UNIT = "spin-updates/s"
 # Algorithmic integer operations per spin update (Philox4x32-10 share, local
 # field and acceptance), fixed a priori for the roofline.
 N_ALG = {2: 32, 3: 36}
+# Swendsen-Wang: algorithmic integer operations per site and sweep of the bond
+# phase alone (one Philox4x32-10 block of about 100 operations, four threshold
+# compares); the data-dependent union-find and root flip draws are not counted,
+# so this fraction is a lower bound.
+N_ALG_SW = {2: 104, 3: 104}
 SM_COUNT, INT_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 L2_FLUSH_BYTES = 512 << 20
 
@@ -68,6 +73,11 @@ def parse_args():
                     help="skip the (untimed) CTA-size autotuning per lattice shape")
     ap.add_argument("--probe", action="store_true",
                     help="print the integer-issue probe rates as JSON and exit")
+    ap.add_argument("--update", choices=["metropolis", "sw"], default="metropolis",
+                    help="Monte Carlo update of every sweep: checkerboard Metropolis or "
+                         "Swendsen-Wang clusters")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="sw: skip the equal-error comparison with Metropolis")
     ap.add_argument("--plain", type=int, default=0,
                     help="also time the plain one-lattice-per-launch baseline on this many "
                          "trajectories of the middle l")
@@ -79,8 +89,11 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def workload_for(config: int, rank: int, traj_per_l=None, n_step=None):
+def workload_for(config: int, rank: int, traj_per_l=None, n_step=None, update="metropolis"):
     w = wl.CONFIGS[config]()
+    if update == "sw":
+        w.jobs = [j.with_(update=1) for j in w.jobs]
+        w.name += "_sw"
     if traj_per_l:
         w.jobs = [j.with_(n_traj=traj_per_l) for j in w.jobs]
         w.name += f"_traj{traj_per_l}"
@@ -190,7 +203,7 @@ def cpu_oracle_rate(w, seconds: float):
     j = jobs[0]
     t0 = time.perf_counter()
     oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, threads, j.seed,
-               n_therm=j.n_therm, traj0=j.traj0, n_threads=threads)
+               n_therm=j.n_therm, traj0=j.traj0, n_threads=threads, update=j.update)
     t_round = time.perf_counter() - t0
     rounds = max(1, int(seconds / max(t_round, 1e-3) / len(jobs)))
     n_per_job = rounds * threads
@@ -198,7 +211,7 @@ def cpu_oracle_rate(w, seconds: float):
     updates = 0
     for j in jobs:
         oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, n_per_job, j.seed,
-                   n_therm=j.n_therm, traj0=j.traj0, n_threads=threads)
+                   n_therm=j.n_therm, traj0=j.traj0, n_threads=threads, update=j.update)
         updates += j.with_(n_traj=n_per_job).updates
     dt = time.perf_counter() - t0
     sample = (f"{n_per_job} trajectories at each of l = {[j.l for j in jobs]} of the same "
@@ -253,19 +266,23 @@ def run_ours(args):
         dist.barrier()
     import paper_2304_03311_gb300 as jz
 
-    w = workload_for(args.config, rank, args.traj_per_l, args.n_step)
+    w = workload_for(args.config, rank, args.traj_per_l, args.n_step, args.update)
+    sw = args.update == "sw"
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
     ctx = jz.ising_replica_init(local_rank, 0, stream.cuda_stream)
     outs = [torch.empty(j.n_traj, dtype=torch.int64, device=dev) for j in w.jobs]
     params = [jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj,
-                             j.seed, n_therm=j.n_therm, direction=j.direction, traj0=j.traj0)
+                             j.seed, n_therm=j.n_therm, direction=j.direction, traj0=j.traj0,
+                             update=j.update)
               for j in w.jobs]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     n_groups = len({(j.d, j.L, j.L_t, j.seed) for j in w.jobs})
     tuned = {}
     plan = None
     est = None
+    if sw and args.config == 4:
+        raise SystemExit("--update sw runs configs 1-3 (the persistent plan is Metropolis only)")
     if args.config == 4:
         # uneven batch: one persistent launch + batched estimator, one CUDA graph
         est = torch.zeros(3 * len(w.jobs), dtype=torch.float64, device=dev)
@@ -278,7 +295,7 @@ def run_ours(args):
             if args.threads:
                 jz.ising_set_threads(ctx, *shape, args.threads)
                 tuned[str(shape)] = args.threads
-            elif not args.no_autotune:
+            elif not args.no_autotune and not sw:
                 p = params[w.jobs.index(j)]
                 tuned[str(shape)] = jz.ising_autotune(ctx, p)
 
@@ -379,7 +396,7 @@ def run_ours(args):
         t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t[0])
-    table_bytes = sum(j.n_step * 8 * j.d * 4 + 96 for j in w.jobs)
+    table_bytes = sum(j.n_step * (2 if sw else 8 * j.d) * 4 + 96 for j in w.jobs)
     h2d = table_bytes + sum(8 * j.n_traj * world for j in w.jobs)
     d2h = sum(8 * j.n_traj for j in w.jobs) + 24 * len(w.jobs)
     e2e = {"value": updates_step / (e2e_s / e2e_steps) if e2e_steps else None, "unit": UNIT,
@@ -387,17 +404,49 @@ def run_ours(args):
 
     d = w.jobs[0].d
     updates_per_launch = w.updates   # one launch per rank per step
-    achieved = N_ALG[d] * updates_per_launch / (kernel_ms / 1e3) / 1e12
+    n_alg = (N_ALG_SW if sw else N_ALG)[d]
+    achieved = n_alg * updates_per_launch / (kernel_ms / 1e3) / 1e12
     peak = SM_COUNT * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     src_hash = kernel_source_hash()
-    roofline = {"bound": "alu", "kernel": f"traj_kernel<{d},...>", "achieved": achieved,
+    kname = (f"sw_kernel<{d}>" if sw else
+             "persistent_kernel" if plan is not None else f"traj_kernel<{d},...>")
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved,
                 "peak": peak, "unit": "Tintop/s", "frac": achieved / peak,
-                "traffic": traffic_from_profile(src_hash),
-                "ops_per_update": N_ALG[d], "kernel_ms": kernel_ms,
+                "traffic": None if sw else traffic_from_profile(src_hash),
+                "ops_per_update": n_alg, "kernel_ms": kernel_ms,
                 "peak_basis": "152 SMs x 128 int lanes/clk x 2070 MHz (derived)"}
 
+    equal_error = None
+    if sw and not args.no_compare:
+        # the same workload with Metropolis sweeps: time per step and the
+        # c-function error it reaches; at equal error the cost scales as err^2 t
+        mparams = [jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj,
+                                  j.seed, n_therm=j.n_therm, direction=j.direction,
+                                  traj0=j.traj0, update=0) for j in w.jobs]
+        if not args.no_autotune and not args.threads:
+            for shape, j in {(j.d, j.L, j.L_t): j for j in w.jobs}.items():
+                jz.ising_autotune(ctx, mparams[w.jobs.index(j)])
+        with torch.cuda.stream(stream):
+            jz.jarzynski_run_batch(ctx, mparams, outs)
+            m0 = torch.cuda.Event(enable_timing=True)
+            m1 = torch.cuda.Event(enable_timing=True)
+            flush.fill_(1)
+            m0.record(stream)
+            jz.jarzynski_run_batch(ctx, mparams, outs)
+            m1.record(stream)
+        stream.synchronize()
+        m_ms = m0.elapsed_time(m1)
+        m_err = [e for _, e in c_function_errors(w, estimate(outs, 1))]
+        s_err = [e for _, e in cfun]
+        rms = lambda v: math.sqrt(sum(x * x for x in v) / len(v))
+        equal_error = {
+            "metropolis": {"kernel_ms": m_ms, "c_err_rms": rms(m_err)},
+            "sw": {"kernel_ms": kernel_ms, "c_err_rms": rms(s_err)},
+            "sw_speedup_at_equal_error": (rms(m_err) ** 2 * m_ms) / (rms(s_err) ** 2 * kernel_ms),
+            "basis": "same trajectories, N, sweeps and n_therm; cost at equal error ~ err^2 x time"}
+
     plain = None
-    if args.plain > 0:
+    if args.plain > 0 and not sw:
         j = w.jobs[len(w.jobs) // 2].with_(n_traj=args.plain)
         pw = torch.empty(j.n_traj, dtype=torch.int64, device=dev)
         pp = jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj, j.seed,
@@ -417,7 +466,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, trate, cores, sample = cpu_oracle_rate(w, args.cpu_seconds)
+        rate, trate, cores, sample = cpu_oracle_rate(w, args.cpu_seconds / (3 if sw else 1))
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
                "trajectories_per_s": trate}
     if plan is not None:
@@ -433,6 +482,7 @@ def run_ours(args):
                 "c_function_err_max": max(e for _, e in cfun) if cfun else None,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "plain_gpu_baseline": plain, "cta_threads": tuned or "default",
+                "update": args.update, "equal_error_vs_metropolis": equal_error,
                 "gpu_launches": args.steps * ((2 if plan is not None else n_groups + len(w.jobs))),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
@@ -499,7 +549,7 @@ def run_reference(args):
     import oracle
     oracle.build()
     threads = oracle.max_threads()
-    w = workload_for(args.config, 0, args.traj_per_l, args.n_step)
+    w = workload_for(args.config, 0, args.traj_per_l, args.n_step, args.update)
     jobs = w.jobs[:: max(1, len(w.jobs) // 2)][:2]
     n_per = threads
 
@@ -507,7 +557,7 @@ def run_reference(args):
         u = 0
         for j in jobs:
             oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, n_per, j.seed,
-                       n_therm=j.n_therm, traj0=j.traj0, n_threads=threads)
+                       n_therm=j.n_therm, traj0=j.traj0, n_threads=threads, update=j.update)
             u += j.with_(n_traj=n_per).updates
         return u
 

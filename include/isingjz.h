@@ -75,6 +75,17 @@ typedef struct ising_ctx ising_ctx;
  *   d          lattice dimension D, 2 or 3 (section 3, "extension to higher
  *              dimensions"); time is one of the D directions
  *   L, L_t     spatial and temporal extents, both even, L >= 2, L_t >= 2
+ *   update     the Monte Carlo update of every sweep (section 3):
+ *              0  checkerboard Metropolis, one site at a time (the default);
+ *              1  Swendsen-Wang clusters: a link of coupling K between equal
+ *                 spins becomes a bond with probability 1 - e^{-2K} and every
+ *                 cluster of bonded sites flips with probability 1/2.  One CTA
+ *                 per trajectory; needs 4 V + 8 ceil(V/32) bytes of shared
+ *                 memory for the V = 2 L_t L^(d-1) sites (at most 227 KiB,
+ *                 V up to about 54,000), else ISING_ERR_UNSUPPORTED.  Served by jarzynski_run_ex and
+ *                 jarzynski_run_batch; the other entry points return
+ *                 ISING_ERR_UNSUPPORTED for it.
+ *              Other values: ISING_ERR_ARG.
  *   beta       coupling, 0 <= beta <= 4
  *   l          width of region A before the move, 0 <= l <= L-1
  *   n_step     N >= 1 protocol steps, n_sweep >= 1 sweeps per step
@@ -84,6 +95,7 @@ typedef struct ising_ctx ising_ctx;
  *   seed       Philox key */
 typedef struct jz_params {
     int d, L, L_t;
+    int update;
     double beta;
     int l;
     int n_step, n_sweep, n_therm;

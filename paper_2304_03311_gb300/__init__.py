@@ -42,7 +42,7 @@ class JzParams(ctypes.Structure):
     """Mirror of ``jz_params`` in include/isingjz.h."""
     _fields_ = [
         ("d", ctypes.c_int), ("L", ctypes.c_int), ("L_t", ctypes.c_int),
-        ("beta", ctypes.c_double), ("l", ctypes.c_int),
+        ("update", ctypes.c_int), ("beta", ctypes.c_double), ("l", ctypes.c_int),
         ("n_step", ctypes.c_int), ("n_sweep", ctypes.c_int), ("n_therm", ctypes.c_int),
         ("n_traj", ctypes.c_int), ("direction", ctypes.c_int),
         ("traj0", ctypes.c_longlong), ("seed", ctypes.c_uint64),
@@ -175,9 +175,13 @@ def jarzynski_run(ctx, d, L, L_t, beta, l, n_step, n_sweep, n_traj, seed, work_i
                                 _ptr(work_int_out)), "jarzynski_run")
 
 
+METROPOLIS, SWENDSEN_WANG = 0, 1
+
+
 def make_params(d, L, L_t, beta, l, n_step, n_sweep, n_traj, seed=0, *, n_therm=1000,
-                direction=1, traj0=0) -> JzParams:
+                direction=1, traj0=0, update=METROPOLIS) -> JzParams:
     p = jz_params_default()
+    p.update = int(update)
     p.d, p.L, p.L_t, p.beta, p.l = int(d), int(L), int(L_t), float(beta), int(l)
     p.n_step, p.n_sweep, p.n_traj = int(n_step), int(n_sweep), int(n_traj)
     p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF

@@ -63,6 +63,7 @@ int check_params(const jz_params* p)
 {
     if (!p) return ISING_ERR_ARG;
     if (p->d != 2 && p->d != 3) return ISING_ERR_UNSUPPORTED;
+    if (p->update != 0 && p->update != 1) return ISING_ERR_ARG;
     if (p->L < 2 || p->L_t < 2 || p->L > 4096 || p->L_t > 4096) return ISING_ERR_ARG;
     if ((p->L & 1) || (p->L_t & 1)) return ISING_ERR_ODD_EXTENT;
     if (p->l < 0 || p->l > p->L - 1) return ISING_ERR_L_RANGE;
@@ -143,6 +144,39 @@ void build_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcu
     }
 }
 
+// Swendsen-Wang bond threshold of a link with x = 2K: a bond between equal
+// spins is active iff u < min(floor(2^32 (1 - e^{-x})), 2^32 - 1), i.e. with
+// probability 1 - e^{-x} to 2^-32 (Swendsen and Wang, PRL 58 (1987) 86).
+uint32_t bond_threshold(double x)
+{
+    double v = std::floor(std::ldexp(-std::expm1(-x), 32));
+    return v >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)v;
+}
+
+// Swendsen-Wang tables of one job: tb[0] the full link (x = 2 beta); per step
+// k the switched column's self and glued links at lambda_{k+1}:
+// x = (2 beta w) / N with w = w_self, w_glue.
+void build_bond_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcut,
+                       size_t off)
+{
+    tb[0] = bond_threshold(2.0 * p.beta);
+    tb[1] = tb[2] = tb[3] = 0;
+    const long long N = p.n_step;
+    for (long long k = 0; k < N; ++k) {
+        const long long kp = k + 1;
+        const long long ws = p.direction > 0 ? N - kp : kp;
+        const long long wg = p.direction > 0 ? kp : N - kp;
+        tcut[off + 2 * k] = bond_threshold((2.0 * p.beta * (double)ws) / (double)N);
+        tcut[off + 2 * k + 1] = bond_threshold((2.0 * p.beta * (double)wg) / (double)N);
+    }
+}
+
+// Whether a Swendsen-Wang trajectory of lattice g fits one CTA's shared memory.
+bool sw_fits(const jz::Geom& g)
+{
+    return jz::sw_smem_bytes(g) <= jz::kMaxSmemPerCta;
+}
+
 // Launch shape for lattices g in CTAs of cta_threads (0 = the default).  With
 // col = GW * L_y words per time slice, each thread owns one word column of
 // every TS-th slice.  col <= 32: warp teams of col * TS threads, TS =
@@ -221,10 +255,12 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
 {
     const jz_params& p0 = jobs[idx[0]];
     const jz::Geom g = make_geom(p0.d, p0.L, p0.L_t);
-    if (!shape_fits(g)) return ISING_ERR_UNSUPPORTED;
-    const jz::LaunchShape sh = ctx_shape(ctx, p0.d, g);
+    const bool sw = p0.update == 1;   // Swendsen-Wang: one trajectory per CTA
+    if (sw ? !sw_fits(g) : !shape_fits(g)) return ISING_ERR_UNSUPPORTED;
+    jz::LaunchShape sh = ctx_shape(ctx, p0.d, g);
+    if (sw) sh.teams = 1;
     const int n_jobs = (int)idx.size();
-    const int per = 8 * p0.d;
+    const int per = sw ? 2 : 8 * p0.d;
     const int V = 2 * p0.L_t * g.Ly * p0.L;
 
     size_t n_tcut = 0;
@@ -261,7 +297,8 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
         J.n_traj = p.n_traj;
         J.traj0 = p.traj0;
         J.cta0 = cta;
-        build_tables(p, J.tb, ctx->h_tcut, off);
+        if (sw) build_bond_tables(p, J.tb, ctx->h_tcut, off);
+        else build_tables(p, J.tb, ctx->h_tcut, off);
         J.tcut = d_tcut + off;
         J.w_out = outs_on_device ? (long long*)outs[idx[i]] : (long long*)ctx->work.ptr + traj_off;
         J.spins_out = nullptr;
@@ -282,9 +319,14 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
                                        n_jobs * sizeof(jz::JobDesc), cudaMemcpyHostToDevice, st))))
         return rc;
     const jz::PhiloxKeys K = key_schedule(p0.seed);
-    if ((rc = cuda_err(jz::launch_traj(p0.d, g, K, (const jz::JobDesc*)ctx->jobs.ptr, n_jobs,
-                                       n_cta, sh, st))))
+    if (sw) {
+        if ((rc = cuda_err(jz::launch_sw(p0.d, g, K, (const jz::JobDesc*)ctx->jobs.ptr, n_jobs,
+                                         n_cta, st))))
+            return rc;
+    } else if ((rc = cuda_err(jz::launch_traj(p0.d, g, K, (const jz::JobDesc*)ctx->jobs.ptr,
+                                              n_jobs, n_cta, sh, st)))) {
         return rc;
+    }
     if (!outs_on_device || (n_spin_traj && !spins_on_device)) {
         long long c = 0, so = 0;
         for (int i = 0; i < n_jobs; ++i) {
@@ -331,11 +373,12 @@ int run_jobs(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const* 
             if (first) { spins_dev = dv; first = false; }
             else if (dv != spins_dev) return ISING_ERR_ARG;
         }
-    // one launch per (d, L, L_t, seed), jobs kept in call order within a group
-    std::map<std::tuple<int, int, int, uint64_t>, std::vector<int>> groups;
-    std::vector<std::tuple<int, int, int, uint64_t>> order;
+    // one launch per (d, L, L_t, seed, update), jobs kept in call order within a group
+    std::map<std::tuple<int, int, int, uint64_t, int>, std::vector<int>> groups;
+    std::vector<std::tuple<int, int, int, uint64_t, int>> order;
     for (int j = 0; j < n_jobs; ++j) {
-        auto key = std::make_tuple(jobs[j].d, jobs[j].L, jobs[j].L_t, jobs[j].seed);
+        auto key = std::make_tuple(jobs[j].d, jobs[j].L, jobs[j].L_t, jobs[j].seed,
+                                   jobs[j].update);
         auto it = groups.find(key);
         if (it == groups.end()) {
             order.push_back(key);
@@ -465,6 +508,7 @@ int ising_autotune(ising_ctx* ctx, const jz_params* p, int* threads)
     if (!ctx || !p) return ISING_ERR_ARG;
     int rc = check_params(p);
     if (rc) return rc;
+    if (p->update != 0) return ISING_ERR_UNSUPPORTED;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
     const jz::Geom g = make_geom(p->d, p->L, p->L_t);
     if (!shape_fits(g)) return ISING_ERR_UNSUPPORTED;
@@ -529,6 +573,7 @@ int jarzynski_run_plain(ising_ctx* ctx, const jz_params* p, int64_t* work_int_ou
     if (!ctx || !p || !work_int_out) return ISING_ERR_ARG;
     int rc = check_params(p);
     if (rc) return rc;
+    if (p->update != 0) return ISING_ERR_UNSUPPORTED;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
     const jz::Geom g = make_geom(p->d, p->L, p->L_t);
     const int V = 2 * p->L_t * g.Ly * p->L;
@@ -695,6 +740,7 @@ extern "C" int jarzynski_run_noalloc(const jz_params* p, int64_t* work_int_out, 
     if (!p || !work_int_out) return ISING_ERR_ARG;
     int rc = check_params(p);
     if (rc) return rc;
+    if (p->update != 0) return ISING_ERR_UNSUPPORTED;
     if ((size_t)p->n_step * 8 * (size_t)p->d > kNoAllocMaxThresholds) return ISING_ERR_SCRATCH_LIMIT;
     const jz::Geom g = make_geom(p->d, p->L, p->L_t);
     if (!shape_fits(g)) return ISING_ERR_UNSUPPORTED;
@@ -941,6 +987,7 @@ int jz_plan_create(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* c
     for (int j = 0; j < n_jobs; ++j) {
         const int rc = check_params(&jobs[j]);
         if (rc) return rc;
+        if (jobs[j].update != 0) return ISING_ERR_UNSUPPORTED;
         if (jobs[j].seed != jobs[0].seed || !work_outs[j] || !is_device_ptr(work_outs[j]))
             return ISING_ERR_ARG;
     }

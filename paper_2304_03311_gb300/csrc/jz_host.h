@@ -19,6 +19,9 @@ cudaError_t launch_traj(int D, const Geom& g, const PhiloxKeys& K, const JobDesc
                         int n_jobs, long long n_cta, const LaunchShape& sh, cudaStream_t st);
 cudaError_t launch_estimator(const long long* w_int, int n, double scale, int direction,
                              int n_blocks, double* out, cudaStream_t st);
+size_t sw_smem_bytes(const Geom& g);
+cudaError_t launch_sw(int D, const Geom& g, const PhiloxKeys& K, const JobDesc* jobs,
+                      int n_jobs, long long n_cta, cudaStream_t st);
 double run_probe(int kind, int device);
 cudaError_t plain_trajectory(int D, const Geom& g, const PhiloxKeys& K, int l, int dir,
                              int n_step, int n_sweep, int n_therm, uint32_t traj,
@@ -55,6 +58,10 @@ jz::Geom make_geom(int d, int L, int Lt);
 uint32_t threshold(double x);
 jz::PhiloxKeys key_schedule(uint64_t seed);
 void build_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcut, size_t off);
+uint32_t bond_threshold(double x);
+void build_bond_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcut,
+                       size_t off);
+bool sw_fits(const jz::Geom& g);
 jz::LaunchShape shape_for(const jz::Geom& g, int cta_threads);
 bool shape_fits(const jz::Geom& g);
 bool threads_ok(const jz::Geom& g, int threads);

@@ -1,0 +1,350 @@
+// jz_sw.cu -- Swendsen-Wang cluster update of the replica lattice (the update
+// of the paper's own GPU code, section 3) inside a Jarzynski transformation.
+//
+// One CTA runs one trajectory.  Shared memory holds, for the V = 2 L_t L_y L
+// sites of the replica lattice in natural order i = ((r L_t + t) L_y + y) L + x:
+//   lab[V]   int32 cluster labels (lab[i] <= i always: a forest whose roots are
+//            the smallest site index of their cluster)
+//   sp[VW]   spin bits, bit i of the lattice = 1 for spin -1
+//   fb[VW]   flip bits of the cluster roots of the current sweep
+// One sweep is three phases separated by CTA barriers:
+//   B  every site draws one Philox block (i, s, traj, dir<<1 | l<<2 | 2<<30);
+//      word w in {+x, +t same replica, +y, +t into replica r+1} activates that
+//      forward link when both spins are equal and the word is below the link's
+//      bond threshold floor(2^32 (1 - e^{-2K})); active links merge clusters by
+//      lock-free union with atomicMin (the larger root is hooked under the
+//      smaller one, so the root of a cluster is its smallest site index);
+//   C  path compression; each root draws Philox block (root, s, traj,
+//      dir<<1 | l<<2 | 3<<30) and its cluster flips iff the top bit of word 0
+//      is set (the warp assembles 32 roots' bits into one fb word);
+//   D  every site flips iff its root's fb bit is set (the warp assembles 32
+//      sites into one spin word) and resets its label for the next sweep.
+// The cluster partition, hence the minimum-index root of every cluster, does
+// not depend on the order of the unions, so the result is the same bit for bit
+// as a sequential union-find over the same bonds.
+//
+// Termination: a label always points to a site with a smaller or equal index
+// (equal only at a root), so every find walks a strictly decreasing chain (at
+// most V steps) and every retry of a union restarts from a strictly smaller
+// site.
+#include <cstdint>
+
+#include "jz_device.cuh"
+#include "jz_host.h"
+
+namespace jz {
+
+namespace {
+
+constexpr int kSwThreads = 256;
+
+// Division by a fixed divisor d >= 1 for numerators n < 2^31 (Granlund and
+// Montgomery, PLDI'94): with s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d)
+// + 1, n / d = (umulhi(m, n) + n) >> s.
+struct FastDiv {
+    uint32_t d, m, s;
+};
+
+FastDiv make_fastdiv(uint32_t d)
+{
+    uint32_t s = 0;
+    while ((1ull << s) < d) ++s;
+    const uint64_t m = (((1ull << s) - d) << 32) / d + 1;
+    return FastDiv{d, (uint32_t)m, s};
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f)
+{
+    return (__umulhi(f.m, n) + n) >> f.s;
+}
+
+struct SwGeom {
+    int L, Lt, Ly;
+    int V;        // sites of the replica lattice
+    int VW;       // 32-bit words of one site bit array, ceil(V / 32)
+    int SL;       // sites of one time slice, L_y * L
+    int VR;       // sites of one replica, L_t * SL
+    int G;        // Philox blocks per colour row of the hot start, ceil(L / 8)
+    FastDiv dL, dLy;
+};
+
+struct Site {
+    int x, y, t, r, row;
+};
+
+template <int D>
+__device__ __forceinline__ Site decode(int i, const SwGeom& g)
+{
+    Site s;
+    s.row = (int)fdiv((uint32_t)i, g.dL);
+    s.x = i - s.row * g.L;
+    int tr = s.row;
+    s.y = 0;
+    if (D == 3) {
+        tr = (int)fdiv((uint32_t)s.row, g.dLy);
+        s.y = s.row - tr * g.Ly;
+    }
+    s.r = tr >= g.Lt;
+    s.t = tr - s.r * g.Lt;
+    return s;
+}
+
+__device__ __forceinline__ int spin_bit(const uint32_t* sp, int i)
+{
+    return (sp[i >> 5] >> (i & 31)) & 1;
+}
+
+// Root of a with path halving: every visited node is re-pointed to its
+// grandparent.  A plain store is enough: the new parent is an ancestor of the
+// node, and a hook that a concurrent union made on that node is only ever
+// overwritten after the union has moved on to join the node's old tree.
+__device__ __forceinline__ int find_root(volatile int* lab, int a)
+{
+    for (;;) {
+        const int p = lab[a];
+        if (p == a) return a;
+        const int gp = lab[p];
+        if (gp == p) return p;
+        lab[a] = gp;
+        a = gp;
+    }
+}
+
+// Root of a without writes: in the compression phase only a node's owner may
+// store to it (a halving store racing with the owner's root store could leave
+// a non-root ancestor behind).
+__device__ __forceinline__ int find_root_ro(const volatile int* lab, int a)
+{
+    int p;
+    while ((p = lab[a]) != a) a = p;
+    return a;
+}
+
+__device__ __forceinline__ void merge(int* lab, int a, int b)
+{
+    volatile int* vl = lab;
+    for (;;) {
+        a = find_root(vl, a);
+        b = find_root(vl, b);
+        if (a == b) return;
+        if (a < b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const int old = atomicMin(&lab[a], b);   // hook root a under b < a
+        if (old == a) return;
+        a = old;                                 // a was hooked meanwhile: retry from its parent
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kSwThreads)
+sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, int n_jobs)
+{
+    extern __shared__ uint32_t smem[];
+    int* lab = (int*)smem;
+    uint32_t* sp = smem + g.V;
+    uint32_t* fb = sp + g.VW;
+
+    // the job owning this CTA: the last j with jobs[j].cta0 <= blockIdx.x
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&jobs[mid].cta0) <= (long long)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    const JobDesc& J = jobs[lo];
+    const long long local = (long long)blockIdx.x - __ldg(&J.cta0);
+    const int l = __ldg(&J.l), dir = __ldg(&J.dir);
+    const int n_step = __ldg(&J.n_step), n_sweep = __ldg(&J.n_sweep);
+    const int n_therm = __ldg(&J.n_therm);
+    const uint32_t t_full = __ldg(&J.tb[0]);
+    const uint32_t* bonds = J.tcut;          // [n_step][2]: self, glue thresholds
+    const uint32_t traj = (uint32_t)(__ldg(&J.traj0) + local);
+    const uint64_t p1 = (uint64_t)kPhiloxM1 * traj;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t c3 = ((uint32_t)(dir < 0) << 1) | ((uint32_t)l << 2);
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n_warps = blockDim.x >> 5;
+    const int chunk = n_warps * 32;
+
+    // hot start: spin -1 iff the top bit of the site's word of the colour-row
+    // Philox block (row G + h/4, 0, traj, colour | dir<<1 | l<<2 | 1<<30), h = x/2
+    for (int base = warp * 32; base < g.V; base += chunk) {
+        const int i = base + lane;
+        int bit = 0;
+        if (i < g.V) {
+            const Site s = decode<D>(i, g);
+            const int h = s.x >> 1;
+            const uint32_t colour = (uint32_t)((s.x + s.y + s.t) & 1);
+            const uint4 u = philox_r0((uint32_t)(s.row * g.G + (h >> 2)), 0u, hi1, lo1,
+                                      colour | c3 | (1u << 30), K);
+            bit = (int)(word_of(u, h & 3) >> 31);
+            lab[i] = i;
+        }
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, bit);
+        if (lane == 0) sp[base >> 5] = m;
+    }
+    __syncthreads();
+
+    long long w = 0;
+    const int n_total = n_therm + n_step * n_sweep;
+    for (int sw = 0; sw < n_total; ++sw) {
+        const int k = sw < n_therm ? -1 : (sw - n_therm) / n_sweep;
+        const bool step_start = k >= 0 && (sw - n_therm) % n_sweep == 0;
+        // work of step k on the configuration before its sweeps:
+        // dE = sum_{r,y} s(l,y,0)^r [s(l,y,1)^r - s(l,y,1)^{r+1}]
+        if (step_start && warp == 0) {
+            int e = 0;
+            for (int q = lane; q < 2 * g.Ly; q += 32) {
+                const int r = q / g.Ly, y = q - r * g.Ly;
+                const int lo_i = (r * g.Lt * g.Ly + y) * g.L + l;
+                const int up_s = lo_i + g.SL;
+                const int up_g = up_s + (r ? -g.VR : g.VR);
+                const int s0 = 1 - 2 * spin_bit(sp, lo_i);
+                e += s0 * ((1 - 2 * spin_bit(sp, up_s)) - (1 - 2 * spin_bit(sp, up_g)));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
+            w += e;
+        }
+        uint32_t t_self = 0, t_glue = 0;   // the switched column's two time links
+        if (k < 0) {
+            if (dir > 0) t_self = t_full; else t_glue = t_full;
+        } else {
+            t_self = __ldg(&bonds[2 * k]);
+            t_glue = __ldg(&bonds[2 * k + 1]);
+        }
+        const uint32_t cb = c3 | (2u << 30);
+        // phase B: bonds and unions
+        for (int i = threadIdx.x; i < g.V; i += blockDim.x) {
+            const Site s = decode<D>(i, g);
+            const int si = spin_bit(sp, i);
+            int j[4];
+            uint32_t T[4];
+            j[0] = s.x == g.L - 1 ? i + 1 - g.L : i + 1;
+            T[0] = t_full;
+            j[2] = -1;
+            T[2] = 0;
+            if (D == 3) {
+                j[2] = s.y == g.Ly - 1 ? i + g.L - g.SL : i + g.L;
+                T[2] = t_full;
+            }
+            j[1] = -1;
+            T[1] = 0;
+            j[3] = -1;
+            T[3] = 0;
+            if (s.t != 0) {
+                j[1] = s.t == g.Lt - 1 ? i + g.SL - g.VR : i + g.SL;
+                T[1] = t_full;
+            } else {
+                const int js = i + g.SL;
+                const int jg = js + (s.r ? -g.VR : g.VR);
+                if (s.x > l) {
+                    j[1] = js;
+                    T[1] = t_full;
+                } else if (s.x < l) {
+                    j[3] = jg;
+                    T[3] = t_full;
+                } else {
+                    j[1] = js;
+                    T[1] = t_self;
+                    j[3] = jg;
+                    T[3] = t_glue;
+                }
+            }
+            bool any = false;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (j[q] >= 0 && (T[q] == 0 || spin_bit(sp, j[q]) != si)) j[q] = -1;
+                any |= j[q] >= 0;
+            }
+            if (!any) continue;
+            const uint4 u = philox_r0((uint32_t)i, (uint32_t)sw, hi1, lo1, cb, K);
+            if (j[0] >= 0 && u.x < T[0]) merge(lab, i, j[0]);
+            if (j[1] >= 0 && u.y < T[1]) merge(lab, i, j[1]);
+            if (D == 3 && j[2] >= 0 && u.z < T[2]) merge(lab, i, j[2]);
+            if (j[3] >= 0 && u.w < T[3]) merge(lab, i, j[3]);
+        }
+        __syncthreads();
+        // phase C: compression and the flip bit of every root
+        const uint32_t cf = c3 | (3u << 30);
+        for (int base = warp * 32; base < g.V; base += chunk) {
+            const int i = base + lane;
+            int f = 0;
+            if (i < g.V) {
+                const int root = find_root_ro((volatile int*)lab, i);
+                if (root == i) {
+                    const uint4 u = philox_r0((uint32_t)i, (uint32_t)sw, hi1, lo1, cf, K);
+                    f = (int)(u.x >> 31);
+                } else {
+                    ((volatile int*)lab)[i] = root;
+                }
+            }
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, f);
+            if (lane == 0) fb[base >> 5] = m;
+        }
+        __syncthreads();
+        // phase D: flip the clusters, reset the labels
+        for (int base = warp * 32; base < g.V; base += chunk) {
+            const int i = base + lane;
+            int f = 0;
+            if (i < g.V) {
+                const int root = lab[i];
+                f = (int)((fb[root >> 5] >> (root & 31)) & 1);
+                lab[i] = i;
+            }
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, f);
+            if (lane == 0) sp[base >> 5] ^= m;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) J.w_out[local] = dir > 0 ? w : -w;
+    int8_t* so = J.spins_out;
+    if (so != nullptr) {
+        so += local * (long long)g.V;
+        for (int i = threadIdx.x; i < g.V; i += blockDim.x)
+            so[i] = spin_bit(sp, i) ? (int8_t)-1 : (int8_t)1;
+    }
+}
+
+SwGeom make_swgeom(int D, const Geom& geo)
+{
+    SwGeom g;
+    g.L = geo.L;
+    g.Lt = geo.Lt;
+    g.Ly = geo.Ly;
+    g.SL = g.Ly * g.L;
+    g.VR = g.Lt * g.SL;
+    g.V = 2 * g.VR;
+    g.VW = (g.V + 31) / 32;
+    g.G = geo.G;
+    g.dL = make_fastdiv((uint32_t)g.L);
+    g.dLy = make_fastdiv((uint32_t)g.Ly);
+    (void)D;
+    return g;
+}
+
+}  // namespace
+
+size_t sw_smem_bytes(const Geom& geo)
+{
+    const size_t V = (size_t)2 * geo.Lt * geo.Ly * geo.L;
+    return V * sizeof(int) + 2 * ((V + 31) / 32) * sizeof(uint32_t);
+}
+
+cudaError_t launch_sw(int D, const Geom& geo, const PhiloxKeys& K, const JobDesc* jobs,
+                      int n_jobs, long long n_cta, cudaStream_t st)
+{
+    const SwGeom g = make_swgeom(D, geo);
+    const size_t smem = sw_smem_bytes(geo);
+    auto kern = D == 3 ? sw_kernel<3> : sw_kernel<2>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)n_cta, kSwThreads, smem, st>>>(g, K, jobs, n_jobs);
+    return cudaGetLastError();
+}
+
+}  // namespace jz

@@ -34,6 +34,7 @@ class Job:
     n_therm: int = 1000
     direction: int = 1
     traj0: int = 0
+    update: int = 0          # 0 checkerboard Metropolis, 1 Swendsen-Wang
 
     @property
     def sites(self) -> int:
@@ -73,6 +74,13 @@ def config2(n_traj: int = 16384) -> Workload:
     N = 1000, 2 sweeps/step, 16384 trajectories per l."""
     return Workload(f"2d_L64_scan_l0-30_N1000_x2_traj{n_traj}",
                     [Job(2, 64, 64, BETA_C_2D, l, 1000, 2, n_traj, seed=0) for l in range(31)])
+
+
+def config2_sw(n_traj: int = 16384) -> Workload:
+    """The 2D L = 64 scan of config2 with Swendsen-Wang cluster sweeps (the
+    update of the paper's own simulations, section 3) in place of Metropolis."""
+    return Workload(f"2d_L64_scan_l0-30_N1000_x2_traj{n_traj}_sw",
+                    [j.with_(update=1) for j in config2(n_traj).jobs])
 
 
 def config3(n_traj: int = 4096) -> Workload:
