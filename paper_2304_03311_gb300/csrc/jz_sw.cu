@@ -6,19 +6,25 @@
 //   lab[V]   int32 cluster labels (lab[i] <= i always: a forest whose roots are
 //            the smallest site index of their cluster)
 //   sp[VW]   spin bits, bit i of the lattice = 1 for spin -1
-//   fb[VW]   flip bits of the cluster roots of the current sweep
-// One sweep is three phases separated by CTA barriers:
-//   B  every site draws one Philox block (i, s, traj, dir<<1 | l<<2 | 2<<30);
+//   bx, bt, bg, by [VW]  bond bits of the current sweep by direction; bx
+//            doubles as the flip bits of the cluster roots, bt and bg as the
+//            warps' rings of 64 queued cluster roots
+// Warps work on chunks of 32 consecutive sites.  One sweep is four phases
+// separated by CTA barriers:
+//   B1 every site draws one Philox block (i, s, traj, dir<<1 | l<<2 | 2<<30);
 //      word w in {+x, +t same replica, +y, +t into replica r+1} activates that
 //      forward link when both spins are equal and the word is below the link's
-//      bond threshold floor(2^32 (1 - e^{-2K})); active links merge clusters by
-//      lock-free union with atomicMin (the larger root is hooked under the
-//      smaller one, so the root of a cluster is its smallest site index);
-//   C  path compression; each root draws Philox block (root, s, traj,
-//      dir<<1 | l<<2 | 3<<30) and its cluster flips iff the top bit of word 0
-//      is set (the warp assembles 32 roots' bits into one fb word);
-//   D  every site flips iff its root's fb bit is set (the warp assembles 32
-//      sites into one spin word) and resets its label for the next sweep.
+//      bond threshold floor(2^32 (1 - e^{-2K})).  +x bonds between lanes of
+//      one chunk form runs found by one ballot; each site's label is set to
+//      its run's first site.  The other active bonds become bits.
+//   B2 each recorded bond merges two clusters by lock-free union with
+//      atomicMin (the larger root is hooked under the smaller one, so the
+//      root of a cluster is its smallest site index);
+//   C  compression; the roots, queued 32 at a time, draw Philox block
+//      (root, s, traj, dir<<1 | l<<2 | 3<<30) and a cluster flips iff the top
+//      bit of its root's word 0 is set;
+//   D  every site flips iff its root's flip bit is set (a ballot assembles
+//      32 sites into one spin word).
 // The cluster partition, hence the minimum-index root of every cluster, does
 // not depend on the order of the unions, so the result is the same bit for bit
 // as a sequential union-find over the same bonds.
@@ -67,6 +73,13 @@ struct SwGeom {
     int G;        // Philox blocks per colour row of the hot start, ceil(L / 8)
     FastDiv dL, dLy;
 };
+
+// Words of the region holding bt and bg in phases B1, B2 and the warps' root
+// rings in phase C.
+__host__ __device__ inline int ring_words(int VW)
+{
+    return 2 * VW > (kSwThreads / 32) * 64 ? 2 * VW : (kSwThreads / 32) * 64;
+}
 
 struct Site {
     int x, y, t, r, row;
@@ -145,7 +158,12 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
     extern __shared__ uint32_t smem[];
     int* lab = (int*)smem;
     uint32_t* sp = smem + g.V;
-    uint32_t* fb = sp + g.VW;
+    uint32_t* bx = sp + g.VW;       // +x bonds not inside one warp chunk
+    uint32_t* bt = bx + g.VW;       // +t bonds inside one replica
+    uint32_t* bg = bt + g.VW;       // +t bonds into replica r+1
+    uint32_t* by = bt + ring_words(g.VW);   // +y bonds (3D)
+    uint32_t* fb = bx;              // root flip bits (phases C, D)
+    int* s_ring = (int*)bt;         // per warp a ring of 64 queued roots (phase C)
 
     // the job owning this CTA: the last j with jobs[j].cta0 <= blockIdx.x
     int lo = 0, hi = n_jobs - 1;
@@ -181,7 +199,6 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
             const uint4 u = philox_r0((uint32_t)(s.row * g.G + (h >> 2)), 0u, hi1, lo1,
                                       colour | c3 | (1u << 30), K);
             bit = (int)(word_of(u, h & 3) >> 31);
-            lab[i] = i;
         }
         const uint32_t m = __ballot_sync(0xFFFFFFFFu, bit);
         if (lane == 0) sp[base >> 5] = m;
@@ -217,83 +234,118 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
             t_glue = __ldg(&bonds[2 * k + 1]);
         }
         const uint32_t cb = c3 | (2u << 30);
-        // phase B: bonds and unions
-        for (int i = threadIdx.x; i < g.V; i += blockDim.x) {
-            const Site s = decode<D>(i, g);
-            const int si = spin_bit(sp, i);
-            int j[4];
-            uint32_t T[4];
-            j[0] = s.x == g.L - 1 ? i + 1 - g.L : i + 1;
-            T[0] = t_full;
-            j[2] = -1;
-            T[2] = 0;
-            if (D == 3) {
-                j[2] = s.y == g.Ly - 1 ? i + g.L - g.SL : i + g.L;
-                T[2] = t_full;
-            }
-            j[1] = -1;
-            T[1] = 0;
-            j[3] = -1;
-            T[3] = 0;
-            if (s.t != 0) {
-                j[1] = s.t == g.Lt - 1 ? i + g.SL - g.VR : i + g.SL;
-                T[1] = t_full;
-            } else {
-                const int js = i + g.SL;
-                const int jg = js + (s.r ? -g.VR : g.VR);
-                if (s.x > l) {
-                    j[1] = js;
-                    T[1] = t_full;
-                } else if (s.x < l) {
-                    j[3] = jg;
-                    T[3] = t_full;
-                } else {
-                    j[1] = js;
-                    T[1] = t_self;
-                    j[3] = jg;
-                    T[3] = t_glue;
-                }
-            }
-            bool any = false;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (j[q] >= 0 && (T[q] == 0 || spin_bit(sp, j[q]) != si)) j[q] = -1;
-                any |= j[q] >= 0;
-            }
-            if (!any) continue;
-            const uint4 u = philox_r0((uint32_t)i, (uint32_t)sw, hi1, lo1, cb, K);
-            if (j[0] >= 0 && u.x < T[0]) merge(lab, i, j[0]);
-            if (j[1] >= 0 && u.y < T[1]) merge(lab, i, j[1]);
-            if (D == 3 && j[2] >= 0 && u.z < T[2]) merge(lab, i, j[2]);
-            if (j[3] >= 0 && u.w < T[3]) merge(lab, i, j[3]);
-        }
-        __syncthreads();
-        // phase C: compression and the flip bit of every root
-        const uint32_t cf = c3 | (3u << 30);
+        // phase B1: bond draws.  A +x bond between two lanes of one warp
+        // chunk joins a run of consecutive sites; every site of a run gets the
+        // run's first site as its label (a star).  All other active bonds are
+        // recorded as bits for phase B2.
         for (int base = warp * 32; base < g.V; base += chunk) {
             const int i = base + lane;
-            int f = 0;
+            bool ax = false, at = false, ay = false, ag = false, last = true;
             if (i < g.V) {
-                const int root = find_root_ro((volatile int*)lab, i);
-                if (root == i) {
-                    const uint4 u = philox_r0((uint32_t)i, (uint32_t)sw, hi1, lo1, cf, K);
-                    f = (int)(u.x >> 31);
+                const Site s = decode<D>(i, g);
+                const int si = spin_bit(sp, i);
+                last = s.x == g.L - 1;
+                const int jx = last ? i + 1 - g.L : i + 1;
+                int jt = -1, jg = -1, jy = -1;
+                uint32_t Tt = t_full, Tg = 0;
+                if (s.t != 0) {
+                    jt = s.t == g.Lt - 1 ? i + g.SL - g.VR : i + g.SL;
                 } else {
-                    ((volatile int*)lab)[i] = root;
+                    const int js = i + g.SL;
+                    const int jgl = js + (s.r ? -g.VR : g.VR);
+                    if (s.x > l) {
+                        jt = js;
+                    } else if (s.x < l) {
+                        jg = jgl;
+                        Tg = t_full;
+                    } else {
+                        jt = js;
+                        Tt = t_self;
+                        jg = jgl;
+                        Tg = t_glue;
+                    }
                 }
+                if (D == 3) jy = s.y == g.Ly - 1 ? i + g.L - g.SL : i + g.L;
+                const uint4 u = philox_r0((uint32_t)i, (uint32_t)sw, hi1, lo1, cb, K);
+                ax = u.x < t_full && spin_bit(sp, jx) == si;
+                at = jt >= 0 && u.y < Tt && spin_bit(sp, jt) == si;
+                if (D == 3) ay = u.z < t_full && spin_bit(sp, jy) == si;
+                ag = jg >= 0 && u.w < Tg && spin_bit(sp, jg) == si;
             }
-            const uint32_t m = __ballot_sync(0xFFFFFFFFu, f);
-            if (lane == 0) fb[base >> 5] = m;
+            const bool inw = ax && lane != 31 && !last;   // bond to the next lane's site
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, inw);
+            const uint32_t brk = ~m & ((1u << lane) - 1u);
+            const int start = brk ? 32 - __clz(brk) : 0;
+            if (i < g.V) lab[i] = base + start;
+            const uint32_t wx = __ballot_sync(0xFFFFFFFFu, ax && !inw);
+            const uint32_t wt = __ballot_sync(0xFFFFFFFFu, at);
+            const uint32_t wg = __ballot_sync(0xFFFFFFFFu, ag);
+            const uint32_t wy = D == 3 ? __ballot_sync(0xFFFFFFFFu, ay) : 0u;
+            if (lane == 0) {
+                const int q = base >> 5;
+                bx[q] = wx;
+                bt[q] = wt;
+                bg[q] = wg;
+                if (D == 3) by[q] = wy;
+            }
         }
         __syncthreads();
-        // phase D: flip the clusters, reset the labels
+        // phase B2: the recorded bonds merge clusters
+        for (int base = warp * 32; base < g.V; base += chunk) {
+            const int i = base + lane;
+            const int q = base >> 5;
+            const uint32_t wx = bx[q], wt = bt[q], wg = bg[q];
+            const uint32_t wy = D == 3 ? by[q] : 0u;
+            __syncwarp();
+            if (lane == 0) bx[q] = 0u;          // bx doubles as the flip bits of phase C
+            const uint32_t me = 1u << lane;
+            if (((wx | wt | wg | wy) & me) == 0u) continue;
+            const Site s = decode<D>(i, g);
+            if (wx & me) merge(lab, i, s.x == g.L - 1 ? i + 1 - g.L : i + 1);
+            if (wt & me) merge(lab, i, s.t == g.Lt - 1 ? i + g.SL - g.VR : i + g.SL);
+            if (wg & me) merge(lab, i, i + g.SL + (s.r ? -g.VR : g.VR));
+            if (D == 3 && (wy & me)) merge(lab, i, s.y == g.Ly - 1 ? i + g.L - g.SL : i + g.L);
+        }
+        __syncthreads();
+        // phase C: compression; the roots are queued per warp and draw their
+        // flip bits 32 at a time
+        const uint32_t cf = c3 | (3u << 30);
+        int* ring = s_ring + warp * 64;
+        int head = 0, n_pend = 0;
+        for (int base = warp * 32; base < g.V; base += chunk) {
+            const int i = base + lane;
+            bool is_root = false;
+            if (i < g.V) {
+                const int root = find_root_ro((volatile int*)lab, i);
+                is_root = root == i;
+                if (!is_root) lab[i] = root;
+            }
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, is_root);
+            if (is_root) ring[(head + n_pend + __popc(m & ((1u << lane) - 1u))) & 63] = i;
+            n_pend += __popc(m);
+            __syncwarp();
+            if (n_pend >= 32) {
+                const int r = ring[(head + lane) & 63];
+                const uint4 u = philox_r0((uint32_t)r, (uint32_t)sw, hi1, lo1, cf, K);
+                if (u.x >> 31) atomicOr(&fb[r >> 5], 1u << (r & 31));
+                head += 32;
+                n_pend -= 32;
+                __syncwarp();
+            }
+        }
+        if (lane < n_pend) {
+            const int r = ring[(head + lane) & 63];
+            const uint4 u = philox_r0((uint32_t)r, (uint32_t)sw, hi1, lo1, cf, K);
+            if (u.x >> 31) atomicOr(&fb[r >> 5], 1u << (r & 31));
+        }
+        __syncthreads();
+        // phase D: flip the clusters
         for (int base = warp * 32; base < g.V; base += chunk) {
             const int i = base + lane;
             int f = 0;
             if (i < g.V) {
                 const int root = lab[i];
                 f = (int)((fb[root >> 5] >> (root & 31)) & 1);
-                lab[i] = i;
             }
             const uint32_t m = __ballot_sync(0xFFFFFFFFu, f);
             if (lane == 0) sp[base >> 5] ^= m;
@@ -331,7 +383,9 @@ SwGeom make_swgeom(int D, const Geom& geo)
 size_t sw_smem_bytes(const Geom& geo)
 {
     const size_t V = (size_t)2 * geo.Lt * geo.Ly * geo.L;
-    return V * sizeof(int) + 2 * ((V + 31) / 32) * sizeof(uint32_t);
+    const int VW = (int)((V + 31) / 32);
+    const size_t words = 2 * (size_t)VW + ring_words(VW) + (geo.Ly > 1 ? VW : 0);
+    return V * sizeof(int) + words * sizeof(uint32_t);
 }
 
 cudaError_t launch_sw(int D, const Geom& geo, const PhiloxKeys& K, const JobDesc* jobs,
