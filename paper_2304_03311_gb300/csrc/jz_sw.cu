@@ -6,9 +6,9 @@
 //   lab[V]   int32 cluster labels (lab[i] <= i always: a forest whose roots are
 //            the smallest site index of their cluster)
 //   sp[VW]   spin bits, bit i of the lattice = 1 for spin -1
-//   bx, bt, bg, by [VW]  bond bits of the current sweep by direction; bx
-//            doubles as the flip bits of the cluster roots, bt and bg as the
-//            warps' rings of 64 queued cluster roots
+//   bx, bt, bg, by [VW]  bond bits of the current sweep by direction; bt
+//            doubles as the warps' rings of 32 queued cluster roots, bg as the
+//            roots' flip bits
 // Warps work on chunks of 32 consecutive sites.  One sweep is four phases
 // separated by CTA barriers:
 //   B1 every site draws one Philox block (i, s, traj, dir<<1 | l<<2 | 2<<30);
@@ -20,9 +20,9 @@
 //   B2 each recorded bond merges two clusters by lock-free union with
 //      atomicMin (the larger root is hooked under the smaller one, so the
 //      root of a cluster is its smallest site index);
-//   C  compression; the roots, queued 32 at a time, draw Philox block
-//      (root, s, traj, dir<<1 | l<<2 | 3<<30) and a cluster flips iff the top
-//      bit of its root's word 0 is set;
+//   C  every site stores its root; the roots, queued 32 at a time, draw
+//      Philox block (root, s, traj, dir<<1 | l<<2 | 3<<30) and a cluster
+//      flips iff the top bit of its root's word 0 is set;
 //   D  every site flips iff its root's flip bit is set (a ballot assembles
 //      32 sites into one spin word).
 // The cluster partition, hence the minimum-index root of every cluster, does
@@ -74,11 +74,11 @@ struct SwGeom {
     FastDiv dL, dLy;
 };
 
-// Words of the region holding bt and bg in phases B1, B2 and the warps' root
-// rings in phase C.
+// Words of the region holding bt in phases B1, B2 and the warps' root rings
+// in phase C.
 __host__ __device__ inline int ring_words(int VW)
 {
-    return 2 * VW > (kSwThreads / 32) * 64 ? 2 * VW : (kSwThreads / 32) * 64;
+    return VW > kSwThreads ? VW : kSwThreads;
 }
 
 struct Site {
@@ -158,12 +158,12 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
     extern __shared__ uint32_t smem[];
     int* lab = (int*)smem;
     uint32_t* sp = smem + g.V;
-    uint32_t* bx = sp + g.VW;       // +x bonds not inside one warp chunk
+    uint32_t* bx = sp + g.VW;       // +x bonds leaving a warp chunk or its row
     uint32_t* bt = bx + g.VW;       // +t bonds inside one replica
-    uint32_t* bg = bt + g.VW;       // +t bonds into replica r+1
-    uint32_t* by = bt + ring_words(g.VW);   // +y bonds (3D)
-    uint32_t* fb = bx;              // root flip bits (phases C, D)
-    int* s_ring = (int*)bt;         // per warp a ring of 64 queued roots (phase C)
+    uint32_t* bg = bt + ring_words(g.VW);   // +t bonds into replica r+1
+    uint32_t* by = bg + g.VW;       // +y bonds (3D)
+    uint32_t* fb = bg;              // root flip bits (phases C, D)
+    int* s_ring = (int*)bt;         // per warp a ring of 32 queued roots (phase C)
 
     // the job owning this CTA: the last j with jobs[j].cta0 <= blockIdx.x
     int lo = 0, hi = n_jobs - 1;
@@ -290,14 +290,15 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
             }
         }
         __syncthreads();
-        // phase B2: the recorded bonds merge clusters
+        // phase B2: the recorded bonds merge clusters (+x bonds inside a
+        // chunk are already joined by the run labels)
         for (int base = warp * 32; base < g.V; base += chunk) {
             const int i = base + lane;
             const int q = base >> 5;
             const uint32_t wx = bx[q], wt = bt[q], wg = bg[q];
             const uint32_t wy = D == 3 ? by[q] : 0u;
             __syncwarp();
-            if (lane == 0) bx[q] = 0u;          // bx doubles as the flip bits of phase C
+            if (lane == 0) bg[q] = 0u;          // bg doubles as the flip bits of phase C
             const uint32_t me = 1u << lane;
             if (((wx | wt | wg | wy) & me) == 0u) continue;
             const Site s = decode<D>(i, g);
@@ -307,11 +308,11 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
             if (D == 3 && (wy & me)) merge(lab, i, s.y == g.Ly - 1 ? i + g.L - g.SL : i + g.L);
         }
         __syncthreads();
-        // phase C: compression; the roots are queued per warp and draw their
-        // flip bits 32 at a time
+        // phase C: every site stores its root; the roots are queued per warp
+        // and draw their flip bits 32 at a time
         const uint32_t cf = c3 | (3u << 30);
-        int* ring = s_ring + warp * 64;
-        int head = 0, n_pend = 0;
+        int* ring = s_ring + warp * 32;
+        int n_pend = 0;
         for (int base = warp * 32; base < g.V; base += chunk) {
             const int i = base + lane;
             bool is_root = false;
@@ -321,20 +322,23 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
                 if (!is_root) lab[i] = root;
             }
             const uint32_t m = __ballot_sync(0xFFFFFFFFu, is_root);
-            if (is_root) ring[(head + n_pend + __popc(m & ((1u << lane) - 1u))) & 63] = i;
+            const int rank = __popc(m & ((1u << lane) - 1u));
+            const int room = 32 - n_pend;
+            if (is_root && rank < room) ring[n_pend + rank] = i;
             n_pend += __popc(m);
-            __syncwarp();
             if (n_pend >= 32) {
-                const int r = ring[(head + lane) & 63];
+                __syncwarp();
+                const int r = ring[lane];
                 const uint4 u = philox_r0((uint32_t)r, (uint32_t)sw, hi1, lo1, cf, K);
                 if (u.x >> 31) atomicOr(&fb[r >> 5], 1u << (r & 31));
-                head += 32;
-                n_pend -= 32;
                 __syncwarp();
+                if (is_root && rank >= room) ring[rank - room] = i;
+                n_pend -= 32;
             }
         }
+        __syncwarp();
         if (lane < n_pend) {
-            const int r = ring[(head + lane) & 63];
+            const int r = ring[lane];
             const uint4 u = philox_r0((uint32_t)r, (uint32_t)sw, hi1, lo1, cf, K);
             if (u.x >> 31) atomicOr(&fb[r >> 5], 1u << (r & 31));
         }
@@ -384,7 +388,7 @@ size_t sw_smem_bytes(const Geom& geo)
 {
     const size_t V = (size_t)2 * geo.Lt * geo.Ly * geo.L;
     const int VW = (int)((V + 31) / 32);
-    const size_t words = 2 * (size_t)VW + ring_words(VW) + (geo.Ly > 1 ? VW : 0);
+    const size_t words = 3 * (size_t)VW + ring_words(VW) + (geo.Ly > 1 ? VW : 0);
     return V * sizeof(int) + words * sizeof(uint32_t);
 }
 
