@@ -232,14 +232,61 @@ def _threshold(beta: float, m: int, n_step: int | None) -> int:
     return min(int(math.floor(math.ldexp(math.exp(-x), 32))), 2 ** 32 - 1)
 
 
+class _Schedule:
+    """Which couplings of the switched columns (x = l, y) move at protocol
+    step k.  Protocol 1 (section 3): every column together, lambda_{k+1} =
+    (k+1)/N.  Protocol 2 (Appendix B): column y alone during the m = N/L_y
+    steps y m .. (y+1) m - 1, with lambda = (k + 1 - y m)/m; columns already
+    switched sit at the end geometry, the others at the start geometry."""
+
+    def __init__(self, d, L, n_step, direction, protocol):
+        self.L, self.L_y = L, (L if d == 3 else 1)
+        self.dir, self.protocol = direction, protocol
+        if protocol == 2 and n_step % self.L_y:
+            raise ValueError("protocol 2 needs n_step to be a multiple of L_y")
+        self.m = n_step // self.L_y if protocol == 2 else n_step
+
+    def site_y(self, i: int) -> int:
+        return (int(i) // self.L) % self.L_y
+
+    def column(self, y: int, k) -> str:
+        """'self', 'glue' or 'switching' for column y at step k (None: the
+        start geometry, lambda = 0 forward, 1 reverse)."""
+        if k is None:
+            return "self" if self.dir > 0 else "glue"
+        if self.protocol != 2:
+            return "switching"
+        active = k // self.m
+        if y == active:
+            return "switching"
+        return "glue" if (y < active) == (self.dir > 0) else "self"
+
+    def weights(self, k: int):
+        """(den, w_self, w_glue): the switching column's couplings at step k
+        are beta w_self/den and beta w_glue/den (lambda_{k+1})."""
+        kp = k + 1 - (k // self.m) * self.m
+        den = self.m
+        return (den, den - kp, kp) if self.dir > 0 else (den, kp, den - kp)
+
+    def work_rows(self, k: int, n_links: int, lower_sites) -> tuple:
+        """Mask of the switched links whose couplings move at step k and the
+        factor that puts their work in units of beta/N."""
+        if self.protocol != 2:
+            return np.ones(n_links, dtype=bool), 1
+        active = k // self.m
+        ys = np.array([self.site_y(i) for i in lower_sites], dtype=np.int64)
+        return ys == active, self.L_y
+
+
 class _Dynamics:
     """Single-site Metropolis probabilities of every site in every state of a
     tiny replica lattice, at the start geometry or at protocol step k."""
 
-    def __init__(self, d, L, L_t, l, beta, n_step, direction, quantised):
+    def __init__(self, d, L, L_t, l, beta, n_step, direction, quantised, protocol=1):
         self.d, self.L, self.L_t, self.l = d, L, L_t, l
         self.beta, self.N, self.dir = beta, n_step, direction
         self.quantised = quantised
+        self.sched = _Schedule(d, L, n_step, direction, protocol)
         self._cache = {}
         self.links = replica_links(d, L, L_t, l)
         self.V = self.links.n_sites
@@ -273,10 +320,10 @@ class _Dynamics:
         for j in self.nb["full"][i]:
             a += s[:, i] * s[:, j]
         special = bool(self.nb["self"][i])
-        if special and k is None:
-            # the switched column is a bulk site at the start geometry
-            key = "self" if self.dir > 0 else "glue"
-            for j in self.nb[key][i]:
+        col = self.sched.column(self.sched.site_y(i), k) if special else None
+        if special and col != "switching":
+            # a column at the start or end geometry is a bulk site
+            for j in self.nb[col][i]:
                 a += s[:, i] * s[:, j]
             special = False
         if not special:
@@ -287,12 +334,10 @@ class _Dynamics:
             (js,), (jg,) = self.nb["self"][i], self.nb["glue"][i]
             b = s[:, i] * s[:, js]
             c = s[:, i] * s[:, jg]
-            kp = k + 1                       # the update of step k uses lambda_{k+1}
-            w_self = self.N - kp if self.dir > 0 else kp
-            w_glue = kp if self.dir > 0 else self.N - kp
-            m = a * self.N + b * w_self + c * w_glue
-            x = (2.0 * self.beta * m) / self.N
-            nstep = self.N
+            den, w_self, w_glue = self.sched.weights(k)   # step k updates at lambda_{k+1}
+            m = a * den + b * w_self + c * w_glue
+            x = (2.0 * self.beta * m) / den
+            nstep = den
         if self.quantised:
             um, inv = np.unique(m, return_inverse=True)
             pu = np.array([1.0 if mm <= 0 else _threshold(self.beta, int(mm), nstep) / 2.0 ** 32
@@ -313,12 +358,12 @@ class _Dynamics:
                 f = f * (1.0 - p) + (f * p)[..., partner]
         return f
 
-    def work_increment(self) -> np.ndarray:
-        """dE(state) with dW_k = (beta/N) dE = H_{lambda_{k+1}} - H_{lambda_k}
-        (Appendix A, eq. work_in_one_MC_step): sum over the switched links of
-        (self - glue) bond products, sign flipped for the reverse protocol."""
-        e = _bond_sums(self.sigma, self.links.self_) - _bond_sums(self.sigma, self.links.glue)
-        return e if self.dir > 0 else -e
+    def work_increment(self, k: int = 0) -> np.ndarray:
+        """dE(state) with dW_k = (beta/N) dE = H_{k+1} - H_k (Appendix A, eq.
+        work_in_one_MC_step): sum over the switched links that move at step k
+        of (self - glue) bond products, in units of beta/N, sign flipped for
+        the reverse protocol."""
+        return _work_increment(self.sigma, self.links, self.sched, k)
 
     def energy(self, lam: float) -> np.ndarray:
         lk = self.links
@@ -326,8 +371,26 @@ class _Dynamics:
                  + lam * _bond_sums(self.sigma, lk.glue))
 
 
+def _work_increment(sigma, links, sched, k):
+    sel, factor = sched.work_rows(k, len(links.self_), links.self_[:, 0])
+    e = factor * (_bond_sums(sigma, links.self_[sel]) - _bond_sums(sigma, links.glue[sel]))
+    return e if sched.dir > 0 else -e
+
+
+def _propagate(F, de):
+    """Shift the work axis of F by dE(state) (W index = W_int + offset)."""
+    G = np.zeros_like(F)
+    for dv in np.unique(de):
+        sel = de == dv
+        if dv >= 0:
+            G[dv:, sel] += F[:F.shape[0] - dv, sel]
+        else:
+            G[:dv, sel] += F[-dv:, sel]
+    return G
+
+
 def exact_path_measure(d, L, L_t, l, beta, n_step, n_sweep, n_therm, *, direction=1,
-                       quantised=True, start="hot"):
+                       quantised=True, start="hot", protocol=1):
     """Exact joint law of (W_int, final state) of the non-equilibrium dynamics.
 
     start="hot": uniform start (independent random spins) followed by n_therm
@@ -336,7 +399,7 @@ def exact_path_measure(d, L, L_t, l, beta, n_step, n_sweep, n_therm, *, directio
     eq. equilibrium_distribution), for the Jarzynski identity.
     Returns (w_values, F) with F[w_index, state] the probability.
     """
-    dyn = _Dynamics(d, L, L_t, l, beta, n_step, direction, quantised)
+    dyn = _Dynamics(d, L, L_t, l, beta, n_step, direction, quantised, protocol)
     n_states = 1 << dyn.V
     lam0 = 0.0 if direction > 0 else 1.0
     if start == "hot":
@@ -347,19 +410,12 @@ def exact_path_measure(d, L, L_t, l, beta, n_step, n_sweep, n_therm, *, directio
         e = -beta * dyn.energy(lam0)
         w = np.exp(e - e.max())
         f = w / w.sum()
-    de = dyn.work_increment()
-    wmax = int(np.max(np.abs(de))) * n_step
+    des = [dyn.work_increment(k) for k in range(n_step)]
+    wmax = sum(int(np.max(np.abs(de))) for de in des)
     F = np.zeros((2 * wmax + 1, n_states))
     F[wmax] = f
     for k in range(n_step):
-        G = np.zeros_like(F)
-        for dv in np.unique(de):
-            sel = de == dv
-            if dv >= 0:
-                G[dv:, sel] += F[:F.shape[0] - dv, sel]
-            else:
-                G[:dv, sel] += F[-dv:, sel]
-        F = G
+        F = _propagate(F, des[k])
         for _ in range(n_sweep):
             F = dyn.sweep(F, k)
     return np.arange(-wmax, wmax + 1), F
@@ -382,8 +438,9 @@ class _SWDynamics:
     T[s, s'] = sum over bond sets B of P(B | s) 2^{-nc(B)} [s' = s with some
     clusters of B flipped], computed by enumerating all bond sets."""
 
-    def __init__(self, d, L, L_t, l, beta, n_step, direction, quantised):
+    def __init__(self, d, L, L_t, l, beta, n_step, direction, quantised, protocol=1):
         self.beta, self.N, self.dir, self.quantised = beta, n_step, direction, quantised
+        self.sched = _Schedule(d, L, n_step, direction, protocol)
         self.links = replica_links(d, L, L_t, l)
         self.V = self.links.n_sites
         if self.V > 10:
@@ -391,28 +448,29 @@ class _SWDynamics:
         lk = self.links
         self.pairs = np.concatenate([lk.full, lk.self_, lk.glue])
         self.kind = np.array([0] * len(lk.full) + [1] * len(lk.self_) + [2] * len(lk.glue))
+        self.link_y = np.array([self.sched.site_y(i) for i in self.pairs[:, 0]])
         self.sigma = _spins_of_states(self.V).astype(np.int64)
         self.aligned = (self.sigma[:, self.pairs[:, 0]] == self.sigma[:, self.pairs[:, 1]])
         self._cache = {}
 
-    def _x(self, kind, k):
-        """x = 2K of a link class at protocol step k (None: thermalisation)."""
+    def _x(self, kind, k, y):
+        """x = 2K of a link of class kind in column y at protocol step k (None:
+        thermalisation at the start geometry)."""
         b = self.beta
         if kind == 0:
             return 2.0 * b
-        if k is None:   # start geometry: forward self-linked, reverse glued
-            full = (kind == 1) == (self.dir > 0)
-            return 2.0 * b if full else 0.0
-        kp = k + 1
-        w_self = self.N - kp if self.dir > 0 else kp
-        w_glue = kp if self.dir > 0 else self.N - kp
+        col = self.sched.column(y, k)
+        if col != "switching":
+            return 2.0 * b if col == ("self" if kind == 1 else "glue") else 0.0
+        den, w_self, w_glue = self.sched.weights(k)
         w = w_self if kind == 1 else w_glue
-        return (2.0 * b * float(w)) / float(self.N)
+        return (2.0 * b * float(w)) / float(den)
 
     def kernel(self, k):
         if k in self._cache:
             return self._cache[k]
-        p = np.array([_bond_prob(self._x(kd, k), self.quantised) for kd in self.kind])
+        p = np.array([_bond_prob(self._x(kd, k, y), self.quantised)
+                      for kd, y in zip(self.kind, self.link_y)])
         live = np.nonzero(p > 0)[0]
         pairs, pl = self.pairs[live], p[live]
         nl, n_states, V = len(live), 1 << self.V, self.V
@@ -458,9 +516,8 @@ class _SWDynamics:
         self._cache[k] = T
         return T
 
-    def work_increment(self):
-        e = _bond_sums(self.sigma, self.links.self_) - _bond_sums(self.sigma, self.links.glue)
-        return e if self.dir > 0 else -e
+    def work_increment(self, k: int = 0):
+        return _work_increment(self.sigma, self.links, self.sched, k)
 
     def energy(self, lam):
         lk = self.links
@@ -469,11 +526,11 @@ class _SWDynamics:
 
 
 def exact_path_measure_sw(d, L, L_t, l, beta, n_step, n_sweep, n_therm, *, direction=1,
-                          quantised=True, start="hot"):
+                          quantised=True, start="hot", protocol=1):
     """Exact joint law of (W_int, final state) of the non-equilibrium dynamics
     with Swendsen-Wang updates (same protocol as exact_path_measure: work
     before each update, update at lambda_{k+1}).  Returns (w_values, F)."""
-    dyn = _SWDynamics(d, L, L_t, l, beta, n_step, direction, quantised)
+    dyn = _SWDynamics(d, L, L_t, l, beta, n_step, direction, quantised, protocol)
     n_states = 1 << dyn.V
     lam0 = 0.0 if direction > 0 else 1.0
     if start == "hot":
@@ -485,19 +542,12 @@ def exact_path_measure_sw(d, L, L_t, l, beta, n_step, n_sweep, n_therm, *, direc
         e = -beta * dyn.energy(lam0)
         w = np.exp(e - e.max())
         f = w / w.sum()
-    de = dyn.work_increment()
-    wmax = int(np.max(np.abs(de))) * n_step
+    des = [dyn.work_increment(k) for k in range(n_step)]
+    wmax = sum(int(np.max(np.abs(de))) for de in des)
     F = np.zeros((2 * wmax + 1, n_states))
     F[wmax] = f
     for k in range(n_step):
-        G = np.zeros_like(F)
-        for dv in np.unique(de):
-            sel = de == dv
-            if dv >= 0:
-                G[dv:, sel] += F[:F.shape[0] - dv, sel]
-            else:
-                G[:dv, sel] += F[-dv:, sel]
-        F = G
+        F = _propagate(F, des[k])
         Tk = dyn.kernel(k)
         for _ in range(n_sweep):
             F = F @ Tk

@@ -27,6 +27,12 @@
  *   dE_k = sum_{r,y} s^r(l,y,0) [s^r(l,y,1) - s^{r+1}(l,y,1)] so that
  *   W = (beta / N) W_int; the reverse protocol (lambda from 1 to 0, start at
  *   geometry l+1) flips the sign of dE_k.
+ *   Protocol 2 (Appendix B, "protocol 2"; 3D): the L_y switched columns
+ *   (x = l, y) are switched one after another, column y during the m = N/L_y
+ *   steps y m .. (y+1) m - 1 with its own lambda = (k + 1 - y m)/m; columns
+ *   already switched keep the end geometry, the others the start geometry.
+ *   Then dE_k sums over the active column only and W_int = L_y sum_k dE_k,
+ *   so again W = (beta / N) W_int.  In 2D (L_y = 1) it is protocol 1.
  *
  * Bit-level conventions (not fixed by the paper; shared only as a written
  * contract with the CUDA path, never as code):
@@ -70,7 +76,9 @@
  *   9 switched bonds of step k at lambda_k
  *  10 each site flips on its own draw instead of its cluster's
  *  11 bonds also between unequal spins
- *  12 glued links of region A stay inside one replica */
+ *  12 glued links of region A stay inside one replica
+ * and in protocol 2:
+ *  13 the work of the active column not scaled by L_y */
 #ifndef ORACLE_MUTANT
 #define ORACLE_MUTANT 0
 #endif
@@ -155,12 +163,15 @@ static int wrap(int v, int n) { return ((v % n) + n) % n; }
 /* Classes of a link seen from a site. */
 enum { FULL = 0, SELF = 1, GLUE = 2 };
 
+/* State of a switched column's pair of time links across the cut. */
+enum { COL_SELF = 0, COL_GLUED = 1, COL_SWITCHING = 2 };
+
 /* Lists the 2d links of site (r,t,y,x): nbr[] = partner site, cls[] = FULL for a
  * beta link, SELF / GLUE for the two switched links of the column x = l.
- * protocol = 0 during thermalisation (switched column reduced to a bulk site),
- * 1 during the non-equilibrium protocol.  Returns the number of entries (2d, or
- * 2d+1 for a switched site, which has both a SELF and a GLUE partner). */
-static int links_of(const geom_t *g, int r, int t, int y, int x, int protocol,
+ * col = the state of the column (x = l, y): COL_SELF or COL_GLUED make it a bulk
+ * site linked inside its replica or to the next one, COL_SWITCHING gives it both
+ * links.  Returns the number of entries (2d, or 2d+1 for a switched site). */
+static int links_of(const geom_t *g, int r, int t, int y, int x, int col,
                     int nbr[8], int cls[8])
 {
     int k = 0;
@@ -193,11 +204,10 @@ static int links_of(const geom_t *g, int r, int t, int y, int x, int protocol,
             nbr[k] = ORACLE_MUTANT == 3 ? self_site : glue_site; cls[k++] = FULL;
         } else if (x > g->l) {
             nbr[k] = self_site; cls[k++] = FULL;
-        } else if (!protocol) {
-            /* thermalisation at the start geometry: forward starts at
-             * lambda = 0 (self-linked), reverse at lambda = 1 (glued) */
-            nbr[k] = (g->dir > 0) != (ORACLE_MUTANT == 4) ? self_site : glue_site;
-            cls[k++] = FULL;
+        } else if (col == COL_SELF) {
+            nbr[k] = self_site; cls[k++] = FULL;
+        } else if (col == COL_GLUED) {
+            nbr[k] = glue_site; cls[k++] = FULL;
         } else {
             nbr[k] = self_site; cls[k++] = SELF;
             nbr[k] = glue_site; cls[k++] = GLUE;
@@ -211,6 +221,8 @@ typedef struct {
     geom_t g;
     double beta;
     int n_step, n_sweep, n_therm;
+    int prot;             /* 1 all columns together, 2 one column y at a time */
+    int m;                /* protocol 2: steps per column, N / L_y; protocol 1: N */
     int update;           /* 0 checkerboard Metropolis, 1 Swendsen-Wang */
     uint32_t key[2];
     uint32_t bulk_T[8];   /* indexed by m/2 for m = 2, 4, ..., 2d */
@@ -246,18 +258,38 @@ static uint32_t word_for(const run_t *R, int colour, int phase, int sweep,
 
 static int colour_of(int t, int y, int x) { return (x + y + t) & 1; }
 
+/* State of the switched column (x = l, y) at protocol step k (k < 0: the start
+ * geometry, lambda = 0 forward / 1 reverse). */
+static int column_state(const run_t *R, int y, int k)
+{
+    const geom_t *g = &R->g;
+    if (k < 0) return (g->dir > 0) != (ORACLE_MUTANT == 4) ? COL_SELF : COL_GLUED;
+    if (R->prot != 2) return COL_SWITCHING;
+    int active = k / R->m;
+    if (y == active) return COL_SWITCHING;
+    /* columns already switched hold the end geometry, the others the start */
+    int at_end = y < active;
+    return at_end == (g->dir > 0) ? COL_GLUED : COL_SELF;
+}
+
+/* Weights of the switching column at step k, in units of 1/den:
+ * lambda_{k+1} = kp/den with kp the step's index inside its column's run. */
+static void step_weights(const run_t *R, int k, long long *den, long long *w_self,
+                         long long *w_glue)
+{
+    long long m = R->prot == 2 ? R->m : R->n_step;
+    long long kp = (ORACLE_MUTANT == 1 ? k : k + 1) - (long long)(k / m) * m * (R->prot == 2);
+    *den = m;
+    *w_self = R->g.dir > 0 ? m - kp : kp;
+    *w_glue = R->g.dir > 0 ? kp : m - kp;
+}
+
 /* One checkerboard sweep at protocol step k (k < 0: thermalisation). */
 static void sweep(const run_t *R, int8_t *s, long long traj, int sweep_index, int k)
 {
     const geom_t *g = &R->g;
-    int protocol = k >= 0;
-    long long N = R->n_step;
-    long long w_self = 0, w_glue = 0;
-    if (protocol) {
-        long long kp = ORACLE_MUTANT == 1 ? k : k + 1; /* step k updates at lambda_{k+1} */
-        w_self = g->dir > 0 ? N - kp : kp;
-        w_glue = g->dir > 0 ? kp : N - kp;
-    }
+    long long N = 1, w_self = 0, w_glue = 0;   /* step k updates at lambda_{k+1} */
+    if (k >= 0) step_weights(R, k, &N, &w_self, &w_glue);
     for (int colour = 0; colour < 2; ++colour) {
         for (int r = 0; r < g->n; ++r)
         for (int t = 0; t < g->Lt; ++t)
@@ -266,7 +298,7 @@ static void sweep(const run_t *R, int8_t *s, long long traj, int sweep_index, in
             if (colour_of(t, y, x) != colour) continue;
             int i = site_of(g, r, t, y, x);
             int nbr[8], cls[8];
-            int nl = links_of(g, r, t, y, x, protocol, nbr, cls);
+            int nl = links_of(g, r, t, y, x, column_state(R, y, k), nbr, cls);
             int a = 0, b = 0, c = 0, special = 0;
             for (int j = 0; j < nl; ++j) {
                 int prod = s[i] * s[nbr[j]];
@@ -334,7 +366,6 @@ static void sw_sweep(const run_t *R, int8_t *s, int *parent, long long traj, int
 {
     const geom_t *g = &R->g;
     const int V = 2 * g->Lt * g->Ly * g->L;
-    const int protocol = k >= 0;
     for (int i = 0; i < V; ++i) parent[i] = i;
     for (int r = 0; r < g->n; ++r)
     for (int t = 0; t < g->Lt; ++t)
@@ -361,9 +392,10 @@ static void sw_sweep(const run_t *R, int8_t *s, int *parent, long long traj, int
                 j[1] = self_site; T[1] = R->bond_full;
             } else if (x < g->l) {
                 j[3] = ORACLE_MUTANT == 12 ? self_site : glue_site; T[3] = R->bond_full;
-            } else if (!protocol) {
-                if (g->dir > 0) { j[1] = self_site; T[1] = R->bond_full; }
-                else { j[3] = glue_site; T[3] = R->bond_full; }
+            } else if (column_state(R, y, k) == COL_SELF) {
+                j[1] = self_site; T[1] = R->bond_full;
+            } else if (column_state(R, y, k) == COL_GLUED) {
+                j[3] = glue_site; T[3] = R->bond_full;
             } else {
                 j[1] = self_site; T[1] = R->bond_self[k];
                 j[3] = glue_site; T[3] = R->bond_glue[k];
@@ -383,18 +415,22 @@ static void sw_sweep(const run_t *R, int8_t *s, int *parent, long long traj, int
 }
 
 /* dE_k = H_{lambda_{k+1}} - H_{lambda_k} on the current configuration, in
- * units of beta / N (Appendix A, eq. work_in_one_MC_step). */
-static long long work_increment(const run_t *R, const int8_t *s)
+ * units of beta / N (Appendix A, eq. work_in_one_MC_step): every column moves
+ * by 1/N in protocol 1; in protocol 2 only the active column moves, by
+ * 1/m = L_y/N. */
+static long long work_increment(const run_t *R, const int8_t *s, int k)
 {
     const geom_t *g = &R->g;
     long long e = 0;
     for (int r = 0; r < g->n; ++r)
     for (int y = 0; y < g->Ly; ++y) {
+        if (R->prot == 2 && y != k / R->m) continue;
         int lo = site_of(g, r, 0, y, g->l);
         int up_self = site_of(g, r, 1, y, g->l);
         int up_glue = site_of(g, wrap(r + 1, g->n), 1, y, g->l);
         e += (long long)s[lo] * (s[up_self] - s[up_glue]);
     }
+    if (R->prot == 2 && ORACLE_MUTANT != 13) e *= g->Ly;
     return (g->dir > 0) != (ORACLE_MUTANT == 6) ? e : -e;
 }
 
@@ -423,10 +459,10 @@ static long long run_trajectory(const run_t *R, long long traj, int8_t *s, int *
     for (int i = 0; i < R->n_therm; ++i) update(R, s, parent, traj, i, -1);
     long long w = 0;
     for (int k = 0; k < R->n_step; ++k) {
-        if (ORACLE_MUTANT != 2) w += work_increment(R, s);
+        if (ORACLE_MUTANT != 2) w += work_increment(R, s, k);
         for (int i = 0; i < R->n_sweep; ++i)
             update(R, s, parent, traj, R->n_therm + k * R->n_sweep + i, k);
-        if (ORACLE_MUTANT == 2) w += work_increment(R, s);
+        if (ORACLE_MUTANT == 2) w += work_increment(R, s, k);
     }
     return w;
 }
@@ -436,20 +472,27 @@ static long long run_trajectory(const run_t *R, long long traj, int8_t *s, int *
  * (dir = +1) or l+1 -> l (dir = -1).  work_out[i] = W_int of trajectory
  * traj0 + i; spins_out (nullable) receives the final configuration of each
  * trajectory as int8 +-1 in the natural order [traj][r][t][y][x].
- * n_threads > 0 sets the OpenMP thread count (trajectories are independent, so
- * the result does not depend on it).  Returns 0, or -1 on bad arguments. */
-int oracle_run_update(int d, int L, int Lt, double beta, int l, int n_step, int n_sweep,
-                      int n_therm, int dir, int upd, uint64_t seed, long long traj0, int n_traj,
-                      int n_threads, long long *work_out, int8_t *spins_out)
+ * upd selects the update (0 Metropolis, 1 Swendsen-Wang), prot the protocol
+ * (1 all switched columns together, 2 one column at a time; n_step must then be
+ * a multiple of L_y).  n_threads > 0 sets the OpenMP thread count (trajectories
+ * are independent, so the result does not depend on it).  Returns 0, or -1 on
+ * bad arguments. */
+int oracle_run_full(int d, int L, int Lt, double beta, int l, int n_step, int n_sweep,
+                    int n_therm, int dir, int upd, int prot, uint64_t seed, long long traj0,
+                    int n_traj, int n_threads, long long *work_out, int8_t *spins_out)
 {
     if ((d != 2 && d != 3) || L < 2 || Lt < 2 || (L & 1) || (Lt & 1)) return -1;
     if (upd != 0 && upd != 1) return -1;
+    if (prot != 1 && prot != 2) return -1;
     if (l < 0 || l >= L || n_step < 1 || n_sweep < 0 || n_therm < 0) return -1;
     if (dir != 1 && dir != -1) return -1;
     run_t R;
     memset(&R, 0, sizeof R);
     R.g.d = d; R.g.L = L; R.g.Lt = Lt; R.g.Ly = d == 3 ? L : 1; R.g.n = 2;
     R.g.l = l; R.g.dir = dir;
+    if (prot == 2 && n_step % R.g.Ly != 0) return -1;
+    R.prot = prot;
+    R.m = prot == 2 ? n_step / R.g.Ly : n_step;
     R.beta = beta; R.n_step = n_step; R.n_sweep = n_sweep; R.n_therm = n_therm;
     R.key[0] = (uint32_t)seed; R.key[1] = (uint32_t)(seed >> 32);
     for (int m = 2; m <= 2 * d; m += 2) R.bulk_T[m / 2] = oracle_threshold_bulk(beta, m);
@@ -457,30 +500,29 @@ int oracle_run_update(int d, int L, int Lt, double beta, int l, int n_step, int 
     uint32_t *cut = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n_step * per_step);
     if (!cut) return -1;
     for (int k = 0; k < n_step; ++k) {
-        long long kp = k + 1;
-        long long w_self = dir > 0 ? n_step - kp : kp;
-        long long w_glue = dir > 0 ? kp : n_step - kp;
+        long long den, w_self, w_glue;
+        step_weights(&R, k, &den, &w_self, &w_glue);
         for (int a = -(2 * d - 1); a <= 2 * d - 1; a += 2)
         for (int b = -1; b <= 1; b += 2)
         for (int c = -1; c <= 1; c += 2) {
-            long long m = (long long)a * n_step + b * w_self + c * w_glue;
+            long long m = (long long)a * den + b * w_self + c * w_glue;
             cut[(size_t)k * per_step + cut_index(&R.g, a, b, c)] =
-                oracle_threshold_cut(beta, m, n_step);
+                oracle_threshold_cut(beta, m, (int)den);
         }
     }
     R.cut_T = cut;
     /* Swendsen-Wang bond thresholds: full links x = 2 beta, switched links at
-     * step k: x = (2 beta w)/N with w = w_self or w_glue of lambda_{k+1} */
+     * step k: x = (2 beta w)/den with w = w_self or w_glue of lambda_{k+1} */
     R.update = upd;
     R.bond_full = quantise_bond(2.0 * beta);
     uint32_t *bonds = (uint32_t *)malloc(sizeof(uint32_t) * 2 * (size_t)n_step);
     if (!bonds) { free(cut); return -1; }
     for (int k = 0; k < n_step; ++k) {
-        long long kp = ORACLE_MUTANT == 9 ? k : k + 1;
-        long long w_self = dir > 0 ? n_step - kp : kp;
-        long long w_glue = dir > 0 ? kp : n_step - kp;
-        bonds[k] = quantise_bond((2.0 * beta * (double)w_self) / (double)n_step);
-        bonds[n_step + k] = quantise_bond((2.0 * beta * (double)w_glue) / (double)n_step);
+        long long den, w_self, w_glue;
+        step_weights(&R, k, &den, &w_self, &w_glue);
+        if (ORACLE_MUTANT == 9) { w_self += dir; w_glue -= dir; }   /* lambda_k */
+        bonds[k] = quantise_bond((2.0 * beta * (double)w_self) / (double)den);
+        bonds[n_step + k] = quantise_bond((2.0 * beta * (double)w_glue) / (double)den);
     }
     R.bond_self = bonds;
     R.bond_glue = bonds + n_step;
@@ -511,6 +553,15 @@ int oracle_run_update(int d, int L, int Lt, double beta, int l, int n_step, int 
     free(cut);
     free(bonds);
     return failed ? -1 : 0;
+}
+
+/* Protocol 1 of oracle_run_full. */
+int oracle_run_update(int d, int L, int Lt, double beta, int l, int n_step, int n_sweep,
+                      int n_therm, int dir, int upd, uint64_t seed, long long traj0, int n_traj,
+                      int n_threads, long long *work_out, int8_t *spins_out)
+{
+    return oracle_run_full(d, L, Lt, beta, l, n_step, n_sweep, n_therm, dir, upd, 1, seed,
+                           traj0, n_traj, n_threads, work_out, spins_out);
 }
 
 /* The Metropolis form (update 0) of oracle_run_update. */
