@@ -76,6 +76,10 @@ def parse_args():
     ap.add_argument("--update", choices=["metropolis", "sw"], default="metropolis",
                     help="Monte Carlo update of every sweep: checkerboard Metropolis or "
                          "Swendsen-Wang clusters")
+    ap.add_argument("--protocol", type=int, choices=[1, 2], default=1,
+                    help="1: every switched column together; 2: one column at a time (3D)")
+    ap.add_argument("--n-therm", type=int, default=None,
+                    help="override the thermalisation sweeps")
     ap.add_argument("--no-compare", action="store_true",
                     help="sw: skip the equal-error comparison with Metropolis")
     ap.add_argument("--plain", type=int, default=0,
@@ -89,11 +93,18 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def workload_for(config: int, rank: int, traj_per_l=None, n_step=None, update="metropolis"):
+def workload_for(config: int, rank: int, traj_per_l=None, n_step=None, update="metropolis",
+                 protocol=1, n_therm=None):
     w = wl.CONFIGS[config]()
     if update == "sw":
         w.jobs = [j.with_(update=1) for j in w.jobs]
         w.name += "_sw"
+    if protocol == 2:
+        w.jobs = [j.with_(protocol=2) for j in w.jobs]
+        w.name += "_protocol2"
+    if n_therm is not None:
+        w.jobs = [j.with_(n_therm=n_therm) for j in w.jobs]
+        w.name += f"_therm{n_therm}"
     if traj_per_l:
         w.jobs = [j.with_(n_traj=traj_per_l) for j in w.jobs]
         w.name += f"_traj{traj_per_l}"
@@ -203,7 +214,8 @@ def cpu_oracle_rate(w, seconds: float):
     j = jobs[0]
     t0 = time.perf_counter()
     oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, threads, j.seed,
-               n_therm=j.n_therm, traj0=j.traj0, n_threads=threads, update=j.update)
+               n_therm=j.n_therm, traj0=j.traj0, n_threads=threads, update=j.update,
+               protocol=j.protocol)
     t_round = time.perf_counter() - t0
     rounds = max(1, int(seconds / max(t_round, 1e-3) / len(jobs)))
     n_per_job = rounds * threads
@@ -211,7 +223,8 @@ def cpu_oracle_rate(w, seconds: float):
     updates = 0
     for j in jobs:
         oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, n_per_job, j.seed,
-                   n_therm=j.n_therm, traj0=j.traj0, n_threads=threads, update=j.update)
+                   n_therm=j.n_therm, traj0=j.traj0, n_threads=threads, update=j.update,
+                   protocol=j.protocol)
         updates += j.with_(n_traj=n_per_job).updates
     dt = time.perf_counter() - t0
     sample = (f"{n_per_job} trajectories at each of l = {[j.l for j in jobs]} of the same "
@@ -266,7 +279,8 @@ def run_ours(args):
         dist.barrier()
     import paper_2304_03311_gb300 as jz
 
-    w = workload_for(args.config, rank, args.traj_per_l, args.n_step, args.update)
+    w = workload_for(args.config, rank, args.traj_per_l, args.n_step, args.update, args.protocol,
+                     args.n_therm)
     sw = args.update == "sw"
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
@@ -274,7 +288,7 @@ def run_ours(args):
     outs = [torch.empty(j.n_traj, dtype=torch.int64, device=dev) for j in w.jobs]
     params = [jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj,
                              j.seed, n_therm=j.n_therm, direction=j.direction, traj0=j.traj0,
-                             update=j.update)
+                             update=j.update, protocol=j.protocol)
               for j in w.jobs]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     n_groups = len({(j.d, j.L, j.L_t, j.seed) for j in w.jobs})
@@ -422,7 +436,8 @@ def run_ours(args):
         # c-function error it reaches; at equal error the cost scales as err^2 t
         mparams = [jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj,
                                   j.seed, n_therm=j.n_therm, direction=j.direction,
-                                  traj0=j.traj0, update=0) for j in w.jobs]
+                                  traj0=j.traj0, update=0, protocol=j.protocol)
+                   for j in w.jobs]
         if not args.no_autotune and not args.threads:
             for shape, j in {(j.d, j.L, j.L_t): j for j in w.jobs}.items():
                 jz.ising_autotune(ctx, mparams[w.jobs.index(j)])
@@ -436,13 +451,18 @@ def run_ours(args):
             m1.record(stream)
         stream.synchronize()
         m_ms = m0.elapsed_time(m1)
-        m_err = [e for _, e in c_function_errors(w, estimate(outs, 1))]
+        mfun = c_function_errors(w, estimate(outs, 1))
+        m_err = [e for _, e in mfun]
         s_err = [e for _, e in cfun]
         rms = lambda v: math.sqrt(sum(x * x for x in v) / len(v))
+        # both updates sample the same Z ratios: their c-functions must agree
+        pulls = [(a - b) / math.hypot(ea, eb) for (a, ea), (b, eb) in zip(cfun, mfun)]
         equal_error = {
             "metropolis": {"kernel_ms": m_ms, "c_err_rms": rms(m_err)},
             "sw": {"kernel_ms": kernel_ms, "c_err_rms": rms(s_err)},
             "sw_speedup_at_equal_error": (rms(m_err) ** 2 * m_ms) / (rms(s_err) ** 2 * kernel_ms),
+            "c_function_pull_max": max(abs(p) for p in pulls),
+            "c_function_chi2_per_l": sum(p * p for p in pulls) / len(pulls),
             "basis": "same trajectories, N, sweeps and n_therm; cost at equal error ~ err^2 x time"}
 
     plain = None
@@ -482,7 +502,8 @@ def run_ours(args):
                 "c_function_err_max": max(e for _, e in cfun) if cfun else None,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "plain_gpu_baseline": plain, "cta_threads": tuned or "default",
-                "update": args.update, "equal_error_vs_metropolis": equal_error,
+                "update": args.update, "protocol": args.protocol,
+                "equal_error_vs_metropolis": equal_error,
                 "gpu_launches": args.steps * ((2 if plan is not None else n_groups + len(w.jobs))),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
@@ -549,7 +570,8 @@ def run_reference(args):
     import oracle
     oracle.build()
     threads = oracle.max_threads()
-    w = workload_for(args.config, 0, args.traj_per_l, args.n_step, args.update)
+    w = workload_for(args.config, 0, args.traj_per_l, args.n_step, args.update, args.protocol,
+                     args.n_therm)
     jobs = w.jobs[:: max(1, len(w.jobs) // 2)][:2]
     n_per = threads
 
@@ -557,7 +579,8 @@ def run_reference(args):
         u = 0
         for j in jobs:
             oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, n_per, j.seed,
-                       n_therm=j.n_therm, traj0=j.traj0, n_threads=threads, update=j.update)
+                       n_therm=j.n_therm, traj0=j.traj0, n_threads=threads, update=j.update,
+                       protocol=j.protocol)
             u += j.with_(n_traj=n_per).updates
         return u
 

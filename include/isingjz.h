@@ -82,9 +82,9 @@ typedef struct ising_ctx ising_ctx;
  *                 cluster of bonded sites flips with probability 1/2.  One CTA
  *                 per trajectory; needs about 4.5 V (2D) or 4.6 V (3D) bytes
  *                 of shared memory for the V = 2 L_t L^(d-1) sites (at most
- *                 227 KiB, V up to about 50,000), else ISING_ERR_UNSUPPORTED.  Served by jarzynski_run_ex and
- *                 jarzynski_run_batch; the other entry points return
- *                 ISING_ERR_UNSUPPORTED for it.
+ *                 227 KiB, V up to about 50,000), else ISING_ERR_UNSUPPORTED.
+ *                 Served by jarzynski_run_ex and jarzynski_run_batch; the
+ *                 other entry points return ISING_ERR_UNSUPPORTED for it.
  *              Other values: ISING_ERR_ARG.
  *   beta       coupling, 0 <= beta <= 4
  *   l          width of region A before the move, 0 <= l <= L-1
@@ -92,7 +92,15 @@ typedef struct ising_ctx ising_ctx;
  *   n_therm    thermalisation sweeps of the start ensemble (section 4 uses 1000)
  *   n_traj     trajectories, traj0 the global index of the first one (the index
  *              enters the random counter, so a range split gives the same result)
- *   seed       Philox key */
+ *   seed       Philox key
+ *   protocol   0 or 1: protocol 1, every switched column (x = l, y) moves
+ *              together, lambda_k = k/N (section 3); 2: protocol 2 (Appendix B),
+ *              the L_y columns move one after another, m = N/L_y steps each
+ *              (n_step must be a multiple of L_y, else ISING_ERR_ARG); the work
+ *              of the moving column is scaled by L_y so that W = (beta/N) W_int
+ *              in both.  In 2D both protocols are the same computation.
+ *              jarzynski_run_plain refuses protocol 2 in 3D
+ *              (ISING_ERR_UNSUPPORTED). */
 typedef struct jz_params {
     int d, L, L_t;
     int update;
@@ -103,10 +111,12 @@ typedef struct jz_params {
     int direction;
     long long traj0;
     uint64_t seed;
+    int protocol;
 } jz_params;
 
 /* Fills *p with defaults (n_therm = 1000, direction = +1, traj0 = 0, n_sweep = 1,
- * seed = 0) and zero sizes; returns ISING_OK or ISING_ERR_ARG for p == NULL. */
+ * seed = 0, update = 0, protocol = 1) and zero sizes; returns ISING_OK or
+ * ISING_ERR_ARG for p == NULL. */
 int jz_params_default(jz_params* p);
 
 /* Creates a context on CUDA device `device`.

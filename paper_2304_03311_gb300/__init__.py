@@ -45,7 +45,7 @@ class JzParams(ctypes.Structure):
         ("update", ctypes.c_int), ("beta", ctypes.c_double), ("l", ctypes.c_int),
         ("n_step", ctypes.c_int), ("n_sweep", ctypes.c_int), ("n_therm", ctypes.c_int),
         ("n_traj", ctypes.c_int), ("direction", ctypes.c_int),
-        ("traj0", ctypes.c_longlong), ("seed", ctypes.c_uint64),
+        ("traj0", ctypes.c_longlong), ("seed", ctypes.c_uint64), ("protocol", ctypes.c_int),
     ]
 
 
@@ -179,9 +179,10 @@ METROPOLIS, SWENDSEN_WANG = 0, 1
 
 
 def make_params(d, L, L_t, beta, l, n_step, n_sweep, n_traj, seed=0, *, n_therm=1000,
-                direction=1, traj0=0, update=METROPOLIS) -> JzParams:
+                direction=1, traj0=0, update=METROPOLIS, protocol=1) -> JzParams:
     p = jz_params_default()
     p.update = int(update)
+    p.protocol = int(protocol)
     p.d, p.L, p.L_t, p.beta, p.l = int(d), int(L), int(L_t), float(beta), int(l)
     p.n_step, p.n_sweep, p.n_traj = int(n_step), int(n_sweep), int(n_traj)
     p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF

@@ -17,7 +17,7 @@
 
 #include "jz_host.h"
 
-static_assert(sizeof(jz_params) == 64, "jz_params layout is part of the ABI");
+static_assert(sizeof(jz_params) == 72, "jz_params layout is part of the ABI");
 
 namespace jzh {
 
@@ -64,6 +64,8 @@ int check_params(const jz_params* p)
     if (!p) return ISING_ERR_ARG;
     if (p->d != 2 && p->d != 3) return ISING_ERR_UNSUPPORTED;
     if (p->update != 0 && p->update != 1) return ISING_ERR_ARG;
+    if (p->protocol < 0 || p->protocol > 2) return ISING_ERR_ARG;
+    if (p->protocol == 2 && p->d == 3 && p->n_step % p->L != 0) return ISING_ERR_ARG;
     if (p->L < 2 || p->L_t < 2 || p->L > 4096 || p->L_t > 4096) return ISING_ERR_ARG;
     if ((p->L & 1) || (p->L_t & 1)) return ISING_ERR_ODD_EXTENT;
     if (p->l < 0 || p->l > p->L - 1) return ISING_ERR_L_RANGE;
@@ -117,7 +119,8 @@ jz::PhiloxKeys key_schedule(uint64_t seed)
 // Host tables of one job: bulk thresholds by anti-aligned count a (m = 2D - 2a,
 // x = 2 beta m) and, per step k, the switched-site thresholds indexed by the
 // fixed-link sum a' (odd, |a'| <= 2D-1) and the self / glue bond products b, c
-// (m = a' N + b w_self + c w_glue, x = (2 beta m) / N).
+// (m = a' den + b w_self + c w_glue, x = (2 beta m) / den, den = N in protocol 1
+// and N / L_y in protocol 2).
 void build_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcut, size_t off)
 {
     const int D = p.d;
@@ -126,11 +129,9 @@ void build_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcu
         tb[a] = (a < D) ? threshold(2.0 * p.beta * (double)m) : 0xFFFFFFFFu;
     }
     const int per = 8 * D;
-    const long long N = p.n_step;
-    for (long long k = 0; k < N; ++k) {
-        const long long kp = k + 1;
-        const long long ws = p.direction > 0 ? N - kp : kp;
-        const long long wg = p.direction > 0 ? kp : N - kp;
+    for (long long k = 0; k < p.n_step; ++k) {
+        long long N, ws, wg;
+        step_weights(p, k, &N, &ws, &wg);
         for (int ia = 0; ia < 2 * D; ++ia) {
             const long long a = 2 * ia - (2 * D - 1);
             for (int ib = 0; ib < 2; ++ib)
@@ -144,6 +145,20 @@ void build_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcu
     }
 }
 
+// Couplings of the switching column at protocol step k, in units of 1/den:
+// lambda_{k+1} = kp/den.  Protocol 1: den = N, kp = k+1.  Protocol 2: den =
+// m = N/L_y and kp = k+1 - y m counts the steps of the active column y = k/m.
+void step_weights(const jz_params& p, long long k, long long* den, long long* w_self,
+                  long long* w_glue)
+{
+    const long long ly = p.d == 3 ? p.L : 1;
+    const long long m = p.protocol == 2 ? p.n_step / ly : p.n_step;
+    const long long kp = k + 1 - (k / m) * m;
+    *den = m;
+    *w_self = p.direction > 0 ? m - kp : kp;
+    *w_glue = p.direction > 0 ? kp : m - kp;
+}
+
 // Swendsen-Wang bond threshold of a link with x = 2K: a bond between equal
 // spins is active iff u < min(floor(2^32 (1 - e^{-x})), 2^32 - 1), i.e. with
 // probability 1 - e^{-x} to 2^-32 (Swendsen and Wang, PRL 58 (1987) 86).
@@ -154,20 +169,18 @@ uint32_t bond_threshold(double x)
 }
 
 // Swendsen-Wang tables of one job: tb[0] the full link (x = 2 beta); per step
-// k the switched column's self and glued links at lambda_{k+1}:
-// x = (2 beta w) / N with w = w_self, w_glue.
+// k the switching column's self and glued links at lambda_{k+1}:
+// x = (2 beta w) / den with w = w_self, w_glue.
 void build_bond_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcut,
                        size_t off)
 {
     tb[0] = bond_threshold(2.0 * p.beta);
     tb[1] = tb[2] = tb[3] = 0;
-    const long long N = p.n_step;
-    for (long long k = 0; k < N; ++k) {
-        const long long kp = k + 1;
-        const long long ws = p.direction > 0 ? N - kp : kp;
-        const long long wg = p.direction > 0 ? kp : N - kp;
-        tcut[off + 2 * k] = bond_threshold((2.0 * p.beta * (double)ws) / (double)N);
-        tcut[off + 2 * k + 1] = bond_threshold((2.0 * p.beta * (double)wg) / (double)N);
+    for (long long k = 0; k < p.n_step; ++k) {
+        long long den, ws, wg;
+        step_weights(p, k, &den, &ws, &wg);
+        tcut[off + 2 * k] = bond_threshold((2.0 * p.beta * (double)ws) / (double)den);
+        tcut[off + 2 * k + 1] = bond_threshold((2.0 * p.beta * (double)wg) / (double)den);
     }
 }
 
@@ -294,6 +307,7 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
         J.n_sweep = p.n_sweep;
         J.n_therm = p.n_therm;
         J.dir = p.direction;
+        J.prot = p.protocol == 2 ? 2 : 1;
         J.n_traj = p.n_traj;
         J.traj0 = p.traj0;
         J.cta0 = cta;
@@ -413,6 +427,7 @@ int jz_params_default(jz_params* p)
     p->n_therm = 1000;
     p->n_sweep = 1;
     p->direction = 1;
+    p->protocol = 1;
     return ISING_OK;
 }
 
@@ -573,7 +588,7 @@ int jarzynski_run_plain(ising_ctx* ctx, const jz_params* p, int64_t* work_int_ou
     if (!ctx || !p || !work_int_out) return ISING_ERR_ARG;
     int rc = check_params(p);
     if (rc) return rc;
-    if (p->update != 0) return ISING_ERR_UNSUPPORTED;
+    if (p->update != 0 || (p->protocol == 2 && p->d == 3)) return ISING_ERR_UNSUPPORTED;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
     const jz::Geom g = make_geom(p->d, p->L, p->L_t);
     const int V = 2 * p->L_t * g.Ly * p->L;
@@ -762,6 +777,7 @@ extern "C" int jarzynski_run_noalloc(const jz_params* p, int64_t* work_int_out, 
     J.n_sweep = p->n_sweep;
     J.n_therm = p->n_therm;
     J.dir = p->direction;
+    J.prot = p->protocol == 2 ? 2 : 1;
     J.n_traj = p->n_traj;
     J.traj0 = p->traj0;
     J.cta0 = 0;
@@ -861,6 +877,7 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
         J.n_sweep = p.n_sweep;
         J.n_therm = p.n_therm;
         J.dir = p.direction;
+        J.prot = p.protocol == 2 ? 2 : 1;
         J.n_traj = p.n_traj;
         J.traj0 = p.traj0;
         J.cta0 = 0;

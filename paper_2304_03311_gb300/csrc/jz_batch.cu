@@ -21,7 +21,7 @@ template <int D, bool FAST, class Bar>
 __device__ __forceinline__ void run_item(const BatchJob& B, const PhiloxKeys& K, int traj_lo,
                                          uint32_t* S, const uint32_t* tab, int* s_work, Bar bar)
 {
-    const TeamJob tj = team_job(B.J);
+    const TeamJob tj = team_job(B.J, B.g.Ly);
     int team, tid;
     team_of(B.sh, &team, &tid);
     if (!B.sh.warp && tid >= B.sh.team_threads) team = -1;   // CTA larger than the team
@@ -36,7 +36,8 @@ __device__ __forceinline__ void run_item(const BatchJob& B, const PhiloxKeys& K,
     if (has && dE != 0) atomicAdd(&s_work[tm], dE);
     __syncthreads();
     if (has && tid == 0)
-        B.J.w_out[local] = (long long)(tj.dir > 0 ? s_work[tm] : -s_work[tm]);
+        B.J.w_out[local] = (long long)(tj.dir > 0 ? s_work[tm] : -s_work[tm]) *
+                           (tj.prot == 2 ? B.g.Ly : 1);
     if (has && B.J.spins_out != nullptr)
         export_spins<D>(B.g, St, B.J.spins_out + local * (long long)(2 * B.g.Lt * B.g.Ly * B.g.L),
                         tid, B.sh.team_threads);

@@ -57,6 +57,7 @@ struct JobDesc {
     int n_step, n_sweep, n_therm;
     int dir;            // +1 forward, -1 reverse
     int n_traj;
+    int prot;           // 1: every switched column together; 2: one column y at a time
     long long traj0;    // global index of the job's first trajectory
     long long cta0;     // first CTA of the job in the launch grid
     uint32_t tb[4];     // bulk thresholds by anti-aligned neighbour count a:

@@ -59,6 +59,8 @@ uint32_t threshold(double x);
 jz::PhiloxKeys key_schedule(uint64_t seed);
 void build_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcut, size_t off);
 uint32_t bond_threshold(double x);
+void step_weights(const jz_params& p, long long k, long long* den, long long* w_self,
+                  long long* w_glue);
 void build_bond_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcut,
                        size_t off);
 bool sw_fits(const jz::Geom& g);

@@ -33,7 +33,7 @@ traj_kernel(const Geom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
 
     const int j = find_job(jobs, n_jobs, (long long)blockIdx.x);
     const JobDesc& J = jobs[j];
-    const TeamJob tj = team_job(J);
+    const TeamJob tj = team_job(J, g.Ly);
     const long long cta_local = (long long)blockIdx.x - __ldg(&J.cta0);
     int team, tid;
     team_of(sh, &team, &tid);
@@ -55,7 +55,9 @@ traj_kernel(const Geom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
                                               CtaBarrier{});
     if (has && dE != 0) atomicAdd(&s_work[tm], dE);
     __syncthreads();
-    if (has && tid == 0) J.w_out[local] = (long long)(tj.dir > 0 ? s_work[tm] : -s_work[tm]);
+    if (has && tid == 0)
+        J.w_out[local] = (long long)(tj.dir > 0 ? s_work[tm] : -s_work[tm]) *
+                         (tj.prot == 2 ? g.Ly : 1);
     int8_t* sp = J.spins_out;
     if (has && sp != nullptr)
         export_spins<D>(g, St, sp + local * (long long)(2 * g.Lt * g.Ly * g.L), tid,

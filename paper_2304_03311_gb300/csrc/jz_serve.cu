@@ -120,6 +120,7 @@ int jz_server::launch(Slot& s, Job& j)
     J.n_sweep = p.n_sweep;
     J.n_therm = p.n_therm;
     J.dir = p.direction;
+    J.prot = p.protocol == 2 ? 2 : 1;
     J.n_traj = p.n_traj;
     J.traj0 = p.traj0;
     J.cta0 = 0;

@@ -176,6 +176,8 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
     const int l = __ldg(&J.l), dir = __ldg(&J.dir);
     const int n_step = __ldg(&J.n_step), n_sweep = __ldg(&J.n_sweep);
     const int n_therm = __ldg(&J.n_therm);
+    const int prot = __ldg(&J.prot);
+    const int den = prot == 2 ? n_step / g.Ly : n_step;   // steps of one column's run
     const uint32_t t_full = __ldg(&J.tb[0]);
     const uint32_t* bonds = J.tcut;          // [n_step][2]: self, glue thresholds
     const uint32_t traj = (uint32_t)(__ldg(&J.traj0) + local);
@@ -210,12 +212,17 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
     for (int sw = 0; sw < n_total; ++sw) {
         const int k = sw < n_therm ? -1 : (sw - n_therm) / n_sweep;
         const bool step_start = k >= 0 && (sw - n_therm) % n_sweep == 0;
+        // protocol 2: only column y = ya moves at step k; columns before it sit
+        // at the end geometry, the ones after it at the start geometry
+        const int ya = (k >= 0 && prot == 2) ? k / den : -1;
         // work of step k on the configuration before its sweeps:
-        // dE = sum_{r,y} s(l,y,0)^r [s(l,y,1)^r - s(l,y,1)^{r+1}]
+        // dE = sum_{r,y} s(l,y,0)^r [s(l,y,1)^r - s(l,y,1)^{r+1}] over the
+        // moving columns
         if (step_start && warp == 0) {
             int e = 0;
             for (int q = lane; q < 2 * g.Ly; q += 32) {
                 const int r = q / g.Ly, y = q - r * g.Ly;
+                if (ya >= 0 && y != ya) continue;
                 const int lo_i = (r * g.Lt * g.Ly + y) * g.L + l;
                 const int up_s = lo_i + g.SL;
                 const int up_g = up_s + (r ? -g.VR : g.VR);
@@ -258,6 +265,13 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
                     } else if (s.x < l) {
                         jg = jgl;
                         Tg = t_full;
+                    } else if (ya >= 0 && s.y != ya) {
+                        if ((s.y < ya) == (dir > 0)) {
+                            jg = jgl;
+                            Tg = t_full;
+                        } else {
+                            jt = js;
+                        }
                     } else {
                         jt = js;
                         Tt = t_self;
@@ -356,7 +370,7 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) J.w_out[local] = dir > 0 ? w : -w;
+    if (threadIdx.x == 0) J.w_out[local] = (dir > 0 ? w : -w) * (prot == 2 ? g.Ly : 1);
     int8_t* so = J.spins_out;
     if (so != nullptr) {
         so += local * (long long)g.V;

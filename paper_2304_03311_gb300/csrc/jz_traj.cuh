@@ -67,6 +67,8 @@ __device__ __forceinline__ uint32_t word8(const uint4& ua, const uint4& ub, int 
 // Per-job values a team needs (read from the job descriptor once).
 struct TeamJob {
     int l, n_step, n_sweep, n_therm, dir;
+    int prot;     // 1: every switched column together; 2: one column y at a time
+    int den;      // steps of one column's run: N (protocol 1), N / L_y (protocol 2)
     const uint32_t* tcut;
 };
 
@@ -197,7 +199,7 @@ struct Traj {
             const int a = (2 * D - 1) - 2 * a_cnt;
             const int b = 1 - 2 * as;
             const int cg = 1 - 2 * ag;
-            const int mm = a * J.n_step + b * w_self + cg * w_glue;
+            const int mm = a * J.den + b * w_self + cg * w_glue;
             const int ti = (((a + 2 * D - 1) >> 1) * 2 + (b > 0)) * 2 + (cg > 0);
             const bool acc = (mm <= 0) || (word8(ua, ub, jl) < __ldg(J.tcut + k * (8 * D) + ti));
             flip = (flip & ~(0xFu << sh)) | ((uint32_t)acc << sh);
@@ -277,8 +279,9 @@ struct WarpBarrier {
 
 // Runs one whole trajectory with the team's threads.  Every thread sharing the
 // barrier calls it with the same job (trip counts match across teams); tid < 0
-// marks a thread without sites.  Returns this thread's share of W_int (in
-// units of beta/N, sign of the direction applied by the caller).
+// marks a thread without sites.  Returns this thread's share of sum_k dE_k
+// (the caller applies the direction's sign and, in protocol 2, the factor L_y
+// that makes W = (beta/N) W_int).
 template <int D, bool FAST, int CW, int CLY, class Bar>
 __device__ __forceinline__ int run_trajectory(const Geom& g, const PhiloxKeys& K, const TeamJob& J,
                                               long long traj, uint32_t* S_team,
@@ -300,13 +303,21 @@ __device__ __forceinline__ int run_trajectory(const Geom& g, const PhiloxKeys& K
     }
     uint32_t s = (uint32_t)J.n_therm;
     for (int k = 0; k < J.n_step; ++k) {
-        const int kp = k + 1;
-        const int w_self = J.dir > 0 ? J.n_step - kp : kp;
-        const int w_glue = J.dir > 0 ? kp : J.n_step - kp;
+        // protocol 2: only column y = k / den moves; the columns before it sit
+        // at the end geometry, the ones after it at the start geometry
+        const int ya = k / J.den;
+        const int kp = k + 1 - ya * J.den;
+        const int w_self = J.dir > 0 ? J.den - kp : kp;
+        const int w_glue = J.dir > 0 ? kp : J.den - kp;
+        int kk = k, lg = J.l;
+        if (J.prot == 2 && tr.y != ya) {
+            kk = -1;
+            lg = (tr.y < ya) == (J.dir > 0) ? J.l + 1 : J.l;
+        }
         for (int i = 0; i < J.n_sweep; ++i, ++s) {
-            tr.half_sweep(0, s, k, J.l, J, w_self, w_glue, i == 0, dE);
+            tr.half_sweep(0, s, kk, lg, J, w_self, w_glue, i == 0, dE);
             bar();
-            tr.half_sweep(1, s, k, J.l, J, w_self, w_glue, false, dE);
+            tr.half_sweep(1, s, kk, lg, J, w_self, w_glue, false, dE);
             bar();
         }
     }
@@ -332,7 +343,8 @@ __device__ __forceinline__ void export_spins(const Geom& g, const uint32_t* S_te
     }
 }
 
-__device__ __forceinline__ TeamJob team_job(const JobDesc& J)
+// ly: L_y of the job's lattice (the number of switched columns).
+__device__ __forceinline__ TeamJob team_job(const JobDesc& J, int ly)
 {
     TeamJob t;
     t.l = __ldg(&J.l);
@@ -340,6 +352,8 @@ __device__ __forceinline__ TeamJob team_job(const JobDesc& J)
     t.n_sweep = __ldg(&J.n_sweep);
     t.n_therm = __ldg(&J.n_therm);
     t.dir = __ldg(&J.dir);
+    t.prot = __ldg(&J.prot);
+    t.den = t.prot == 2 ? t.n_step / ly : t.n_step;
     t.tcut = J.tcut;
     return t;
 }

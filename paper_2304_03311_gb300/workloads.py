@@ -35,6 +35,7 @@ class Job:
     direction: int = 1
     traj0: int = 0
     update: int = 0          # 0 checkerboard Metropolis, 1 Swendsen-Wang
+    protocol: int = 1        # 1 every switched column together, 2 one column at a time
 
     @property
     def sites(self) -> int:
