@@ -44,16 +44,21 @@ class Links:
     n_sites: int
 
 
-def replica_links(d: int, L: int, L_t: int, l: int) -> Links:
-    """Every link once, from each site towards +x, +y (3D) and +t.
+def replica_links(d: int, L: int, L_t: int, l: int, n: int = N_REPLICA,
+                  whole: bool = False) -> Links:
+    """Every link once, from each site towards +x, +y (3D) and +t, for n
+    replicas.
 
     The +t link leaving t = 0 crosses the cut: for x < l it lands in replica
-    r + 1 (glued), for x > l in replica r, and for x = l both links exist with
-    the switched couplings (section 3, replica H/T and the linear protocol).
+    r + 1 (mod n, glued), for x > l in replica r, and for x = l both links
+    exist with the switched couplings (section 3, replica H/T and the linear
+    protocol).  whole: Alba et al.'s whole-cut transformation (section 3), the
+    columns x < l switch and nothing is glued beforehand.
     """
     L_y = L if d == 3 else 1
+    g0, g1 = (0, l) if whole else (l, l + 1)
     full, self_, glue = [], [], []
-    for r in range(N_REPLICA):
+    for r in range(n):
         for t in range(L_t):
             for y in range(L_y):
                 for x in range(L):
@@ -66,16 +71,16 @@ def replica_links(d: int, L: int, L_t: int, l: int) -> Links:
                     if t != 0:
                         full.append((i, same))
                         continue
-                    other = _site(L, L_t, L_y, (r + 1) % N_REPLICA, tn, y, x)
-                    if x < l:
+                    other = _site(L, L_t, L_y, (r + 1) % n, tn, y, x)
+                    if x < g0:
                         full.append((i, other))
-                    elif x > l:
+                    elif x >= g1:
                         full.append((i, same))
                     else:
                         self_.append((i, same))
                         glue.append((i, other))
     as_arr = lambda v: np.array(v, dtype=np.int64).reshape(-1, 2)
-    return Links(as_arr(full), as_arr(self_), as_arr(glue), N_REPLICA * L_t * L_y * L)
+    return Links(as_arr(full), as_arr(self_), as_arr(glue), n * L_t * L_y * L)
 
 
 def _spins_of_states(n_sites: int) -> np.ndarray:
@@ -96,11 +101,12 @@ def _logsumexp(v: np.ndarray) -> float:
     return m + math.log(float(np.sum(np.exp(v - m))))
 
 
-def log_z_enumerate(d: int, L: int, L_t: int, l: int, beta: float, lam: float = 0.0) -> float:
-    """ln Z_2 of the replica lattice at protocol parameter lambda by summing
-    exp(-H/T) over all 2^V states (H/T of section 3 with the switched column's
-    couplings beta (1 - lambda), beta lambda).  V <= 20."""
-    lk = replica_links(d, L, L_t, l)
+def log_z_enumerate(d: int, L: int, L_t: int, l: int, beta: float, lam: float = 0.0,
+                    n: int = N_REPLICA, whole: bool = False) -> float:
+    """ln Z_n of the replica lattice at protocol parameter lambda by summing
+    exp(-H/T) over all 2^V states (H/T of section 3 with the switched
+    columns' couplings beta (1 - lambda), beta lambda).  V <= 20."""
+    lk = replica_links(d, L, L_t, l, n, whole)
     sigma = _spins_of_states(lk.n_sites)
     e = (_bond_sums(sigma, lk.full) + (1.0 - lam) * _bond_sums(sigma, lk.self_)
          + lam * _bond_sums(sigma, lk.glue))
@@ -172,6 +178,44 @@ def log_z2_transfer(d: int, L: int, L_t: int, ls, beta: float) -> np.ndarray:
         z = np.sum(P[A, mix_ba] * P[B, mix_ab])
         out.append(math.log(z))
     return np.array(out)
+
+
+def log_zn_transfer(d: int, L: int, L_t: int, ls, beta: float, n: int) -> np.ndarray:
+    """ln Z_n(l) for n replicas (up to an l-independent constant), l in ls.
+
+    Generalises log_z2_transfer: with P = T^(L_t) and M_l(u, v) = P(v, mix(u, v))
+    (v's propagation closes on the slice that takes the previous replica's
+    columns x < l), the replicas form a ring, so Z_n(l) = Tr M_l^n; for n = 2
+    this is log_z2_transfer's double sum, and for l = 0 it is (Tr P)^n = Z^n.
+    """
+    T, column = _slice_transfer(d, L, beta)
+    P = np.linalg.matrix_power(T, L_t)
+    m = P.shape[0]
+    a = np.arange(m, dtype=np.int64)
+    U, V = np.meshgrid(a, a, indexing="ij")
+    out = []
+    for l in ls:
+        mask = 0
+        for bit, col in enumerate(column):
+            if col < l:
+                mask |= 1 << bit
+        M = P[V, (U & mask) | (V & ~mask)]
+        out.append(math.log(np.trace(np.linalg.matrix_power(M, n))))
+    return np.array(out)
+
+
+def delta_sn_transfer(d: int, L: int, L_t: int, beta: float, n: int) -> np.ndarray:
+    """Exact Delta S_n(l -> l+1) = -ln[Z_n(l+1)/Z_n(l)]/(n-1), l = 0..L-1
+    (section 2, eq. definition_of_derivative_of_Renyi_entropy with epsilon = a)."""
+    lz = log_zn_transfer(d, L, L_t, range(L + 1), beta, n)
+    return -(lz[1:] - lz[:-1]) / (n - 1)
+
+
+def renyi_sn_transfer(d: int, L: int, L_t: int, beta: float, n: int) -> np.ndarray:
+    """Exact S_n(l) = ln[Z_n(l)/Z^n]/(1-n) for l = 0..L (section 2, eq.
+    trace_of_rho_n_as_ratio_of_partition_functions); S_n(0) = 0."""
+    lz = log_zn_transfer(d, L, L_t, range(L + 1), beta, n)
+    return (lz - lz[0]) / (1 - n)
 
 
 def delta_s2_transfer(d: int, L: int, L_t: int, beta: float) -> np.ndarray:
@@ -282,18 +326,19 @@ class _Dynamics:
     """Single-site Metropolis probabilities of every site in every state of a
     tiny replica lattice, at the start geometry or at protocol step k."""
 
-    def __init__(self, d, L, L_t, l, beta, n_step, direction, quantised, protocol=1):
+    def __init__(self, d, L, L_t, l, beta, n_step, direction, quantised, protocol=1,
+                 n=N_REPLICA, whole=False):
         self.d, self.L, self.L_t, self.l = d, L, L_t, l
         self.beta, self.N, self.dir = beta, n_step, direction
         self.quantised = quantised
         self.sched = _Schedule(d, L, n_step, direction, protocol)
         self._cache = {}
-        self.links = replica_links(d, L, L_t, l)
+        self.links = replica_links(d, L, L_t, l, n, whole)
         self.V = self.links.n_sites
         self.sigma = _spins_of_states(self.V).astype(np.int64)
         L_y = L if d == 3 else 1
         self.colour = np.zeros(self.V, dtype=np.int64)
-        for r in range(N_REPLICA):
+        for r in range(n):
             for t in range(L_t):
                 for y in range(L_y):
                     for x in range(L):
@@ -390,7 +435,7 @@ def _propagate(F, de):
 
 
 def exact_path_measure(d, L, L_t, l, beta, n_step, n_sweep, n_therm, *, direction=1,
-                       quantised=True, start="hot", protocol=1):
+                       quantised=True, start="hot", protocol=1, n=N_REPLICA, whole=False):
     """Exact joint law of (W_int, final state) of the non-equilibrium dynamics.
 
     start="hot": uniform start (independent random spins) followed by n_therm
@@ -399,7 +444,7 @@ def exact_path_measure(d, L, L_t, l, beta, n_step, n_sweep, n_therm, *, directio
     eq. equilibrium_distribution), for the Jarzynski identity.
     Returns (w_values, F) with F[w_index, state] the probability.
     """
-    dyn = _Dynamics(d, L, L_t, l, beta, n_step, direction, quantised, protocol)
+    dyn = _Dynamics(d, L, L_t, l, beta, n_step, direction, quantised, protocol, n, whole)
     n_states = 1 << dyn.V
     lam0 = 0.0 if direction > 0 else 1.0
     if start == "hot":
@@ -438,10 +483,11 @@ class _SWDynamics:
     T[s, s'] = sum over bond sets B of P(B | s) 2^{-nc(B)} [s' = s with some
     clusters of B flipped], computed by enumerating all bond sets."""
 
-    def __init__(self, d, L, L_t, l, beta, n_step, direction, quantised, protocol=1):
+    def __init__(self, d, L, L_t, l, beta, n_step, direction, quantised, protocol=1,
+                 n=N_REPLICA, whole=False):
         self.beta, self.N, self.dir, self.quantised = beta, n_step, direction, quantised
         self.sched = _Schedule(d, L, n_step, direction, protocol)
-        self.links = replica_links(d, L, L_t, l)
+        self.links = replica_links(d, L, L_t, l, n, whole)
         self.V = self.links.n_sites
         if self.V > 10:
             raise ValueError("exact Swendsen-Wang kernel needs V <= 10")
@@ -526,11 +572,11 @@ class _SWDynamics:
 
 
 def exact_path_measure_sw(d, L, L_t, l, beta, n_step, n_sweep, n_therm, *, direction=1,
-                          quantised=True, start="hot", protocol=1):
+                          quantised=True, start="hot", protocol=1, n=N_REPLICA, whole=False):
     """Exact joint law of (W_int, final state) of the non-equilibrium dynamics
     with Swendsen-Wang updates (same protocol as exact_path_measure: work
     before each update, update at lambda_{k+1}).  Returns (w_values, F)."""
-    dyn = _SWDynamics(d, L, L_t, l, beta, n_step, direction, quantised, protocol)
+    dyn = _SWDynamics(d, L, L_t, l, beta, n_step, direction, quantised, protocol, n, whole)
     n_states = 1 << dyn.V
     lam0 = 0.0 if direction > 0 else 1.0
     if start == "hot":

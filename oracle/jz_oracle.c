@@ -27,6 +27,12 @@
  *   dE_k = sum_{r,y} s^r(l,y,0) [s^r(l,y,1) - s^{r+1}(l,y,1)] so that
  *   W = (beta / N) W_int; the reverse protocol (lambda from 1 to 0, start at
  *   geometry l+1) flips the sign of dE_k.
+ *   n replicas (section 2, Z_n / Z^n): the same geometry with the glue of
+ *   replica r landing in replica r+1 mod n; Delta S_n = -ln<e^-W>/(n-1).
+ *   Whole cut (Alba et al., section 3, eq.
+ *   off-equilibrium_evolution_of_the_couplings): every column x < l switches
+ *   together from n decoupled replicas to glued ones, so <e^-W> = Z_n(l)/Z^n
+ *   and S_n(l) = -ln<e^-W>/(n-1).
  *   Protocol 2 (Appendix B, "protocol 2"; 3D): the L_y switched columns
  *   (x = l, y) are switched one after another, column y during the m = N/L_y
  *   steps y m .. (y+1) m - 1 with its own lambda = (k + 1 - y m)/m; columns
@@ -149,7 +155,8 @@ uint32_t oracle_threshold_cut(double beta, long long m, int n_step)
 /* -------------------------------------------------------------- geometry --- */
 typedef struct {
     int d, L, Lt, Ly, n;
-    int l;        /* the switched column                                     */
+    int l;        /* the switched column (shift mode) or the cut length (whole) */
+    int g0, g1;   /* columns x < g0 are glued, g0 <= x < g1 switch, x >= g1 self */
     int dir;      /* +1 forward (l -> l+1), -1 reverse (l+1 -> l)            */
 } geom_t;
 
@@ -200,9 +207,9 @@ static int links_of(const geom_t *g, int r, int t, int y, int x, int col,
         int rg = side == 1 ? wrap(r + 1, g->n) : wrap(r - 1, g->n);
         int self_site = site_of(g, r, tn, y, x);
         int glue_site = site_of(g, rg, tn, y, x);
-        if (x < g->l) {
+        if (x < g->g0) {
             nbr[k] = ORACLE_MUTANT == 3 ? self_site : glue_site; cls[k++] = FULL;
-        } else if (x > g->l) {
+        } else if (x >= g->g1) {
             nbr[k] = self_site; cls[k++] = FULL;
         } else if (col == COL_SELF) {
             nbr[k] = self_site; cls[k++] = FULL;
@@ -365,7 +372,7 @@ static void sw_sweep(const run_t *R, int8_t *s, int *parent, long long traj, int
                      int k)
 {
     const geom_t *g = &R->g;
-    const int V = 2 * g->Lt * g->Ly * g->L;
+    const int V = g->n * g->Lt * g->Ly * g->L;
     for (int i = 0; i < V; ++i) parent[i] = i;
     for (int r = 0; r < g->n; ++r)
     for (int t = 0; t < g->Lt; ++t)
@@ -388,9 +395,9 @@ static void sw_sweep(const run_t *R, int8_t *s, int *parent, long long traj, int
         } else {
             int self_site = site_of(g, r, tn, y, x);
             int glue_site = site_of(g, wrap(r + 1, g->n), tn, y, x);
-            if (x > g->l) {
+            if (x >= g->g1) {
                 j[1] = self_site; T[1] = R->bond_full;
-            } else if (x < g->l) {
+            } else if (x < g->g0) {
                 j[3] = ORACLE_MUTANT == 12 ? self_site : glue_site; T[3] = R->bond_full;
             } else if (column_state(R, y, k) == COL_SELF) {
                 j[1] = self_site; T[1] = R->bond_full;
@@ -423,11 +430,12 @@ static long long work_increment(const run_t *R, const int8_t *s, int k)
     const geom_t *g = &R->g;
     long long e = 0;
     for (int r = 0; r < g->n; ++r)
-    for (int y = 0; y < g->Ly; ++y) {
+    for (int y = 0; y < g->Ly; ++y)
+    for (int x = g->g0; x < g->g1; ++x) {
         if (R->prot == 2 && y != k / R->m) continue;
-        int lo = site_of(g, r, 0, y, g->l);
-        int up_self = site_of(g, r, 1, y, g->l);
-        int up_glue = site_of(g, wrap(r + 1, g->n), 1, y, g->l);
+        int lo = site_of(g, r, 0, y, x);
+        int up_self = site_of(g, r, 1, y, x);
+        int up_glue = site_of(g, wrap(r + 1, g->n), 1, y, x);
         e += (long long)s[lo] * (s[up_self] - s[up_glue]);
     }
     if (R->prot == 2 && ORACLE_MUTANT != 13) e *= g->Ly;
@@ -474,22 +482,31 @@ static long long run_trajectory(const run_t *R, long long traj, int8_t *s, int *
  * trajectory as int8 +-1 in the natural order [traj][r][t][y][x].
  * upd selects the update (0 Metropolis, 1 Swendsen-Wang), prot the protocol
  * (1 all switched columns together, 2 one column at a time; n_step must then be
- * a multiple of L_y).  n_threads > 0 sets the OpenMP thread count (trajectories
- * are independent, so the result does not depend on it).  Returns 0, or -1 on
- * bad arguments. */
-int oracle_run_full(int d, int L, int Lt, double beta, int l, int n_step, int n_sweep,
-                    int n_therm, int dir, int upd, int prot, uint64_t seed, long long traj0,
-                    int n_traj, int n_threads, long long *work_out, int8_t *spins_out)
+ * a multiple of L_y).  n_rep >= 2 is the number of replicas n.  whole = 0: the
+ * transformation moves the end of region A by one column (x < l glued, column
+ * l switching); whole = 1: Alba et al.'s whole-cut transformation from n
+ * decoupled replicas to replicas glued along x < l (columns 0 .. l-1 switching,
+ * 1 <= l <= L; section 3, eq. off-equilibrium_evolution_of_the_couplings).
+ * n_threads > 0 sets the OpenMP thread count (trajectories are independent, so
+ * the result does not depend on it).  Returns 0, or -1 on bad arguments. */
+int oracle_run_general(int d, int L, int Lt, double beta, int l, int n_step, int n_sweep,
+                       int n_therm, int dir, int upd, int prot, int n_rep, int whole,
+                       uint64_t seed, long long traj0, int n_traj, int n_threads,
+                       long long *work_out, int8_t *spins_out)
 {
     if ((d != 2 && d != 3) || L < 2 || Lt < 2 || (L & 1) || (Lt & 1)) return -1;
     if (upd != 0 && upd != 1) return -1;
     if (prot != 1 && prot != 2) return -1;
-    if (l < 0 || l >= L || n_step < 1 || n_sweep < 0 || n_therm < 0) return -1;
+    if (n_rep < 2 || n_rep > 16 || (whole != 0 && whole != 1)) return -1;
+    if (whole ? (l < 1 || l > L || prot != 1) : (l < 0 || l >= L)) return -1;
+    if (n_step < 1 || n_sweep < 0 || n_therm < 0) return -1;
     if (dir != 1 && dir != -1) return -1;
     run_t R;
     memset(&R, 0, sizeof R);
-    R.g.d = d; R.g.L = L; R.g.Lt = Lt; R.g.Ly = d == 3 ? L : 1; R.g.n = 2;
+    R.g.d = d; R.g.L = L; R.g.Lt = Lt; R.g.Ly = d == 3 ? L : 1; R.g.n = n_rep;
     R.g.l = l; R.g.dir = dir;
+    R.g.g0 = whole ? 0 : l;
+    R.g.g1 = whole ? l : l + 1;
     if (prot == 2 && n_step % R.g.Ly != 0) return -1;
     R.prot = prot;
     R.m = prot == 2 ? n_step / R.g.Ly : n_step;
@@ -526,7 +543,7 @@ int oracle_run_full(int d, int L, int Lt, double beta, int l, int n_step, int n_
     }
     R.bond_self = bonds;
     R.bond_glue = bonds + n_step;
-    int V = 2 * L * Lt * R.g.Ly;
+    int V = n_rep * L * Lt * R.g.Ly;
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
 #else
@@ -553,6 +570,15 @@ int oracle_run_full(int d, int L, int Lt, double beta, int l, int n_step, int n_
     free(cut);
     free(bonds);
     return failed ? -1 : 0;
+}
+
+/* Two replicas, shift mode. */
+int oracle_run_full(int d, int L, int Lt, double beta, int l, int n_step, int n_sweep,
+                    int n_therm, int dir, int upd, int prot, uint64_t seed, long long traj0,
+                    int n_traj, int n_threads, long long *work_out, int8_t *spins_out)
+{
+    return oracle_run_general(d, L, Lt, beta, l, n_step, n_sweep, n_therm, dir, upd, prot, 2, 0,
+                              seed, traj0, n_traj, n_threads, work_out, spins_out);
 }
 
 /* Protocol 1 of oracle_run_full. */
