@@ -80,6 +80,10 @@ def parse_args():
                     help="1: every switched column together; 2: one column at a time (3D)")
     ap.add_argument("--n-therm", type=int, default=None,
                     help="override the thermalisation sweeps")
+    ap.add_argument("--therm-study", action="store_true",
+                    help="run the scan with Metropolis (n_therm 1000, 4000, 16000) and "
+                         "Swendsen-Wang (n_therm 100, 1000) and print the c-function pulls "
+                         "against Swendsen-Wang at n_therm 1000 (thermalisation bias)")
     ap.add_argument("--no-compare", action="store_true",
                     help="sw: skip the equal-error comparison with Metropolis")
     ap.add_argument("--plain", type=int, default=0,
@@ -606,10 +610,56 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_therm_study(args):
+    """The same scan with both updates and several thermalisation lengths:
+    the Jarzynski estimate is unbiased only from an equilibrium start, so a
+    start that has not thermalised shows up as a pull against a reference
+    that has (Swendsen-Wang with 1000 cluster sweeps)."""
+    import torch
+    from paper_2304_03311_gb300 import build as jzbuild
+    jzbuild.build()
+    import paper_2304_03311_gb300 as jz
+    n = args.traj_per_l or 512
+    ctx = jz.ising_replica_init(0, 0, None)
+    runs = {}
+    for name, upd, nth, seed in [("metropolis_therm1000", 0, 1000, 0),
+                                 ("metropolis_therm1000_seed7", 0, 1000, 7),
+                                 ("metropolis_therm4000", 0, 4000, 0),
+                                 ("metropolis_therm16000", 0, 16000, 0),
+                                 ("sw_therm1000", 1, 1000, 0), ("sw_therm100", 1, 100, 3)]:
+        w = wl.CONFIGS[args.config]()
+        jobs = [j.with_(n_traj=n, n_therm=nth, seed=seed, update=upd) for j in w.jobs]
+        outs = [torch.empty(n, dtype=torch.int64, device="cuda") for _ in jobs]
+        ps = [jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj, j.seed,
+                             n_therm=j.n_therm, update=upd) for j in jobs]
+        t0 = time.perf_counter()
+        jz.jarzynski_run_batch(ctx, ps, outs)
+        jz.ising_sync(ctx)
+        dt = time.perf_counter() - t0
+        res = []
+        for j, o in zip(jobs, outs):
+            _, ds, err = jz.estimator_reduce(ctx, o, n, j.beta, j.n_step, 1, 32)
+            res.append((ds, err))
+        runs[name] = (res, dt)
+    ref = runs["sw_therm1000"][0]
+    table = {}
+    for name, (res, dt) in runs.items():
+        pulls = [(a - b) / math.hypot(ea, eb) for (a, ea), (b, eb) in zip(res, ref)]
+        table[name] = {"seconds": dt, "chi2_per_l": sum(p * p for p in pulls) / len(pulls),
+                       "mean_pull": sum(pulls) / len(pulls),
+                       "max_abs_pull": max(abs(p) for p in pulls),
+                       "dS_err_l0": res[0][1], "dS_err_lmax": res[-1][1]}
+    jz.ising_replica_free(ctx)
+    print(json.dumps({"therm_study": table, "workload": wl.CONFIGS[args.config]().name,
+                      "n_traj_per_l": n, "reference": "sw_therm1000"}), flush=True)
+
+
 def main():
     args = parse_args()
     if args.probe:
         run_probe()
+    elif args.therm_study:
+        run_therm_study(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.config == 5:
