@@ -78,6 +78,10 @@ def parse_args():
                          "Swendsen-Wang clusters")
     ap.add_argument("--protocol", type=int, choices=[1, 2], default=1,
                     help="1: every switched column together; 2: one column at a time (3D)")
+    ap.add_argument("--n-replica", type=int, default=2, help="replicas n (Renyi index)")
+    ap.add_argument("--whole", action="store_true",
+                    help="whole-cut transformations (cut lengths l+1) instead of moving the "
+                         "end of region A by one column")
     ap.add_argument("--n-therm", type=int, default=None,
                     help="override the thermalisation sweeps")
     ap.add_argument("--therm-study", action="store_true",
@@ -98,8 +102,14 @@ def dist_env():
 
 
 def workload_for(config: int, rank: int, traj_per_l=None, n_step=None, update="metropolis",
-                 protocol=1, n_therm=None):
+                 protocol=1, n_therm=None, n_replica=2, whole=False):
     w = wl.CONFIGS[config]()
+    if n_replica != 2:
+        w.jobs = [j.with_(n_replica=n_replica) for j in w.jobs]
+        w.name += f"_n{n_replica}"
+    if whole:
+        w.jobs = [j.with_(whole=True, l=j.l + 1) for j in w.jobs]
+        w.name += "_wholecut"
     if update == "sw":
         w.jobs = [j.with_(update=1) for j in w.jobs]
         w.name += "_sw"
@@ -219,7 +229,7 @@ def cpu_oracle_rate(w, seconds: float):
     t0 = time.perf_counter()
     oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, threads, j.seed,
                n_therm=j.n_therm, traj0=j.traj0, n_threads=threads, update=j.update,
-               protocol=j.protocol)
+               protocol=j.protocol, n_replica=j.n_replica, whole=j.whole)
     t_round = time.perf_counter() - t0
     rounds = max(1, int(seconds / max(t_round, 1e-3) / len(jobs)))
     n_per_job = rounds * threads
@@ -228,7 +238,7 @@ def cpu_oracle_rate(w, seconds: float):
     for j in jobs:
         oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, n_per_job, j.seed,
                    n_therm=j.n_therm, traj0=j.traj0, n_threads=threads, update=j.update,
-                   protocol=j.protocol)
+                   protocol=j.protocol, n_replica=j.n_replica, whole=j.whole)
         updates += j.with_(n_traj=n_per_job).updates
     dt = time.perf_counter() - t0
     sample = (f"{n_per_job} trajectories at each of l = {[j.l for j in jobs]} of the same "
@@ -257,9 +267,15 @@ def kernel_source_hash():
 
 
 def c_function_errors(w, results):
+    """(C_n, error) per job: C_n from Delta S_n = Delta S / (n-1) for the
+    one-column moves; for whole-cut jobs S_n(l) itself."""
     import math as m
     out = []
     for j, (ds, err) in zip(w.jobs, results):
+        ds, err = ds / (j.n_replica - 1), err / (j.n_replica - 1)
+        if j.whole:
+            out.append((ds, err))
+            continue
         x = (j.l + 0.5) / j.L
         fac = (j.L / m.pi * m.sin(m.pi * x)) ** (j.d - 1) / (2.0 * j.L ** (j.d - 2))
         out.append((fac * ds, fac * err))
@@ -284,7 +300,7 @@ def run_ours(args):
     import paper_2304_03311_gb300 as jz
 
     w = workload_for(args.config, rank, args.traj_per_l, args.n_step, args.update, args.protocol,
-                     args.n_therm)
+                     args.n_therm, args.n_replica, args.whole)
     sw = args.update == "sw"
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
@@ -292,7 +308,8 @@ def run_ours(args):
     outs = [torch.empty(j.n_traj, dtype=torch.int64, device=dev) for j in w.jobs]
     params = [jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj,
                              j.seed, n_therm=j.n_therm, direction=j.direction, traj0=j.traj0,
-                             update=j.update, protocol=j.protocol)
+                             update=j.update, protocol=j.protocol, n_replica=j.n_replica,
+                             whole=j.whole)
               for j in w.jobs]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     n_groups = len({(j.d, j.L, j.L_t, j.seed) for j in w.jobs})
@@ -440,7 +457,8 @@ def run_ours(args):
         # c-function error it reaches; at equal error the cost scales as err^2 t
         mparams = [jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj,
                                   j.seed, n_therm=j.n_therm, direction=j.direction,
-                                  traj0=j.traj0, update=0, protocol=j.protocol)
+                                  traj0=j.traj0, update=0, protocol=j.protocol,
+                                  n_replica=j.n_replica, whole=j.whole)
                    for j in w.jobs]
         if not args.no_autotune and not args.threads:
             for shape, j in {(j.d, j.L, j.L_t): j for j in w.jobs}.items():
@@ -507,6 +525,7 @@ def run_ours(args):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "plain_gpu_baseline": plain, "cta_threads": tuned or "default",
                 "update": args.update, "protocol": args.protocol,
+                "n_replica": args.n_replica, "whole_cut": args.whole,
                 "equal_error_vs_metropolis": equal_error,
                 "gpu_launches": args.steps * ((2 if plan is not None else n_groups + len(w.jobs))),
                 "clocks": clocks}
@@ -575,7 +594,7 @@ def run_reference(args):
     oracle.build()
     threads = oracle.max_threads()
     w = workload_for(args.config, 0, args.traj_per_l, args.n_step, args.update, args.protocol,
-                     args.n_therm)
+                     args.n_therm, args.n_replica, args.whole)
     jobs = w.jobs[:: max(1, len(w.jobs) // 2)][:2]
     n_per = threads
 
@@ -584,7 +603,7 @@ def run_reference(args):
         for j in jobs:
             oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, n_per, j.seed,
                        n_therm=j.n_therm, traj0=j.traj0, n_threads=threads, update=j.update,
-                       protocol=j.protocol)
+                       protocol=j.protocol, n_replica=j.n_replica, whole=j.whole)
             u += j.with_(n_traj=n_per).updates
         return u
 

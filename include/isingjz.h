@@ -100,7 +100,19 @@ typedef struct ising_ctx ising_ctx;
  *              of the moving column is scaled by L_y so that W = (beta/N) W_int
  *              in both.  In 2D both protocols are the same computation.
  *              jarzynski_run_plain refuses protocol 2 in 3D
- *              (ISING_ERR_UNSUPPORTED). */
+ *              (ISING_ERR_UNSUPPORTED).
+ *   n_replica  n, the number of replicas (section 2: Tr rho_A^n = Z_n / Z^n);
+ *              0 or 2 for the paper's n = 2, at most 8.  The glue of replica r
+ *              lands in replica r+1 mod n.  -ln<e^-W> then estimates
+ *              (n-1) Delta S_n.
+ *   whole      0: the transformation moves the end of region A by one column
+ *              (x < l glued, column l switching; 0 <= l <= L-1).  1: Alba et
+ *              al.'s whole-cut transformation (section 3, eq.
+ *              off-equilibrium_evolution_of_the_couplings): the columns x < l
+ *              switch together from n decoupled replicas to glued ones
+ *              (1 <= l <= L, protocol 1 only), so <e^-W> = Z_n(l)/Z^n and
+ *              -ln<e^-W> = (n-1) S_n(l).  jarzynski_run_plain refuses
+ *              n_replica != 2 and whole = 1 (ISING_ERR_UNSUPPORTED). */
 typedef struct jz_params {
     int d, L, L_t;
     int update;
@@ -112,11 +124,13 @@ typedef struct jz_params {
     long long traj0;
     uint64_t seed;
     int protocol;
+    int n_replica;
+    int whole;
 } jz_params;
 
 /* Fills *p with defaults (n_therm = 1000, direction = +1, traj0 = 0, n_sweep = 1,
- * seed = 0, update = 0, protocol = 1) and zero sizes; returns ISING_OK or
- * ISING_ERR_ARG for p == NULL. */
+ * seed = 0, update = 0, protocol = 1, n_replica = 2, whole = 0) and zero sizes;
+ * returns ISING_OK or ISING_ERR_ARG for p == NULL. */
 int jz_params_default(jz_params* p);
 
 /* Creates a context on CUDA device `device`.

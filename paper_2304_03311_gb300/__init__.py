@@ -46,6 +46,7 @@ class JzParams(ctypes.Structure):
         ("n_step", ctypes.c_int), ("n_sweep", ctypes.c_int), ("n_therm", ctypes.c_int),
         ("n_traj", ctypes.c_int), ("direction", ctypes.c_int),
         ("traj0", ctypes.c_longlong), ("seed", ctypes.c_uint64), ("protocol", ctypes.c_int),
+        ("n_replica", ctypes.c_int), ("whole", ctypes.c_int),
     ]
 
 
@@ -179,10 +180,13 @@ METROPOLIS, SWENDSEN_WANG = 0, 1
 
 
 def make_params(d, L, L_t, beta, l, n_step, n_sweep, n_traj, seed=0, *, n_therm=1000,
-                direction=1, traj0=0, update=METROPOLIS, protocol=1) -> JzParams:
+                direction=1, traj0=0, update=METROPOLIS, protocol=1, n_replica=2,
+                whole=False) -> JzParams:
     p = jz_params_default()
     p.update = int(update)
     p.protocol = int(protocol)
+    p.n_replica = int(n_replica)
+    p.whole = int(bool(whole))
     p.d, p.L, p.L_t, p.beta, p.l = int(d), int(L), int(L_t), float(beta), int(l)
     p.n_step, p.n_sweep, p.n_traj = int(n_step), int(n_sweep), int(n_traj)
     p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF

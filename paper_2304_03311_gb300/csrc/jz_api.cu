@@ -17,7 +17,7 @@
 
 #include "jz_host.h"
 
-static_assert(sizeof(jz_params) == 72, "jz_params layout is part of the ABI");
+static_assert(sizeof(jz_params) == 80, "jz_params layout is part of the ABI");
 
 namespace jzh {
 
@@ -68,7 +68,11 @@ int check_params(const jz_params* p)
     if (p->protocol == 2 && p->d == 3 && p->n_step % p->L != 0) return ISING_ERR_ARG;
     if (p->L < 2 || p->L_t < 2 || p->L > 4096 || p->L_t > 4096) return ISING_ERR_ARG;
     if ((p->L & 1) || (p->L_t & 1)) return ISING_ERR_ODD_EXTENT;
-    if (p->l < 0 || p->l > p->L - 1) return ISING_ERR_L_RANGE;
+    if (p->n_replica != 0 && (p->n_replica < 2 || p->n_replica > 8)) return ISING_ERR_ARG;
+    if (p->whole != 0 && p->whole != 1) return ISING_ERR_ARG;
+    if (p->whole ? (p->l < 1 || p->l > p->L) : (p->l < 0 || p->l > p->L - 1))
+        return ISING_ERR_L_RANGE;
+    if (p->whole && p->protocol == 2) return ISING_ERR_ARG;
     if (p->n_step < 1 || p->n_sweep < 1 || p->n_therm < 0 || p->n_traj < 1)
         return ISING_ERR_ARG;
     if (p->direction != 1 && p->direction != -1) return ISING_ERR_ARG;
@@ -79,10 +83,26 @@ int check_params(const jz_params* p)
     if (sweeps >= 0x100000000LL) return ISING_ERR_ARG;
     // m = a N + b w_self + c w_glue must fit an int: |m| <= (2d+1) N
     if ((long long)p->n_step * (2 * p->d + 1) >= 0x7FFFFFFFLL) return ISING_ERR_ARG;
+    // |W_int| <= N * 2 n L_y (switching columns), accumulated in an int
+    const long long ly = p->d == 3 ? p->L : 1;
+    const long long cols = p->whole ? p->l : 1;
+    if ((long long)p->n_step * 2 * nrep_of(*p) * ly * cols * (p->protocol == 2 ? ly : 1) >=
+        0x7FFFFFFFLL)
+        return ISING_ERR_ARG;
     return ISING_OK;
 }
 
-jz::Geom make_geom(int d, int L, int Lt)
+int nrep_of(const jz_params& p) { return p.n_replica == 0 ? 2 : p.n_replica; }
+
+// Switching columns of a job: [l, l+1) when the end of region A moves by one
+// column, [0, l) for the whole-cut transformation.
+void cut_range(const jz_params& p, int* g0, int* g1)
+{
+    *g0 = p.whole ? 0 : p.l;
+    *g1 = p.whole ? p.l : p.l + 1;
+}
+
+jz::Geom make_geom(int d, int L, int Lt, int nrep)
 {
     jz::Geom g;
     g.L = L;
@@ -91,7 +111,8 @@ jz::Geom make_geom(int d, int L, int Lt)
     g.Lh = L / 2;
     g.G = (g.Lh + 3) / 4;
     g.GW = (g.Lh + 7) / 8;
-    g.NR = 2 * Lt * g.Ly;
+    g.nrep = nrep;
+    g.NR = nrep * Lt * g.Ly;
     return g;
 }
 
@@ -267,14 +288,14 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
               bool spins_on_device)
 {
     const jz_params& p0 = jobs[idx[0]];
-    const jz::Geom g = make_geom(p0.d, p0.L, p0.L_t);
+    const jz::Geom g = make_geom(p0.d, p0.L, p0.L_t, nrep_of(p0));
     const bool sw = p0.update == 1;   // Swendsen-Wang: one trajectory per CTA
     if (sw ? !sw_fits(g) : !shape_fits(g)) return ISING_ERR_UNSUPPORTED;
     jz::LaunchShape sh = ctx_shape(ctx, p0.d, g);
     if (sw) sh.teams = 1;
     const int n_jobs = (int)idx.size();
     const int per = sw ? 2 : 8 * p0.d;
-    const int V = 2 * p0.L_t * g.Ly * p0.L;
+    const int V = g.nrep * p0.L_t * g.Ly * p0.L;
 
     size_t n_tcut = 0;
     long long n_cta = 0, n_traj_all = 0, n_spin_traj = 0;
@@ -308,6 +329,7 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
         J.n_therm = p.n_therm;
         J.dir = p.direction;
         J.prot = p.protocol == 2 ? 2 : 1;
+        cut_range(p, &J.g0, &J.g1);
         J.n_traj = p.n_traj;
         J.traj0 = p.traj0;
         J.cta0 = cta;
@@ -387,12 +409,12 @@ int run_jobs(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const* 
             if (first) { spins_dev = dv; first = false; }
             else if (dv != spins_dev) return ISING_ERR_ARG;
         }
-    // one launch per (d, L, L_t, seed, update), jobs kept in call order within a group
-    std::map<std::tuple<int, int, int, uint64_t, int>, std::vector<int>> groups;
-    std::vector<std::tuple<int, int, int, uint64_t, int>> order;
+    // one launch per (d, L, L_t, seed, update, n), jobs kept in call order within a group
+    std::map<std::tuple<int, int, int, uint64_t, int, int>, std::vector<int>> groups;
+    std::vector<std::tuple<int, int, int, uint64_t, int, int>> order;
     for (int j = 0; j < n_jobs; ++j) {
         auto key = std::make_tuple(jobs[j].d, jobs[j].L, jobs[j].L_t, jobs[j].seed,
-                                   jobs[j].update);
+                                   jobs[j].update, nrep_of(jobs[j]));
         auto it = groups.find(key);
         if (it == groups.end()) {
             order.push_back(key);
@@ -428,6 +450,7 @@ int jz_params_default(jz_params* p)
     p->n_sweep = 1;
     p->direction = 1;
     p->protocol = 1;
+    p->n_replica = 2;
     return ISING_OK;
 }
 
@@ -513,7 +536,7 @@ int ising_set_threads(ising_ctx* ctx, int d, int L, int L_t, int threads)
         ctx->threads.erase(key);
         return ISING_OK;
     }
-    if (!threads_ok(make_geom(d, L, L_t), threads)) return ISING_ERR_ARG;
+    if (!threads_ok(make_geom(d, L, L_t, 2), threads)) return ISING_ERR_ARG;
     ctx->threads[key] = threads;
     return ISING_OK;
 }
@@ -525,7 +548,7 @@ int ising_autotune(ising_ctx* ctx, const jz_params* p, int* threads)
     if (rc) return rc;
     if (p->update != 0) return ISING_ERR_UNSUPPORTED;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
-    const jz::Geom g = make_geom(p->d, p->L, p->L_t);
+    const jz::Geom g = make_geom(p->d, p->L, p->L_t, nrep_of(*p));
     if (!shape_fits(g)) return ISING_ERR_UNSUPPORTED;
     jz_params s = *p;
     s.n_therm = 16;
@@ -588,9 +611,10 @@ int jarzynski_run_plain(ising_ctx* ctx, const jz_params* p, int64_t* work_int_ou
     if (!ctx || !p || !work_int_out) return ISING_ERR_ARG;
     int rc = check_params(p);
     if (rc) return rc;
-    if (p->update != 0 || (p->protocol == 2 && p->d == 3)) return ISING_ERR_UNSUPPORTED;
+    if (p->update != 0 || (p->protocol == 2 && p->d == 3) || nrep_of(*p) != 2 || p->whole)
+        return ISING_ERR_UNSUPPORTED;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
-    const jz::Geom g = make_geom(p->d, p->L, p->L_t);
+    const jz::Geom g = make_geom(p->d, p->L, p->L_t, 2);
     const int V = 2 * p->L_t * g.Ly * p->L;
     const bool w_dev = is_device_ptr(work_int_out);
     const bool s_dev = spins_out && is_device_ptr(spins_out);
@@ -757,7 +781,7 @@ extern "C" int jarzynski_run_noalloc(const jz_params* p, int64_t* work_int_out, 
     if (rc) return rc;
     if (p->update != 0) return ISING_ERR_UNSUPPORTED;
     if ((size_t)p->n_step * 8 * (size_t)p->d > kNoAllocMaxThresholds) return ISING_ERR_SCRATCH_LIMIT;
-    const jz::Geom g = make_geom(p->d, p->L, p->L_t);
+    const jz::Geom g = make_geom(p->d, p->L, p->L_t, nrep_of(*p));
     if (!shape_fits(g)) return ISING_ERR_UNSUPPORTED;
     if (!is_device_ptr(work_int_out)) return ISING_ERR_ARG;
     int device = 0;
@@ -778,6 +802,7 @@ extern "C" int jarzynski_run_noalloc(const jz_params* p, int64_t* work_int_out, 
     J.n_therm = p->n_therm;
     J.dir = p->direction;
     J.prot = p->protocol == 2 ? 2 : 1;
+    cut_range(*p, &J.g0, &J.g1);
     J.n_traj = p->n_traj;
     J.traj0 = p->traj0;
     J.cta0 = 0;
@@ -854,7 +879,7 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
     for (int j = 0; j < n_jobs; ++j) {
         const jz_params& p = jobs[j];
         jz::BatchJob& B = bj[j];
-        B.g = make_geom(p.d, p.L, p.L_t);
+        B.g = make_geom(p.d, p.L, p.L_t, nrep_of(p));
         B.D = p.d;
         B.fast = (B.g.Lh % 8) == 0;   // rows of whole 8-site words
         B.sh = shape_for(B.g, cta);
@@ -878,13 +903,14 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
         J.n_therm = p.n_therm;
         J.dir = p.direction;
         J.prot = p.protocol == 2 ? 2 : 1;
+        cut_range(p, &J.g0, &J.g1);
         J.n_traj = p.n_traj;
         J.traj0 = p.traj0;
         J.cta0 = 0;
         build_tables(p, J.tb, tcut, toff[j]);
         J.w_out = (long long*)work_outs[j];
         J.spins_out = nullptr;
-        const double per_traj = (double)(2 * p.L_t * B.g.Ly * p.L) *
+        const double per_traj = (double)(B.g.nrep * p.L_t * B.g.Ly * p.L) *
                                 ((double)p.n_therm + (double)p.n_step * p.n_sweep);
         for (int lo = 0; lo < p.n_traj; lo += B.sh.teams) {
             const int cnt = std::min(B.sh.teams, p.n_traj - lo);

@@ -39,7 +39,8 @@ __device__ __forceinline__ void run_item(const BatchJob& B, const PhiloxKeys& K,
         B.J.w_out[local] = (long long)(tj.dir > 0 ? s_work[tm] : -s_work[tm]) *
                            (tj.prot == 2 ? B.g.Ly : 1);
     if (has && B.J.spins_out != nullptr)
-        export_spins<D>(B.g, St, B.J.spins_out + local * (long long)(2 * B.g.Lt * B.g.Ly * B.g.L),
+        export_spins<D>(B.g, St,
+                        B.J.spins_out + local * (long long)(B.g.nrep * B.g.Lt * B.g.Ly * B.g.L),
                         tid, B.sh.team_threads);
 }
 

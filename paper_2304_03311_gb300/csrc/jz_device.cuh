@@ -37,7 +37,8 @@ struct Geom {
     int Lh;             // L / 2 sites of one colour per row
     int G;              // Philox blocks per row, ceil(Lh / 4) (the random-stream layout)
     int GW;             // shared-memory words per row, ceil(Lh / 8) (8 sites per word)
-    int NR;             // rows per colour, 2 * Lt * Ly
+    int nrep;           // replicas n
+    int NR;             // rows per colour, n * Lt * Ly
 };
 
 // How one launch maps trajectories onto threads: a team of team_threads runs
@@ -58,6 +59,7 @@ struct JobDesc {
     int dir;            // +1 forward, -1 reverse
     int n_traj;
     int prot;           // 1: every switched column together; 2: one column y at a time
+    int g0, g1;         // columns x < g0 glued, g0 <= x < g1 switching, x >= g1 self
     long long traj0;    // global index of the job's first trajectory
     long long cta0;     // first CTA of the job in the launch grid
     uint32_t tb[4];     // bulk thresholds by anti-aligned neighbour count a:

@@ -54,7 +54,9 @@ namespace jzh {
 int ensure(ising_ctx* ctx, DevBuf& b, size_t bytes);
 int is_device_ptr(const void* p);
 int check_params(const jz_params* p);
-jz::Geom make_geom(int d, int L, int Lt);
+int nrep_of(const jz_params& p);
+void cut_range(const jz_params& p, int* g0, int* g1);
+jz::Geom make_geom(int d, int L, int Lt, int nrep);
 uint32_t threshold(double x);
 jz::PhiloxKeys key_schedule(uint64_t seed);
 void build_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcut, size_t off);

@@ -60,7 +60,7 @@ traj_kernel(const Geom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
                          (tj.prot == 2 ? g.Ly : 1);
     int8_t* sp = J.spins_out;
     if (has && sp != nullptr)
-        export_spins<D>(g, St, sp + local * (long long)(2 * g.Lt * g.Ly * g.L), tid,
+        export_spins<D>(g, St, sp + local * (long long)(g.nrep * g.Lt * g.Ly * g.L), tid,
                         sh.team_threads);
 }
 

@@ -97,7 +97,7 @@ struct jz_server {
 int jz_server::launch(Slot& s, Job& j)
 {
     const jz_params& p = j.p;
-    const jz::Geom g = make_geom(p.d, p.L, p.L_t);
+    const jz::Geom g = make_geom(p.d, p.L, p.L_t, nrep_of(p));
     const size_t n_tcut = (size_t)p.n_step * 8 * p.d;
     int rc;
     if ((rc = grow_pinned((void**)&s.h_tcut, &s.h_tcut_cap, n_tcut, sizeof(uint32_t))) ||
@@ -121,6 +121,7 @@ int jz_server::launch(Slot& s, Job& j)
     J.n_therm = p.n_therm;
     J.dir = p.direction;
     J.prot = p.protocol == 2 ? 2 : 1;
+    cut_range(p, &J.g0, &J.g1);
     J.n_traj = p.n_traj;
     J.traj0 = p.traj0;
     J.cta0 = 0;
@@ -269,14 +270,14 @@ int jz_submit(jz_server* s, const jz_params* p, uint64_t* job_id)
     int rc = check_params(p);
     if (rc) return rc;
     if (p->update != 0) return ISING_ERR_UNSUPPORTED;
-    const jz::Geom g = make_geom(p->d, p->L, p->L_t);
+    const jz::Geom g = make_geom(p->d, p->L, p->L_t, nrep_of(*p));
     if (!shape_fits(g)) return ISING_ERR_UNSUPPORTED;
     std::unique_ptr<Job> j(new (std::nothrow) Job());
     if (!j) return ISING_ERR_NOMEM;
     j->p = *p;
     j->need = job_bytes(*p);
     j->res.status = ISING_ERR_PENDING;
-    j->res.updates = (long long)p->n_traj * (2LL * p->L_t * g.Ly * p->L) *
+    j->res.updates = (long long)p->n_traj * ((long long)g.nrep * p->L_t * g.Ly * p->L) *
                      ((long long)p->n_therm + (long long)p->n_step * p->n_sweep);
     {
         std::lock_guard<std::mutex> lk(s->mu);

@@ -1,7 +1,7 @@
 // jz_sw.cu -- Swendsen-Wang cluster update of the replica lattice (the update
 // of the paper's own GPU code, section 3) inside a Jarzynski transformation.
 //
-// One CTA runs one trajectory.  Shared memory holds, for the V = 2 L_t L_y L
+// One CTA runs one trajectory.  Shared memory holds, for the V = n L_t L_y L
 // sites of the replica lattice in natural order i = ((r L_t + t) L_y + y) L + x:
 //   lab[V]   int32 cluster labels (lab[i] <= i always: a forest whose roots are
 //            the smallest site index of their cluster)
@@ -66,12 +66,13 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f)
 
 struct SwGeom {
     int L, Lt, Ly;
+    int nrep;     // replicas n
     int V;        // sites of the replica lattice
     int VW;       // 32-bit words of one site bit array, ceil(V / 32)
     int SL;       // sites of one time slice, L_y * L
     int VR;       // sites of one replica, L_t * SL
     int G;        // Philox blocks per colour row of the hot start, ceil(L / 8)
-    FastDiv dL, dLy;
+    FastDiv dL, dLy, dLt;
 };
 
 // Words of the region holding bt in phases B1, B2 and the warps' root rings
@@ -97,9 +98,15 @@ __device__ __forceinline__ Site decode(int i, const SwGeom& g)
         tr = (int)fdiv((uint32_t)s.row, g.dLy);
         s.y = s.row - tr * g.Ly;
     }
-    s.r = tr >= g.Lt;
+    s.r = (int)fdiv((uint32_t)tr, g.dLt);
     s.t = tr - s.r * g.Lt;
     return s;
+}
+
+// Offset from site i at t = 1 to its glued partner's replica: r+1 mod n.
+__device__ __forceinline__ int glue_offset(const SwGeom& g, int r)
+{
+    return r == g.nrep - 1 ? -(g.nrep - 1) * g.VR : g.VR;
 }
 
 __device__ __forceinline__ int spin_bit(const uint32_t* sp, int i)
@@ -174,6 +181,7 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
     const JobDesc& J = jobs[lo];
     const long long local = (long long)blockIdx.x - __ldg(&J.cta0);
     const int l = __ldg(&J.l), dir = __ldg(&J.dir);
+    const int g0 = __ldg(&J.g0), g1 = __ldg(&J.g1);   // switching columns [g0, g1)
     const int n_step = __ldg(&J.n_step), n_sweep = __ldg(&J.n_sweep);
     const int n_therm = __ldg(&J.n_therm);
     const int prot = __ldg(&J.prot);
@@ -220,12 +228,14 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
         // moving columns
         if (step_start && warp == 0) {
             int e = 0;
-            for (int q = lane; q < 2 * g.Ly; q += 32) {
-                const int r = q / g.Ly, y = q - r * g.Ly;
+            const int nx = g1 - g0;
+            for (int q = lane; q < g.nrep * g.Ly * nx; q += 32) {
+                const int ry = q / nx, x = g0 + (q - ry * nx);
+                const int r = ry / g.Ly, y = ry - r * g.Ly;
                 if (ya >= 0 && y != ya) continue;
-                const int lo_i = (r * g.Lt * g.Ly + y) * g.L + l;
+                const int lo_i = (r * g.Lt * g.Ly + y) * g.L + x;
                 const int up_s = lo_i + g.SL;
-                const int up_g = up_s + (r ? -g.VR : g.VR);
+                const int up_g = up_s + glue_offset(g, r);
                 const int s0 = 1 - 2 * spin_bit(sp, lo_i);
                 e += s0 * ((1 - 2 * spin_bit(sp, up_s)) - (1 - 2 * spin_bit(sp, up_g)));
             }
@@ -259,10 +269,10 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
                     jt = s.t == g.Lt - 1 ? i + g.SL - g.VR : i + g.SL;
                 } else {
                     const int js = i + g.SL;
-                    const int jgl = js + (s.r ? -g.VR : g.VR);
-                    if (s.x > l) {
+                    const int jgl = js + glue_offset(g, s.r);
+                    if (s.x >= g1) {
                         jt = js;
-                    } else if (s.x < l) {
+                    } else if (s.x < g0) {
                         jg = jgl;
                         Tg = t_full;
                     } else if (ya >= 0 && s.y != ya) {
@@ -318,7 +328,7 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
             const Site s = decode<D>(i, g);
             if (wx & me) merge(lab, i, s.x == g.L - 1 ? i + 1 - g.L : i + 1);
             if (wt & me) merge(lab, i, s.t == g.Lt - 1 ? i + g.SL - g.VR : i + g.SL);
-            if (wg & me) merge(lab, i, i + g.SL + (s.r ? -g.VR : g.VR));
+            if (wg & me) merge(lab, i, i + g.SL + glue_offset(g, s.r));
             if (D == 3 && (wy & me)) merge(lab, i, s.y == g.Ly - 1 ? i + g.L - g.SL : i + g.L);
         }
         __syncthreads();
@@ -387,11 +397,13 @@ SwGeom make_swgeom(int D, const Geom& geo)
     g.Ly = geo.Ly;
     g.SL = g.Ly * g.L;
     g.VR = g.Lt * g.SL;
-    g.V = 2 * g.VR;
+    g.nrep = geo.nrep;
+    g.V = g.nrep * g.VR;
     g.VW = (g.V + 31) / 32;
     g.G = geo.G;
     g.dL = make_fastdiv((uint32_t)g.L);
     g.dLy = make_fastdiv((uint32_t)g.Ly);
+    g.dLt = make_fastdiv((uint32_t)g.Lt);
     (void)D;
     return g;
 }
@@ -400,7 +412,7 @@ SwGeom make_swgeom(int D, const Geom& geo)
 
 size_t sw_smem_bytes(const Geom& geo)
 {
-    const size_t V = (size_t)2 * geo.Lt * geo.Ly * geo.L;
+    const size_t V = (size_t)geo.nrep * geo.Lt * geo.Ly * geo.L;
     const int VW = (int)((V + 31) / 32);
     const size_t words = 3 * (size_t)VW + ring_words(VW) + (geo.Ly > 1 ? VW : 0);
     return V * sizeof(int) + words * sizeof(uint32_t);

@@ -67,6 +67,7 @@ __device__ __forceinline__ uint32_t word8(const uint4& ua, const uint4& ub, int 
 // Per-job values a team needs (read from the job descriptor once).
 struct TeamJob {
     int l, n_step, n_sweep, n_therm, dir;
+    int g0, g1;   // columns x < g0 glued, g0 <= x < g1 switching, x >= g1 self
     int prot;     // 1: every switched column together; 2: one column y at a time
     int den;      // steps of one column's run: N (protocol 1), N / L_y (protocol 2)
     const uint32_t* tcut;
@@ -175,7 +176,11 @@ struct Traj {
         const uint32_t own = own_b[w];
         const int cross_off = t == 0 ? rw : -rw;                   // self row across the cut
         const uint32_t self_w = o[cross_off];
-        const uint32_t glue_w = o[cross_off + (r == 0 ? repW : -repW)];
+        // the glued partner: replica r+1 above the cut, r-1 below it (mod n)
+        const int n = g.nrep;
+        const int glue_off = t == 0 ? (r == n - 1 ? -(n - 1) * repW : repW)
+                                    : (r == 0 ? (n - 1) * repW : -repW);
+        const uint32_t glue_w = o[cross_off + glue_off];
         const uint32_t normal = o[t == 0 ? (g.Lt - 1) * rw : (g.Lt == 2 ? -rw : rw)];
         const uint32_t m = glue_mask(lg, p);
         const uint32_t cross = (self_w & ~m) | (glue_w & m);
@@ -186,11 +191,13 @@ struct Traj {
         const uint4 ua = philox_r0(c0, sweep, hi1, lo1, c3, K);
         const uint4 ub = philox_r0(c0 + 1u, sweep, hi1, lo1, c3, K);
         uint32_t flip = accept8<D>(dsum, ua, ub, tab);
-        // Switched site x = l during the protocol: couplings beta (1 - lambda)
-        // to its own replica, beta lambda to the next one.
-        const int l = J.l;
-        if (k >= 0 && ((l - p) & 1) == 0 && ((l - p) >> 4) == q) {
-            const int jl = ((l - p) >> 1) & 7;
+        // Switching sites g0 <= x < g1 during the protocol: couplings
+        // beta (1 - lambda) to their own replica, beta lambda to the next one.
+        // Site j of the word has x = 2 (8q + j) + p.
+        const int jlo = k >= 0 ? max(((J.g0 - p + 1) >> 1) - 8 * q, 0) : 8;
+        const int jhi = min(((J.g1 - p + 1) >> 1) - 8 * q, 8);
+#pragma unroll 1
+        for (int jl = jlo; jl < jhi; ++jl) {
             const int sh = 4 * jl;
             const uint32_t ob = (own >> sh) & 1u;
             const int as = (int)(ob ^ ((self_w >> sh) & 1u));
@@ -215,7 +222,7 @@ struct Traj {
     {
         const int rw = rowW();
         const int Lt = g.Lt;
-        const int cw = 2 * Lt * rw;
+        const int cw = g.nrep * Lt * rw;
         uint32_t* own_b = S + c * cw;
         const uint32_t* oth = S + (1 - c) * cw;
         const uint32_t c3 = (uint32_t)c | c3base;
@@ -224,7 +231,7 @@ struct Traj {
         const int pc = (c + y) & 1;
         const int wrap_up = -(Lt - 1) * rw;
 #pragma unroll 1
-        for (int r = 0; r < 2; ++r) {
+        for (int r = 0; r < g.nrep; ++r) {
             int t = t0;
             int w = (r * Lt + t0) * rw + y * W() + q;
             uint32_t c0 = (uint32_t)(((r * Lt + t0) * Ly() + y) * g.G + 2 * q);
@@ -248,12 +255,12 @@ struct Traj {
     __device__ __forceinline__ void hot_start() const
     {
         const int rw = rowW();
-        const int cw = 2 * g.Lt * rw;
+        const int cw = g.nrep * g.Lt * rw;
         const uint32_t cstride = (uint32_t)(TS * Ly() * g.G);
         for (int c = 0; c < 2; ++c) {
             uint32_t* base = S + c * cw;
             const uint32_t c3 = (uint32_t)c | c3base | (1u << 30);
-            for (int r = 0; r < 2; ++r) {
+            for (int r = 0; r < g.nrep; ++r) {
                 int w = (r * g.Lt + t0) * rw + y * W() + q;
                 uint32_t c0 = (uint32_t)(((r * g.Lt + t0) * Ly() + y) * g.G + 2 * q);
                 for (int t = t0; t < g.Lt; t += TS, w += TS * rw, c0 += cstride) {
@@ -292,9 +299,9 @@ __device__ __forceinline__ int run_trajectory(const Geom& g, const PhiloxKeys& K
     tr.hot_start();
     bar();
     int dE = 0;
-    // thermalisation at the start geometry: forward lambda = 0 (x < l glued),
-    // reverse lambda = 1 (x <= l glued)
-    const int lg_therm = J.dir > 0 ? J.l : J.l + 1;
+    // thermalisation at the start geometry: forward lambda = 0 (x < g0 glued),
+    // reverse lambda = 1 (x < g1 glued)
+    const int lg_therm = J.dir > 0 ? J.g0 : J.g1;
     for (int s = 0; s < J.n_therm; ++s) {
         tr.half_sweep(0, (uint32_t)s, -1, lg_therm, J, 0, 0, false, dE);
         bar();
@@ -309,10 +316,10 @@ __device__ __forceinline__ int run_trajectory(const Geom& g, const PhiloxKeys& K
         const int kp = k + 1 - ya * J.den;
         const int w_self = J.dir > 0 ? J.den - kp : kp;
         const int w_glue = J.dir > 0 ? kp : J.den - kp;
-        int kk = k, lg = J.l;
+        int kk = k, lg = J.g0;
         if (J.prot == 2 && tr.y != ya) {
             kk = -1;
-            lg = (tr.y < ya) == (J.dir > 0) ? J.l + 1 : J.l;
+            lg = (tr.y < ya) == (J.dir > 0) ? J.g1 : J.g0;
         }
         for (int i = 0; i < J.n_sweep; ++i, ++s) {
             tr.half_sweep(0, s, kk, lg, J, w_self, w_glue, i == 0, dE);
@@ -329,7 +336,7 @@ template <int D>
 __device__ __forceinline__ void export_spins(const Geom& g, const uint32_t* S_team, int8_t* dst,
                                              int tid, int nthr)
 {
-    const int V = 2 * g.Lt * g.Ly * g.L;
+    const int V = g.nrep * g.Lt * g.Ly * g.L;
     for (int i = tid; i < V; i += nthr) {
         const int x = i % g.L;
         const int R = i / g.L;                      // (r, t, y) row
@@ -353,6 +360,8 @@ __device__ __forceinline__ TeamJob team_job(const JobDesc& J, int ly)
     t.n_therm = __ldg(&J.n_therm);
     t.dir = __ldg(&J.dir);
     t.prot = __ldg(&J.prot);
+    t.g0 = __ldg(&J.g0);
+    t.g1 = __ldg(&J.g1);
     t.den = t.prot == 2 ? t.n_step / ly : t.n_step;
     t.tcut = J.tcut;
     return t;

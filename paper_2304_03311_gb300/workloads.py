@@ -36,10 +36,12 @@ class Job:
     traj0: int = 0
     update: int = 0          # 0 checkerboard Metropolis, 1 Swendsen-Wang
     protocol: int = 1        # 1 every switched column together, 2 one column at a time
+    n_replica: int = 2       # replicas n
+    whole: bool = False      # True: whole-cut transformation of the columns x < l
 
     @property
     def sites(self) -> int:
-        return 2 * self.L_t * self.L ** (self.d - 1)
+        return self.n_replica * self.L_t * self.L ** (self.d - 1)
 
     @property
     def updates(self) -> int:

@@ -58,16 +58,17 @@ def test_device_code_is_sm103a(lib):
 
 
 def test_struct_layout_matches_header(lib):
-    # jz_params: 4 ints, double, 6 ints, long long, uint64, int (+4 padding) -> 72 bytes
-    assert ctypes.sizeof(jz.JzParams) == 72
+    # jz_params: 4 ints, double, 6 ints, long long, uint64, 3 ints (+4 padding) -> 80 bytes
+    assert ctypes.sizeof(jz.JzParams) == 80
     offs = {name: getattr(jz.JzParams, name).offset for name, _ in jz.JzParams._fields_}
     assert offs == {"d": 0, "L": 4, "L_t": 8, "update": 12, "beta": 16, "l": 24, "n_step": 28,
                     "n_sweep": 32, "n_therm": 36, "n_traj": 40, "direction": 44, "traj0": 48,
-                    "seed": 56, "protocol": 64}
+                    "seed": 56, "protocol": 64, "n_replica": 68, "whole": 72}
     p = jz.jz_params_default()
     assert (p.n_therm, p.n_sweep, p.direction, p.traj0, p.seed) == (1000, 1, 1, 0, 0)
     assert p.update == jz.METROPOLIS
     assert p.protocol == 1
+    assert (p.n_replica, p.whole) == (2, 0)
 
 
 def test_strerror_and_host_only_entry_points(lib):
