@@ -83,8 +83,9 @@ typedef struct ising_ctx ising_ctx;
  *                 per trajectory; needs about 4.5 V (2D) or 4.6 V (3D) bytes
  *                 of shared memory for the V = 2 L_t L^(d-1) sites (at most
  *                 227 KiB, V up to about 50,000), else ISING_ERR_UNSUPPORTED.
- *                 Served by jarzynski_run_ex and jarzynski_run_batch; the
- *                 other entry points return ISING_ERR_UNSUPPORTED for it.
+ *                 Served by jarzynski_run_ex, jarzynski_run_batch and the
+ *                 server (jz_submit); the other entry points return
+ *                 ISING_ERR_UNSUPPORTED for it.
  *              Other values: ISING_ERR_ARG.
  *   beta       coupling, 0 <= beta <= 4
  *   l          width of region A before the move, 0 <= l <= L-1

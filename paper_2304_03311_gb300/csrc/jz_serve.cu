@@ -51,9 +51,16 @@ struct Slot {
     size_t h_work_cap = 0;             // entries
 };
 
+// Threshold words of a job: per step 8d switched-site thresholds (Metropolis)
+// or the two switched bond thresholds (Swendsen-Wang).
+size_t tcut_words(const jz_params& p)
+{
+    return (size_t)p.n_step * (p.update == 1 ? 2 : 8 * p.d);
+}
+
 size_t job_bytes(const jz_params& p)
 {
-    const size_t tcut = (size_t)p.n_step * 8 * p.d * sizeof(uint32_t);
+    const size_t tcut = tcut_words(p) * sizeof(uint32_t);
     return ((tcut + 255) & ~(size_t)255) + 256 + (size_t)p.n_traj * sizeof(int64_t) + 256;
 }
 
@@ -98,7 +105,7 @@ int jz_server::launch(Slot& s, Job& j)
 {
     const jz_params& p = j.p;
     const jz::Geom g = make_geom(p.d, p.L, p.L_t, nrep_of(p));
-    const size_t n_tcut = (size_t)p.n_step * 8 * p.d;
+    const size_t n_tcut = tcut_words(p);
     int rc;
     if ((rc = grow_pinned((void**)&s.h_tcut, &s.h_tcut_cap, n_tcut, sizeof(uint32_t))) ||
         (rc = grow_pinned((void**)&s.h_work, &s.h_work_cap, (size_t)p.n_traj, sizeof(int64_t))))
@@ -106,7 +113,8 @@ int jz_server::launch(Slot& s, Job& j)
     s.tcut.assign(n_tcut, 0);
     jz::JobDesc& J = *s.h_desc;
     std::memset(&J, 0, sizeof J);
-    build_tables(p, J.tb, s.tcut, 0);
+    if (p.update == 1) build_bond_tables(p, J.tb, s.tcut, 0);
+    else build_tables(p, J.tb, s.tcut, 0);
     std::memcpy(s.h_tcut, s.tcut.data(), n_tcut * sizeof(uint32_t));
     char* d = nullptr;
     if ((rc = cuda_err(cudaMallocAsync((void**)&d, j.need, s.stream)))) return rc;
@@ -135,8 +143,11 @@ int jz_server::launch(Slot& s, Job& j)
                                        cudaMemcpyHostToDevice, s.stream))) ||
         (rc = cuda_err(cudaMemcpyAsync(d_desc, s.h_desc, sizeof(jz::JobDesc),
                                        cudaMemcpyHostToDevice, s.stream))) ||
-        (rc = cuda_err(jz::launch_traj(p.d, g, K, d_desc, 1,
-                                       (p.n_traj + sh.teams - 1) / sh.teams, sh, s.stream))) ||
+        (rc = cuda_err(p.update == 1   // Swendsen-Wang: one trajectory per CTA
+                           ? jz::launch_sw(p.d, g, K, d_desc, 1, p.n_traj, s.stream)
+                           : jz::launch_traj(p.d, g, K, d_desc, 1,
+                                             (p.n_traj + sh.teams - 1) / sh.teams, sh,
+                                             s.stream))) ||
         (rc = cuda_err(jz::launch_estimator(d_work, p.n_traj, p.beta / (double)p.n_step,
                                             p.direction, B, d_est, s.stream))) ||
         (rc = cuda_err(cudaMemcpyAsync(s.h_est, d_est, 3 * sizeof(double),
@@ -269,9 +280,8 @@ int jz_submit(jz_server* s, const jz_params* p, uint64_t* job_id)
     if (!s || !p || !job_id) return ISING_ERR_ARG;
     int rc = check_params(p);
     if (rc) return rc;
-    if (p->update != 0) return ISING_ERR_UNSUPPORTED;
     const jz::Geom g = make_geom(p->d, p->L, p->L_t, nrep_of(*p));
-    if (!shape_fits(g)) return ISING_ERR_UNSUPPORTED;
+    if (p->update == 1 ? !sw_fits(g) : !shape_fits(g)) return ISING_ERR_UNSUPPORTED;
     std::unique_ptr<Job> j(new (std::nothrow) Job());
     if (!j) return ISING_ERR_NOMEM;
     j->p = *p;

@@ -9,6 +9,7 @@
 //   bx, bt, bg, by [VW]  bond bits of the current sweep by direction; bt
 //            doubles as the warps' rings of 32 queued cluster roots, bg as the
 //            roots' flip bits
+//   bq       per warp 32 queued bonds
 // Warps work on chunks of 32 consecutive sites.  One sweep is four phases
 // separated by CTA barriers:
 //   B1 every site draws one Philox block (i, s, traj, dir<<1 | l<<2 | 2<<30);
@@ -17,9 +18,10 @@
 //      bond threshold floor(2^32 (1 - e^{-2K})).  +x bonds between lanes of
 //      one chunk form runs found by one ballot; each site's label is set to
 //      its run's first site.  The other active bonds become bits.
-//   B2 each recorded bond merges two clusters by lock-free union with
-//      atomicMin (the larger root is hooked under the smaller one, so the
-//      root of a cluster is its smallest site index);
+//   B2 the recorded bonds, queued per warp and taken 32 at a time, merge
+//      clusters by lock-free union with atomicMin (the larger root is hooked
+//      under the smaller one, so the root of a cluster is its smallest site
+//      index);
 //   C  every site stores its root; the roots, queued 32 at a time, draw
 //      Philox block (root, s, traj, dir<<1 | l<<2 | 3<<30) and a cluster
 //      flips iff the top bit of its root's word 0 is set;
@@ -171,6 +173,7 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
     uint32_t* by = bg + g.VW;       // +y bonds (3D)
     uint32_t* fb = bg;              // root flip bits (phases C, D)
     int* s_ring = (int*)bt;         // per warp a ring of 32 queued roots (phase C)
+    int* s_bq = (int*)(by + (D == 3 ? g.VW : 0));   // per warp 32 queued bonds (phase B2)
 
     // the job owning this CTA: the last j with jobs[j].cta0 <= blockIdx.x
     int lo = 0, hi = n_jobs - 1;
@@ -315,21 +318,52 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
         }
         __syncthreads();
         // phase B2: the recorded bonds merge clusters (+x bonds inside a
-        // chunk are already joined by the run labels)
-        for (int base = warp * 32; base < g.V; base += chunk) {
-            const int i = base + lane;
-            const int q = base >> 5;
-            const uint32_t wx = bx[q], wt = bt[q], wg = bg[q];
-            const uint32_t wy = D == 3 ? by[q] : 0u;
+        // chunk are already joined by the run labels).  Each warp queues its
+        // chunks' bonds as (site << 2 | direction) and merges them 32 at a
+        // time, so every merge round runs on a full warp.
+        {
+            int* bq = s_bq + warp * 32;
+            int nb = 0;
+            auto merge_entry = [&](int e) {
+                const int i = e >> 2, dirn = e & 3;
+                const Site s = decode<D>(i, g);
+                int j;
+                if (dirn == 0) j = s.x == g.L - 1 ? i + 1 - g.L : i + 1;
+                else if (dirn == 1) j = s.t == g.Lt - 1 ? i + g.SL - g.VR : i + g.SL;
+                else if (dirn == 2) j = i + g.SL + glue_offset(g, s.r);
+                else j = s.y == g.Ly - 1 ? i + g.L - g.SL : i + g.L;
+                merge(lab, i, j);
+            };
+            auto push = [&](uint32_t m, int e) {   // m: the warp's mask of bonds
+                const int c = __popc(m);
+                if (c == 0) return;
+                const bool mine = (m >> lane) & 1u;
+                const int rank = __popc(m & ((1u << lane) - 1u));
+                const int room = 32 - nb;
+                if (mine && rank < room) bq[nb + rank] = e;
+                nb += c;
+                if (nb >= 32) {
+                    __syncwarp();
+                    merge_entry(bq[lane]);
+                    __syncwarp();
+                    if (mine && rank >= room) bq[rank - room] = e;
+                    nb -= 32;
+                }
+            };
+            for (int base = warp * 32; base < g.V; base += chunk) {
+                const int i = base + lane;
+                const int q = base >> 5;
+                const uint32_t wx = bx[q], wt = bt[q], wg = bg[q];
+                const uint32_t wy = D == 3 ? by[q] : 0u;
+                __syncwarp();
+                if (lane == 0) bg[q] = 0u;      // bg doubles as the flip bits of phase C
+                push(wx, i << 2);
+                push(wt, (i << 2) | 1);
+                push(wg, (i << 2) | 2);
+                if (D == 3) push(wy, (i << 2) | 3);
+            }
             __syncwarp();
-            if (lane == 0) bg[q] = 0u;          // bg doubles as the flip bits of phase C
-            const uint32_t me = 1u << lane;
-            if (((wx | wt | wg | wy) & me) == 0u) continue;
-            const Site s = decode<D>(i, g);
-            if (wx & me) merge(lab, i, s.x == g.L - 1 ? i + 1 - g.L : i + 1);
-            if (wt & me) merge(lab, i, s.t == g.Lt - 1 ? i + g.SL - g.VR : i + g.SL);
-            if (wg & me) merge(lab, i, i + g.SL + glue_offset(g, s.r));
-            if (D == 3 && (wy & me)) merge(lab, i, s.y == g.Ly - 1 ? i + g.L - g.SL : i + g.L);
+            if (lane < nb) merge_entry(bq[lane]);
         }
         __syncthreads();
         // phase C: every site stores its root; the roots are queued per warp
@@ -414,7 +448,8 @@ size_t sw_smem_bytes(const Geom& geo)
 {
     const size_t V = (size_t)geo.nrep * geo.Lt * geo.Ly * geo.L;
     const int VW = (int)((V + 31) / 32);
-    const size_t words = 3 * (size_t)VW + ring_words(VW) + (geo.Ly > 1 ? VW : 0);
+    const size_t words = 3 * (size_t)VW + ring_words(VW) + (geo.Ly > 1 ? VW : 0) +
+                         (size_t)(kSwThreads / 32) * 32;
     return V * sizeof(int) + words * sizeof(uint32_t);
 }
 

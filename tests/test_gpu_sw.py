@@ -135,7 +135,21 @@ def test_full_scan_workload_sampled(ctx):
             assert got[t] == W[0], (jl, t)
 
 
-@pytest.mark.parametrize("entry", ["autotune", "plain", "noalloc", "plan", "server"])
+def test_server_runs_the_cluster_update(ctx):
+    jobs = [SMALL[0], SMALL[9], SMALL[1]]
+    server = jz.jz_server_create(ctx, 1 << 30, 2)
+    try:
+        ids = [jz.jz_submit(server, params(j)) for j in jobs]
+        for jid, j in zip(ids, jobs):
+            assert jz.jz_wait(server, jid, 600.0).status == 0
+            W = np.empty(j.n_traj, dtype=np.int64)
+            jz.jz_server_work(server, jid, W)
+            np.testing.assert_array_equal(W, oracle_run(j)[0])
+    finally:
+        jz.jz_server_free(server)
+
+
+@pytest.mark.parametrize("entry", ["autotune", "plain", "noalloc", "plan"])
 def test_other_entry_points_refuse_the_cluster_update(ctx, entry):
     job = SMALL[0]
     p = params(job)
@@ -147,14 +161,8 @@ def test_other_entry_points_refuse_the_cluster_update(ctx, entry):
             jz.jarzynski_run_plain(ctx, p, w)
         elif entry == "noalloc":
             jz.jarzynski_run_noalloc(p, w)
-        elif entry == "plan":
-            jz.jz_plan_create(ctx, [p], [w])
         else:
-            srv = jz.jz_server_create(ctx, 1 << 30, 1)
-            try:
-                jz.jz_submit(srv, p)
-            finally:
-                jz.jz_server_free(srv)
+            jz.jz_plan_create(ctx, [p], [w])
     assert e.value.code == jz.ISING_ERR_UNSUPPORTED
 
 
