@@ -1,7 +1,7 @@
 // jz_sw.cu -- Swendsen-Wang cluster update of the replica lattice (the update
 // of the paper's own GPU code, section 3) inside a Jarzynski transformation.
 //
-// One CTA runs one trajectory.  Shared memory holds, for the V = n L_t L_y L
+// One CTA (256 threads in 2D, 512 in 3D) runs one trajectory.  Shared memory holds, for the V = n L_t L_y L
 // sites of the replica lattice in natural order i = ((r L_t + t) L_y + y) L + x:
 //   lab[V]   int32 cluster labels (lab[i] <= i always: a forest whose roots are
 //            the smallest site index of their cluster)
@@ -44,7 +44,9 @@ namespace jz {
 
 namespace {
 
-constexpr int kSwThreads = 256;
+// Threads per CTA (one trajectory): 256 in 2D, 512 in 3D, whose extra +y
+// bonds make the union phase longer (measured on 2D 64^2 and 3D 16^3).
+__host__ __device__ constexpr int sw_threads(int D) { return D == 3 ? 512 : 256; }
 
 // Division by a fixed divisor d >= 1 for numerators n < 2^31 (Granlund and
 // Montgomery, PLDI'94): with s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d)
@@ -78,10 +80,10 @@ struct SwGeom {
 };
 
 // Words of the region holding bt in phases B1, B2 and the warps' root rings
-// in phase C.
-__host__ __device__ inline int ring_words(int VW)
+// (32 per warp) in phase C.
+__host__ __device__ inline int ring_words(int VW, int threads)
 {
-    return VW > kSwThreads ? VW : kSwThreads;
+    return VW > threads ? VW : threads;
 }
 
 struct Site {
@@ -161,7 +163,7 @@ __device__ __forceinline__ void merge(int* lab, int a, int b)
 }
 
 template <int D>
-__global__ void __launch_bounds__(kSwThreads)
+__global__ void __launch_bounds__(sw_threads(D))
 sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, int n_jobs)
 {
     extern __shared__ uint32_t smem[];
@@ -169,7 +171,7 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
     uint32_t* sp = smem + g.V;
     uint32_t* bx = sp + g.VW;       // +x bonds leaving a warp chunk or its row
     uint32_t* bt = bx + g.VW;       // +t bonds inside one replica
-    uint32_t* bg = bt + ring_words(g.VW);   // +t bonds into replica r+1
+    uint32_t* bg = bt + ring_words(g.VW, sw_threads(D));   // +t bonds into replica r+1
     uint32_t* by = bg + g.VW;       // +y bonds (3D)
     uint32_t* fb = bg;              // root flip bits (phases C, D)
     int* s_ring = (int*)bt;         // per warp a ring of 32 queued roots (phase C)
@@ -448,8 +450,9 @@ size_t sw_smem_bytes(const Geom& geo)
 {
     const size_t V = (size_t)geo.nrep * geo.Lt * geo.Ly * geo.L;
     const int VW = (int)((V + 31) / 32);
-    const size_t words = 3 * (size_t)VW + ring_words(VW) + (geo.Ly > 1 ? VW : 0) +
-                         (size_t)(kSwThreads / 32) * 32;
+    const int threads = sw_threads(geo.Ly > 1 ? 3 : 2);
+    const size_t words = 3 * (size_t)VW + ring_words(VW, threads) + (geo.Ly > 1 ? VW : 0) +
+                         (size_t)threads;
     return V * sizeof(int) + words * sizeof(uint32_t);
 }
 
@@ -462,7 +465,7 @@ cudaError_t launch_sw(int D, const Geom& geo, const PhiloxKeys& K, const JobDesc
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)n_cta, kSwThreads, smem, st>>>(g, K, jobs, n_jobs);
+    kern<<<(unsigned)n_cta, sw_threads(D), smem, st>>>(g, K, jobs, n_jobs);
     return cudaGetLastError();
 }
 
