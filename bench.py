@@ -79,6 +79,8 @@ def parse_args():
     ap.add_argument("--protocol", type=int, choices=[1, 2], default=1,
                     help="1: every switched column together; 2: one column at a time (3D)")
     ap.add_argument("--n-replica", type=int, default=2, help="replicas n (Renyi index)")
+    ap.add_argument("--lattice", type=str, default=None,
+                    help="L,L_t override for every job of the config (l values kept below L)")
     ap.add_argument("--whole", action="store_true",
                     help="whole-cut transformations (cut lengths l+1) instead of moving the "
                          "end of region A by one column")
@@ -102,8 +104,12 @@ def dist_env():
 
 
 def workload_for(config: int, rank: int, traj_per_l=None, n_step=None, update="metropolis",
-                 protocol=1, n_therm=None, n_replica=2, whole=False):
+                 protocol=1, n_therm=None, n_replica=2, whole=False, lattice=None):
     w = wl.CONFIGS[config]()
+    if lattice:
+        L, L_t = (int(v) for v in lattice.split(","))
+        w.jobs = [j.with_(L=L, L_t=L_t) for j in w.jobs if j.l < L]
+        w.name += f"_L{L}_T{L_t}"
     if n_replica != 2:
         w.jobs = [j.with_(n_replica=n_replica) for j in w.jobs]
         w.name += f"_n{n_replica}"
@@ -300,7 +306,7 @@ def run_ours(args):
     import paper_2304_03311_gb300 as jz
 
     w = workload_for(args.config, rank, args.traj_per_l, args.n_step, args.update, args.protocol,
-                     args.n_therm, args.n_replica, args.whole)
+                     args.n_therm, args.n_replica, args.whole, args.lattice)
     sw = args.update == "sw"
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
@@ -332,7 +338,10 @@ def run_ours(args):
                 tuned[str(shape)] = args.threads
             elif not args.no_autotune and not sw:
                 p = params[w.jobs.index(j)]
-                tuned[str(shape)] = jz.ising_autotune(ctx, p)
+                try:
+                    tuned[str(shape)] = jz.ising_autotune(ctx, p)
+                except jz.IsingError:      # lattices beyond shared memory are not tuned
+                    tuned[str(shape)] = "default (lattice in HBM)"
 
     def estimate(buffers, gathered_world):
         res = []
@@ -462,7 +471,10 @@ def run_ours(args):
                    for j in w.jobs]
         if not args.no_autotune and not args.threads:
             for shape, j in {(j.d, j.L, j.L_t): j for j in w.jobs}.items():
-                jz.ising_autotune(ctx, mparams[w.jobs.index(j)])
+                try:
+                    jz.ising_autotune(ctx, mparams[w.jobs.index(j)])
+                except jz.IsingError:
+                    pass
         with torch.cuda.stream(stream):
             jz.jarzynski_run_batch(ctx, mparams, outs)
             m0 = torch.cuda.Event(enable_timing=True)
@@ -594,7 +606,7 @@ def run_reference(args):
     oracle.build()
     threads = oracle.max_threads()
     w = workload_for(args.config, 0, args.traj_per_l, args.n_step, args.update, args.protocol,
-                     args.n_therm, args.n_replica, args.whole)
+                     args.n_therm, args.n_replica, args.whole, args.lattice)
     jobs = w.jobs[:: max(1, len(w.jobs) // 2)][:2]
     n_per = threads
 

@@ -63,7 +63,7 @@ extern "C" {
 #define ISING_ERR_NOMEM       -4  /* device allocation or HBM budget exceeded    */
 #define ISING_ERR_CUDA        -5  /* a CUDA runtime call failed                  */
 #define ISING_ERR_TIMEOUT     -6  /* a bounded device wait gave up               */
-#define ISING_ERR_UNSUPPORTED -7  /* d not in {2,3}, lattice too large for SMEM  */
+#define ISING_ERR_UNSUPPORTED -7  /* d not in {2,3}, lattice too large, option not served */
 #define ISING_ERR_NOT_FOUND   -8  /* unknown job id                              */
 #define ISING_ERR_PENDING     -9  /* job not finished yet (jz_poll)              */
 #define ISING_ERR_SCRATCH_LIMIT -10 /* too large for jarzynski_run_noalloc     */
@@ -162,7 +162,12 @@ int jarzynski_run(ising_ctx* ctx, int d, int L, int L_t, double beta, int l,
 /* As jarzynski_run with every parameter of jz_params.  spins_out (nullable,
  * caller-owned, host or device) receives the final configuration of each
  * trajectory as int8 +-1 in the order [traj][r][t][y][x] (x fastest, n_traj *
- * 2 * L_t * L_y * L bytes). */
+ * n * L_t * L_y * L bytes).  A Metropolis replica lattice (n * L_t * L_y * L
+ * / 4 bytes nibble-packed) that does not fit one CTA's 227 KiB of shared
+ * memory runs from an HBM slice per CTA instead (for example the paper's 3D
+ * L = 48, L_t = 4L lattice); such shapes need only L_y ceil(L/16) <= 512, and
+ * the persistent plan, server, allocation-free call and autotuner refuse them
+ * (ISING_ERR_UNSUPPORTED). */
 int jarzynski_run_ex(ising_ctx* ctx, const jz_params* p, int64_t* work_int_out,
                      int8_t* spins_out);
 
@@ -212,7 +217,9 @@ void jz_plan_free(jz_plan* plan);
  * arrive while others run overlap on the device -- and, when its completion
  * event fires, copies the result back and frees the slot for the next job.
  * A job's lattice and random state stay in one CTA's shared memory for its
- * whole protocol.  Results are bit-identical to running the job alone. */
+ * whole protocol (jobs whose lattice does not fit are refused with
+ * ISING_ERR_UNSUPPORTED).  Results are bit-identical to running the job
+ * alone. */
 typedef struct jz_server jz_server;
 
 typedef struct jz_result {

@@ -250,11 +250,15 @@ jz::LaunchShape shape_for(const jz::Geom& g, int cta_threads)
     return s;
 }
 
-// Whether g can run at all: one team's lattice fits a CTA's shared memory and
-// one time slice of words fits 512 threads.
+// Whether one time slice of words fits a CTA of 512 threads (any lattice
+// satisfying this runs, with its lattice in HBM if not in shared memory).
+bool threads_fit(const jz::Geom& g) { return g.GW * g.Ly <= 512; }
+
+// Whether g runs with its lattice in shared memory: one team's lattice fits a
+// CTA's shared memory and one time slice of words fits 512 threads.
 bool shape_fits(const jz::Geom& g)
 {
-    return jz::traj_smem_bytes(g) <= jz::kMaxSmemPerCta && g.GW * g.Ly <= 512;
+    return jz::traj_smem_bytes(g) <= jz::kMaxSmemPerCta && threads_fit(g);
 }
 
 // A CTA size is admissible: a multiple of 32 for warp teams, col * TS with
@@ -290,7 +294,9 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
     const jz_params& p0 = jobs[idx[0]];
     const jz::Geom g = make_geom(p0.d, p0.L, p0.L_t, nrep_of(p0));
     const bool sw = p0.update == 1;   // Swendsen-Wang: one trajectory per CTA
-    if (sw ? !sw_fits(g) : !shape_fits(g)) return ISING_ERR_UNSUPPORTED;
+    if (sw ? !sw_fits(g) : !threads_fit(g)) return ISING_ERR_UNSUPPORTED;
+    // Metropolis lattices beyond shared memory run from HBM, one slice per CTA
+    const bool in_hbm = !sw && !shape_fits(g);
     jz::LaunchShape sh = ctx_shape(ctx, p0.d, g);
     if (sw) sh.teams = 1;
     const int n_jobs = (int)idx.size();
@@ -359,9 +365,16 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
         if ((rc = cuda_err(jz::launch_sw(p0.d, g, K, (const jz::JobDesc*)ctx->jobs.ptr, n_jobs,
                                          n_cta, st))))
             return rc;
-    } else if ((rc = cuda_err(jz::launch_traj(p0.d, g, K, (const jz::JobDesc*)ctx->jobs.ptr,
-                                              n_jobs, n_cta, sh, st)))) {
-        return rc;
+    } else {
+        uint32_t* gS = nullptr;
+        if (in_hbm) {
+            const size_t words = (size_t)n_cta * sh.teams * 2 * g.NR * g.GW;
+            if ((rc = ensure(ctx, ctx->lattice, words * sizeof(uint32_t)))) return rc;
+            gS = (uint32_t*)ctx->lattice.ptr;
+        }
+        if ((rc = cuda_err(jz::launch_traj(p0.d, g, K, (const jz::JobDesc*)ctx->jobs.ptr,
+                                           n_jobs, n_cta, sh, st, gS))))
+            return rc;
     }
     if (!outs_on_device || (n_spin_traj && !spins_on_device)) {
         long long c = 0, so = 0;
@@ -488,7 +501,7 @@ void ising_replica_free(ising_ctx* ctx)
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     for (DevBuf* b : {&ctx->tcut, &ctx->jobs, &ctx->work, &ctx->spins, &ctx->est_in,
-                      &ctx->est_out})
+                      &ctx->est_out, &ctx->lattice})
         if (b->ptr) cudaFree(b->ptr);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;

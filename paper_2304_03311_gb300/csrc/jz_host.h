@@ -15,8 +15,11 @@
 
 namespace jz {
 size_t traj_smem_bytes(const Geom& g);
+// gS: nullptr to keep the lattices in shared memory, else an HBM buffer of
+// n_cta * sh.teams * 2 * NR * GW words, one slice per CTA.
 cudaError_t launch_traj(int D, const Geom& g, const PhiloxKeys& K, const JobDesc* jobs,
-                        int n_jobs, long long n_cta, const LaunchShape& sh, cudaStream_t st);
+                        int n_jobs, long long n_cta, const LaunchShape& sh, cudaStream_t st,
+                        uint32_t* gS = nullptr);
 cudaError_t launch_estimator(const long long* w_int, int n, double scale, int direction,
                              int n_blocks, double* out, cudaStream_t st);
 size_t sw_smem_bytes(const Geom& g);
@@ -45,6 +48,7 @@ struct ising_ctx {
     size_t budget = 0;   // 0 = unlimited
     size_t used = 0;
     DevBuf tcut, jobs, work, spins, est_in, est_out;
+    DevBuf lattice;   // HBM lattices of shapes too large for shared memory
     std::vector<uint32_t> h_tcut;
     std::vector<jz::JobDesc> h_jobs;
     std::map<std::tuple<int, int, int>, int> threads;   // per-shape CTA size (tuned)
@@ -68,6 +72,7 @@ void build_bond_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>
 bool sw_fits(const jz::Geom& g);
 jz::LaunchShape shape_for(const jz::Geom& g, int cta_threads);
 bool shape_fits(const jz::Geom& g);
+bool threads_fit(const jz::Geom& g);
 bool threads_ok(const jz::Geom& g, int threads);
 jz::LaunchShape ctx_shape(const ising_ctx* ctx, int d, const jz::Geom& g);
 int cuda_err(cudaError_t e);

@@ -21,13 +21,16 @@ __device__ __forceinline__ int find_job(const JobDesc* __restrict__ jobs, int n_
 constexpr int kMaxTeams = 64;
 
 // One CTA runs `teams` trajectories of the job that owns it (sh.teams per
-// CTA; warp teams sync with __syncwarp, a CTA team with __syncthreads).
+// CTA; warp teams sync with __syncwarp, a CTA team with __syncthreads).  The
+// lattices live in shared memory, or, when they do not fit there (gS !=
+// nullptr), in this CTA's own slice of an HBM buffer (L1/L2-cached).
 template <int D, bool FAST, int CW, int CLY, bool WARP>
 __global__ void __launch_bounds__(512)
 traj_kernel(const Geom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, int n_jobs,
-            const LaunchShape sh)
+            const LaunchShape sh, uint32_t* __restrict__ gS)
 {
-    extern __shared__ uint32_t S[];
+    extern __shared__ uint32_t S_shared[];
+    uint32_t* S = gS ? gS + (size_t)blockIdx.x * sh.teams * (2 * g.NR * g.GW) : S_shared;
     __shared__ int s_work[kMaxTeams];
     __shared__ uint32_t s_tab[8];
 
@@ -130,33 +133,36 @@ size_t traj_smem_bytes(const Geom& g) { return (size_t)2 * g.NR * g.GW * sizeof(
 template <int D, bool FAST, int CW, int CLY>
 static cudaError_t launch_traj_t(const Geom& g, const PhiloxKeys& K, const JobDesc* jobs,
                                  int n_jobs, long long n_cta, const LaunchShape& sh,
-                                 cudaStream_t st)
+                                 cudaStream_t st, uint32_t* gS)
 {
-    const size_t smem = traj_smem_bytes(g) * sh.teams;
+    const size_t smem = gS ? 0 : traj_smem_bytes(g) * sh.teams;
     auto kern = sh.warp ? traj_kernel<D, FAST, CW, CLY, true> : traj_kernel<D, FAST, CW, CLY, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)n_cta, sh.cta_threads, smem, st>>>(g, K, jobs, n_jobs, sh);
+    kern<<<(unsigned)n_cta, sh.cta_threads, smem, st>>>(g, K, jobs, n_jobs, sh, gS);
     return cudaGetLastError();
 }
 
 // Shapes with compile-time row geometry: 2D L = 16 and 64 (GW = 1, 4) and 3D
 // L = 16 (GW = 1, L_y = 16); every other shape runs the generic instantiation.
 cudaError_t launch_traj(int D, const Geom& g, const PhiloxKeys& K, const JobDesc* jobs,
-                        int n_jobs, long long n_cta, const LaunchShape& sh, cudaStream_t st)
+                        int n_jobs, long long n_cta, const LaunchShape& sh, cudaStream_t st,
+                        uint32_t* gS)
 {
     const bool fast = (g.Lh % 8) == 0;
     if (D == 2) {
-        if (fast && g.GW == 4) return launch_traj_t<2, true, 4, 1>(g, K, jobs, n_jobs, n_cta, sh, st);
-        if (fast && g.GW == 1) return launch_traj_t<2, true, 1, 1>(g, K, jobs, n_jobs, n_cta, sh, st);
-        return fast ? launch_traj_t<2, true, 0, 0>(g, K, jobs, n_jobs, n_cta, sh, st)
-                    : launch_traj_t<2, false, 0, 0>(g, K, jobs, n_jobs, n_cta, sh, st);
+        if (fast && g.GW == 4)
+            return launch_traj_t<2, true, 4, 1>(g, K, jobs, n_jobs, n_cta, sh, st, gS);
+        if (fast && g.GW == 1)
+            return launch_traj_t<2, true, 1, 1>(g, K, jobs, n_jobs, n_cta, sh, st, gS);
+        return fast ? launch_traj_t<2, true, 0, 0>(g, K, jobs, n_jobs, n_cta, sh, st, gS)
+                    : launch_traj_t<2, false, 0, 0>(g, K, jobs, n_jobs, n_cta, sh, st, gS);
     }
     if (fast && g.GW == 1 && g.Ly == 16)
-        return launch_traj_t<3, true, 1, 16>(g, K, jobs, n_jobs, n_cta, sh, st);
-    return fast ? launch_traj_t<3, true, 0, 0>(g, K, jobs, n_jobs, n_cta, sh, st)
-                : launch_traj_t<3, false, 0, 0>(g, K, jobs, n_jobs, n_cta, sh, st);
+        return launch_traj_t<3, true, 1, 16>(g, K, jobs, n_jobs, n_cta, sh, st, gS);
+    return fast ? launch_traj_t<3, true, 0, 0>(g, K, jobs, n_jobs, n_cta, sh, st, gS)
+                : launch_traj_t<3, false, 0, 0>(g, K, jobs, n_jobs, n_cta, sh, st, gS);
 }
 
 cudaError_t launch_estimator(const long long* w_int, int n, double scale, int direction,

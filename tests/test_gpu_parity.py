@@ -205,7 +205,8 @@ def test_argument_errors(ctx):
              ((2, 8, 8, -0.1, 1, 5, 1, 4, 0), jz.ISING_ERR_ARG),
              ((2, 8, 8, 0.4, 1, 0, 1, 4, 0), jz.ISING_ERR_ARG),
              ((2, 8, 8, 0.4, 1, 5, 1, 0, 0), jz.ISING_ERR_ARG),
-             ((3, 64, 64, 0.2, 1, 5, 1, 4, 0), jz.ISING_ERR_UNSUPPORTED)]
+             # a 3D time slice of L_y ceil(L/16) = 1024 words exceeds 512 threads
+             ((3, 128, 4, 0.2, 1, 5, 1, 4, 0), jz.ISING_ERR_UNSUPPORTED)]
     for args, code in cases:
         with pytest.raises(jz.IsingError) as e:
             jz.jarzynski_run(ctx, *args, w)
@@ -275,3 +276,16 @@ def test_full_config3_sampled(ctx):
     res = _run_workload(ctx, w)
     _check_properties(w, res)
     _check_sampled(w, res, [(0, 0), (7, 4095)])
+
+
+@pytest.mark.parametrize("job", [
+    wl.Job(2, 64, 4096, BC2, 5, 2, 1, 6, seed=21, n_therm=3),           # 262 KB per lattice
+    wl.Job(3, 12, 1280, BC3, 4, 2, 1, 4, seed=22, n_therm=2, direction=-1),
+], ids=["2d_L64_T4096", "3d_L12_T1280"])
+def test_lattice_beyond_shared_memory_runs_from_hbm(ctx, job):
+    """Replica lattices too large for one CTA's shared memory keep their spins
+    in an HBM slice per CTA; the bits stay those of the oracle."""
+    Wg, Sg = gpu_run(ctx, job)
+    Wo, So = oracle_run(job)
+    np.testing.assert_array_equal(Wg, Wo)
+    np.testing.assert_array_equal(Sg, So)
