@@ -80,9 +80,10 @@ typedef struct ising_ctx ising_ctx;
  *              1  Swendsen-Wang clusters: a link of coupling K between equal
  *                 spins becomes a bond with probability 1 - e^{-2K} and every
  *                 cluster of bonded sites flips with probability 1/2.  One CTA
- *                 per trajectory; needs about 4.5 V (2D) or 4.6 V (3D) bytes
- *                 of shared memory for the V = 2 L_t L^(d-1) sites (at most
- *                 227 KiB, V up to about 50,000), else ISING_ERR_UNSUPPORTED.
+ *                 per trajectory; its state takes about 4.5 V (2D) or 4.6 V
+ *                 (3D) bytes for the V = n L_t L^(d-1) sites, in shared memory
+ *                 up to 227 KiB (V up to about 50,000), beyond that in an HBM
+ *                 slice per CTA.
  *                 Served by jarzynski_run_ex, jarzynski_run_batch and the
  *                 server (jz_submit); the other entry points return
  *                 ISING_ERR_UNSUPPORTED for it.

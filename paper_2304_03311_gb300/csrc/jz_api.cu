@@ -215,7 +215,8 @@ bool sw_fits(const jz::Geom& g)
 // col = GW * L_y words per time slice, each thread owns one word column of
 // every TS-th slice.  col <= 32: warp teams of col * TS threads, TS =
 // min(32 / col, L_t), as many per CTA as fit (default CTA 128 threads).
-// Wider slices: the CTA is one team of col * TS threads, TS <= L_t (default
+// Wider slices, and narrow ones whose lattice leaves room for fewer than four
+// warp teams: the CTA is one team of col * TS threads, TS <= L_t (default
 // about 256 threads, at most 512).  Teams per CTA stay <= 64 and within the
 // per-CTA shared memory.
 jz::LaunchShape shape_for(const jz::Geom& g, int cta_threads)
@@ -223,7 +224,12 @@ jz::LaunchShape shape_for(const jz::Geom& g, int cta_threads)
     jz::LaunchShape s{};
     const int col = g.GW * g.Ly;
     const size_t lat = jz::traj_smem_bytes(g);
-    if (col <= 32) {
+    // narrow slices whose lattices are so large that fewer than four warp
+    // teams fit a CTA's shared memory (or none: lattices in HBM) run as one
+    // CTA team instead, so the SM still has several warps per lattice
+    const size_t fit = jz::kMaxSmemPerCta / lat;
+    const bool big = col <= 32 && 32 % col == 0 && fit < 4 && g.Lt * col > 32;
+    if (col <= 32 && !big) {
         int ts = 32 / col;
         if (ts > g.Lt) ts = g.Lt;
         s.team_threads = col * ts;
@@ -294,9 +300,9 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
     const jz_params& p0 = jobs[idx[0]];
     const jz::Geom g = make_geom(p0.d, p0.L, p0.L_t, nrep_of(p0));
     const bool sw = p0.update == 1;   // Swendsen-Wang: one trajectory per CTA
-    if (sw ? !sw_fits(g) : !threads_fit(g)) return ISING_ERR_UNSUPPORTED;
-    // Metropolis lattices beyond shared memory run from HBM, one slice per CTA
-    const bool in_hbm = !sw && !shape_fits(g);
+    if (!sw && !threads_fit(g)) return ISING_ERR_UNSUPPORTED;
+    // lattices beyond shared memory run from HBM, one slice per CTA
+    const bool in_hbm = sw ? !sw_fits(g) : !shape_fits(g);
     jz::LaunchShape sh = ctx_shape(ctx, p0.d, g);
     if (sw) sh.teams = 1;
     const int n_jobs = (int)idx.size();
@@ -362,8 +368,13 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
         return rc;
     const jz::PhiloxKeys K = key_schedule(p0.seed);
     if (sw) {
+        uint32_t* gS = nullptr;
+        if (in_hbm) {
+            if ((rc = ensure(ctx, ctx->lattice, (size_t)n_cta * jz::sw_smem_bytes(g)))) return rc;
+            gS = (uint32_t*)ctx->lattice.ptr;
+        }
         if ((rc = cuda_err(jz::launch_sw(p0.d, g, K, (const jz::JobDesc*)ctx->jobs.ptr, n_jobs,
-                                         n_cta, st))))
+                                         n_cta, st, gS))))
             return rc;
     } else {
         uint32_t* gS = nullptr;

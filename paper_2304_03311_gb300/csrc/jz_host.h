@@ -23,8 +23,10 @@ cudaError_t launch_traj(int D, const Geom& g, const PhiloxKeys& K, const JobDesc
 cudaError_t launch_estimator(const long long* w_int, int n, double scale, int direction,
                              int n_blocks, double* out, cudaStream_t st);
 size_t sw_smem_bytes(const Geom& g);
+// gS: nullptr to keep each trajectory's state in shared memory, else an HBM
+// buffer of n_cta * sw_smem_bytes(g) bytes, one slice per CTA.
 cudaError_t launch_sw(int D, const Geom& g, const PhiloxKeys& K, const JobDesc* jobs,
-                      int n_jobs, long long n_cta, cudaStream_t st);
+                      int n_jobs, long long n_cta, cudaStream_t st, uint32_t* gS = nullptr);
 double run_probe(int kind, int device);
 cudaError_t plain_trajectory(int D, const Geom& g, const PhiloxKeys& K, int l, int dir,
                              int n_step, int n_sweep, int n_therm, uint32_t traj,

@@ -164,9 +164,13 @@ __device__ __forceinline__ void merge(int* lab, int a, int b)
 
 template <int D>
 __global__ void __launch_bounds__(sw_threads(D))
-sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, int n_jobs)
+sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, int n_jobs,
+          uint32_t* __restrict__ gS, size_t g_words)
 {
-    extern __shared__ uint32_t smem[];
+    // the trajectory's state: shared memory, or this CTA's slice of an HBM
+    // buffer when it does not fit (gS != nullptr)
+    extern __shared__ uint32_t smem_shared[];
+    uint32_t* smem = gS ? gS + (size_t)blockIdx.x * g_words : smem_shared;
     int* lab = (int*)smem;
     uint32_t* sp = smem + g.V;
     uint32_t* bx = sp + g.VW;       // +x bonds leaving a warp chunk or its row
@@ -408,8 +412,9 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
             const int i = base + lane;
             int f = 0;
             if (i < g.V) {
+                // fb was written by atomics: read it past L1 when it lives in HBM
                 const int root = lab[i];
-                f = (int)((fb[root >> 5] >> (root & 31)) & 1);
+                f = (int)((((volatile uint32_t*)fb)[root >> 5] >> (root & 31)) & 1);
             }
             const uint32_t m = __ballot_sync(0xFFFFFFFFu, f);
             if (lane == 0) sp[base >> 5] ^= m;
@@ -457,15 +462,17 @@ size_t sw_smem_bytes(const Geom& geo)
 }
 
 cudaError_t launch_sw(int D, const Geom& geo, const PhiloxKeys& K, const JobDesc* jobs,
-                      int n_jobs, long long n_cta, cudaStream_t st)
+                      int n_jobs, long long n_cta, cudaStream_t st, uint32_t* gS)
 {
     const SwGeom g = make_swgeom(D, geo);
-    const size_t smem = sw_smem_bytes(geo);
+    const size_t bytes = sw_smem_bytes(geo);
+    const size_t smem = gS ? 0 : bytes;
     auto kern = D == 3 ? sw_kernel<3> : sw_kernel<2>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)n_cta, sw_threads(D), smem, st>>>(g, K, jobs, n_jobs);
+    kern<<<(unsigned)n_cta, sw_threads(D), smem, st>>>(g, K, jobs, n_jobs, gS,
+                                                       bytes / sizeof(uint32_t));
     return cudaGetLastError();
 }
 

@@ -289,3 +289,20 @@ def test_lattice_beyond_shared_memory_runs_from_hbm(ctx, job):
     Wo, So = oracle_run(job)
     np.testing.assert_array_equal(Wg, Wo)
     np.testing.assert_array_equal(Sg, So)
+
+
+def test_large_narrow_lattice_runs_as_cta_team(ctx):
+    """The paper's 2D lattice L = 128, L_t = 8L: 131 KB per trajectory leaves
+    room for one warp team per CTA, so it runs as one CTA team; every CTA
+    size gives the oracle's bits."""
+    job = wl.Job(2, 128, 1024, BC2, 40, 2, 1, 3, seed=23, n_therm=2)
+    Wo, So = oracle_run(job)
+    c = jz.ising_replica_init(0, 0, None)
+    try:
+        for t in (0, 64, 256, 512):
+            jz.ising_set_threads(c, 2, 128, 1024, t)
+            Wg, Sg = gpu_run(c, job)
+            np.testing.assert_array_equal(Wg, Wo)
+            np.testing.assert_array_equal(Sg, So)
+    finally:
+        jz.ising_replica_free(c)

@@ -166,14 +166,27 @@ def test_other_entry_points_refuse_the_cluster_update(ctx, entry):
     assert e.value.code == jz.ISING_ERR_UNSUPPORTED
 
 
+@pytest.mark.parametrize("job", [
+    wl.Job(2, 64, 512, BC2, 20, 2, 1, 4, seed=31, n_therm=2),            # V = 65536
+    wl.Job(3, 32, 32, BC3, 9, 2, 1, 3, seed=32, n_therm=1, direction=-1),  # V = 65536
+], ids=["2d_L64_T512", "3d_L32_T32"])
+def test_state_beyond_shared_memory_runs_from_hbm(ctx, job):
+    """Trajectories whose labels and bits exceed shared memory run from an
+    HBM slice per CTA, with the bits of the oracle."""
+    Wg, Sg = gpu_run(ctx, job)
+    Wo, So = oracle_run(job)
+    np.testing.assert_array_equal(Wg, Wo)
+    np.testing.assert_array_equal(Sg, So)
+
+
 def test_bad_update_and_oversized_lattice_are_rejected(ctx):
     w = torch.empty(4, dtype=torch.int64, device="cuda")
     p = jz.make_params(2, 8, 8, BC2, 1, 2, 1, 4, 0, n_therm=1, update=2)
     with pytest.raises(jz.IsingError) as e:
         jz.jarzynski_run_ex(ctx, p, w)
     assert e.value.code == jz.ISING_ERR_ARG
-    # 3D L = 32, L_t = 32: V = 65536 sites need 264 KiB of shared memory
+    # beyond shared memory the persistent plan refuses it
     p = jz.make_params(3, 32, 32, BC3, 1, 2, 1, 4, 0, n_therm=1, update=SW)
     with pytest.raises(jz.IsingError) as e:
-        jz.jarzynski_run_ex(ctx, p, w)
+        jz.jz_plan_create(ctx, [p], [w])
     assert e.value.code == jz.ISING_ERR_UNSUPPORTED
