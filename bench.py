@@ -252,15 +252,18 @@ def cpu_oracle_rate(w, seconds: float):
     return updates / dt, len(jobs) * n_per_job / dt, threads, sample
 
 
-def traffic_from_profile(src_hash: str):
-    path = os.path.join(ROOT, "profiles", "traj_kernel_traffic.json")
+def traffic_from_profile(src_hash: str, workload: str):
+    """DRAM bytes (read + write) of one launch of this workload's dominant
+    kernel, from the ncu capture recorded in profiles/dram_traffic.json; None
+    when there is none or the kernel sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         rec = json.load(open(path))
     except (OSError, ValueError):
         return None
     if rec.get("source_sha256") != src_hash:
         return None
-    return rec.get("dram_bytes_per_launch")
+    return (rec.get("launches", {}).get(workload) or {}).get("dram_bytes_per_launch")
 
 
 def kernel_source_hash():
@@ -456,7 +459,7 @@ def run_ours(args):
              "persistent_kernel" if plan is not None else f"traj_kernel<{d},...>")
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved,
                 "peak": peak, "unit": "Tintop/s", "frac": achieved / peak,
-                "traffic": None if sw else traffic_from_profile(src_hash),
+                "traffic": traffic_from_profile(src_hash, w.name),
                 "ops_per_update": n_alg, "kernel_ms": kernel_ms,
                 "peak_basis": "152 SMs x 128 int lanes/clk x 2070 MHz (derived)"}
 

@@ -172,6 +172,22 @@ int jarzynski_run(ising_ctx* ctx, int d, int L, int L_t, double beta, int l,
 int jarzynski_run_ex(ising_ctx* ctx, const jz_params* p, int64_t* work_int_out,
                      int8_t* spins_out);
 
+/* Checkpoint / resume: runs only protocol steps k_begin .. k_end-1 of the
+ * transformation p (0 <= k_begin < k_end <= n_step).  spins_io (device memory,
+ * n_traj * n * L_t * L_y * L int8, order as jarzynski_run_ex's spins_out) and
+ * work_io (device memory, n_traj int64) carry the state between segments: for
+ * k_begin = 0 the trajectories start from the hot start and n_therm sweeps and
+ * their inputs are ignored; for k_begin > 0 they hold the configuration after
+ * step k_begin-1 and W_int of steps 0 .. k_begin-1.  On return (after
+ * ising_sync) spins_io holds the configuration after step k_end-1 and work_io
+ * W_int of steps 0 .. k_end-1.  The random counter is a function of the
+ * global sweep index, so any split of [0, n_step) into segments gives the bits
+ * of one jarzynski_run_ex call; the paper has no such facility.  Errors: as
+ * jarzynski_run_ex, and ISING_ERR_ARG for an empty or out-of-range step range
+ * or host buffers. */
+int jarzynski_run_segment(ising_ctx* ctx, const jz_params* p, int k_begin, int k_end,
+                          int64_t* work_io, int8_t* spins_io);
+
 /* Runs n_jobs transformations in one device launch per lattice shape (jobs of
  * equal (d, L, L_t) share a launch; the c-function scan of section 3 is one
  * call with one job per l).  work_outs[j] is job j's caller-owned output of

@@ -92,6 +92,8 @@ def load():
                                          ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_int, ctypes.c_uint64, vp]),
         "jarzynski_run_ex": (ctypes.c_int, [vp, P(JzParams), vp, vp]),
+        "jarzynski_run_segment": (ctypes.c_int, [vp, P(JzParams), ctypes.c_int, ctypes.c_int,
+                                                 vp, vp]),
         "jarzynski_run_batch": (ctypes.c_int, [vp, P(JzParams), ctypes.c_int, P(vp)]),
         "jarzynski_run_plain": (ctypes.c_int, [vp, P(JzParams), vp, vp]),
         "jarzynski_run_noalloc": (ctypes.c_int, [P(JzParams), vp, vp]),
@@ -197,6 +199,13 @@ def make_params(d, L, L_t, beta, l, n_step, n_sweep, n_traj, seed=0, *, n_therm=
 def jarzynski_run_ex(ctx, params: JzParams, work_int_out, spins_out=None):
     _check(load().jarzynski_run_ex(ctx, ctypes.byref(params), _ptr(work_int_out),
                                    _ptr(spins_out)), "jarzynski_run_ex")
+
+
+def jarzynski_run_segment(ctx, params: JzParams, k_begin: int, k_end: int, work_io, spins_io):
+    """Protocol steps k_begin..k_end-1 resumed from device buffers work_io and
+    spins_io (see include/isingjz.h); both are updated in place."""
+    _check(load().jarzynski_run_segment(ctx, ctypes.byref(params), int(k_begin), int(k_end),
+                                        _ptr(work_io), _ptr(spins_io)), "jarzynski_run_segment")
 
 
 def jarzynski_run_plain(ctx, params: JzParams, work_int_out, spins_out=None):

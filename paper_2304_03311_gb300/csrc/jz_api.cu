@@ -295,7 +295,7 @@ int cuda_err(cudaError_t e)
 // Runs jobs[idx[0..]] (equal d, L, L_t, seed) in one launch.
 int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx,
               int64_t* const* outs, int8_t* const* spins, bool outs_on_device,
-              bool spins_on_device)
+              bool spins_on_device, const Segment* seg)
 {
     const jz_params& p0 = jobs[idx[0]];
     const jz::Geom g = make_geom(p0.d, p0.L, p0.L_t, nrep_of(p0));
@@ -342,6 +342,10 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
         J.dir = p.direction;
         J.prot = p.protocol == 2 ? 2 : 1;
         cut_range(p, &J.g0, &J.g1);
+        J.k_begin = seg ? seg->k_begin : 0;
+        J.k_end = seg ? seg->k_end : p.n_step;
+        J.spins_in = seg ? seg->spins_in : nullptr;
+        J.w_in = seg ? seg->w_in : nullptr;
         J.n_traj = p.n_traj;
         J.traj0 = p.traj0;
         J.cta0 = cta;
@@ -453,7 +457,7 @@ int run_jobs(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const* 
         for (size_t s = 0; s < idx.size(); s += jz::kMaxJobsPerLaunch) {
             std::vector<int> part(idx.begin() + s,
                                   idx.begin() + std::min(idx.size(), s + jz::kMaxJobsPerLaunch));
-            int rc = run_group(ctx, jobs, part, outs, spins, outs_dev, spins_dev);
+            int rc = run_group(ctx, jobs, part, outs, spins, outs_dev, spins_dev, nullptr);
             if (rc) return rc;
         }
     }
@@ -627,6 +631,21 @@ int jarzynski_run_batch(ising_ctx* ctx, const jz_params* jobs, int n_jobs,
                         int64_t* const* work_outs)
 {
     return run_jobs(ctx, jobs, n_jobs, work_outs, nullptr);
+}
+
+int jarzynski_run_segment(ising_ctx* ctx, const jz_params* p, int k_begin, int k_end,
+                          int64_t* work_io, int8_t* spins_io)
+{
+    if (!ctx || !p || !work_io || !spins_io) return ISING_ERR_ARG;
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (k_begin < 0 || k_end <= k_begin || k_end > p->n_step) return ISING_ERR_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
+    if (!is_device_ptr(work_io) || !is_device_ptr(spins_io)) return ISING_ERR_ARG;
+    const Segment seg{k_begin, k_end, spins_io, (const long long*)work_io};
+    int64_t* outs[1] = {work_io};
+    int8_t* sp[1] = {spins_io};
+    return run_group(ctx, p, std::vector<int>{0}, outs, sp, true, true, &seg);
 }
 
 int jarzynski_run_plain(ising_ctx* ctx, const jz_params* p, int64_t* work_int_out,
@@ -827,6 +846,8 @@ extern "C" int jarzynski_run_noalloc(const jz_params* p, int64_t* work_int_out, 
     J.dir = p->direction;
     J.prot = p->protocol == 2 ? 2 : 1;
     cut_range(*p, &J.g0, &J.g1);
+    J.k_begin = 0;
+    J.k_end = p->n_step;
     J.n_traj = p->n_traj;
     J.traj0 = p->traj0;
     J.cta0 = 0;
@@ -928,6 +949,8 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
         J.dir = p.direction;
         J.prot = p.protocol == 2 ? 2 : 1;
         cut_range(p, &J.g0, &J.g1);
+        J.k_begin = 0;
+        J.k_end = p.n_step;
         J.n_traj = p.n_traj;
         J.traj0 = p.traj0;
         J.cta0 = 0;

@@ -60,6 +60,9 @@ struct JobDesc {
     int n_traj;
     int prot;           // 1: every switched column together; 2: one column y at a time
     int g0, g1;         // columns x < g0 glued, g0 <= x < g1 switching, x >= g1 self
+    int k_begin, k_end; // protocol steps run: [k_begin, k_end); 0 starts from the hot start
+    const int8_t* spins_in;     // k_begin > 0: [n_traj][V] state after step k_begin - 1
+    const long long* w_in;      // k_begin > 0: [n_traj] W_int of steps 0 .. k_begin - 1
     long long traj0;    // global index of the job's first trajectory
     long long cta0;     // first CTA of the job in the launch grid
     uint32_t tb[4];     // bulk thresholds by anti-aligned neighbour count a:

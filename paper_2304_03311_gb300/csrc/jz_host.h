@@ -80,4 +80,10 @@ jz::LaunchShape ctx_shape(const ising_ctx* ctx, int d, const jz::Geom& g);
 int cuda_err(cudaError_t e);
 int run_jobs(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const* outs,
              int8_t* const* spins);
+// Protocol steps [k_begin, k_end) resumed from stored spins and W_int (k_begin > 0).
+struct Segment {
+    int k_begin, k_end;
+    const int8_t* spins_in;
+    const long long* w_in;
+};
 }  // namespace jzh

@@ -49,22 +49,23 @@ traj_kernel(const Geom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
     if (threadIdx.x < kMaxTeams) s_work[threadIdx.x] = 0;
     __syncthreads();
     const long long traj = __ldg(&J.traj0) + local;
+    const long long V = (long long)g.nrep * g.Lt * g.Ly * g.L;
+    const int8_t* sin = (has && tj.k_begin > 0) ? J.spins_in + local * V : nullptr;
     int dE;
     if (WARP)
         dE = run_trajectory<D, FAST, CW, CLY>(g, K, tj, traj, St, s_tab, tid, sh.team_threads,
-                                              WarpBarrier{});
+                                              WarpBarrier{}, sin);
     else
         dE = run_trajectory<D, FAST, CW, CLY>(g, K, tj, traj, St, s_tab, tid, sh.team_threads,
-                                              CtaBarrier{});
+                                              CtaBarrier{}, sin);
     if (has && dE != 0) atomicAdd(&s_work[tm], dE);
     __syncthreads();
     if (has && tid == 0)
-        J.w_out[local] = (long long)(tj.dir > 0 ? s_work[tm] : -s_work[tm]) *
-                         (tj.prot == 2 ? g.Ly : 1);
+        J.w_out[local] = (tj.k_begin > 0 ? J.w_in[local] : 0) +
+                         (long long)(tj.dir > 0 ? s_work[tm] : -s_work[tm]) *
+                             (tj.prot == 2 ? g.Ly : 1);
     int8_t* sp = J.spins_out;
-    if (has && sp != nullptr)
-        export_spins<D>(g, St, sp + local * (long long)(g.nrep * g.Lt * g.Ly * g.L), tid,
-                        sh.team_threads);
+    if (has && sp != nullptr) export_spins<D>(g, St, sp + local * V, tid, sh.team_threads);
 }
 
 // ---------------------------------------------------------------- estimator --

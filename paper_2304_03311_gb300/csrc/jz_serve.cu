@@ -130,6 +130,8 @@ int jz_server::launch(Slot& s, Job& j)
     J.dir = p.direction;
     J.prot = p.protocol == 2 ? 2 : 1;
     cut_range(p, &J.g0, &J.g1);
+    J.k_begin = 0;
+    J.k_end = p.n_step;
     J.n_traj = p.n_traj;
     J.traj0 = p.traj0;
     J.cta0 = 0;

@@ -207,11 +207,16 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
     const int chunk = n_warps * 32;
 
     // hot start: spin -1 iff the top bit of the site's word of the colour-row
-    // Philox block (row G + h/4, 0, traj, colour | dir<<1 | l<<2 | 1<<30), h = x/2
+    // Philox block (row G + h/4, 0, traj, colour | dir<<1 | l<<2 | 1<<30), h = x/2;
+    // a resumed segment (k_begin > 0) loads the stored configuration instead
+    const int k_begin = __ldg(&J.k_begin), k_end = __ldg(&J.k_end);
+    const int8_t* sin = k_begin > 0 ? J.spins_in + local * (long long)g.V : nullptr;
     for (int base = warp * 32; base < g.V; base += chunk) {
         const int i = base + lane;
         int bit = 0;
-        if (i < g.V) {
+        if (i < g.V && sin) {
+            bit = sin[i] < 0;
+        } else if (i < g.V) {
             const Site s = decode<D>(i, g);
             const int h = s.x >> 1;
             const uint32_t colour = (uint32_t)((s.x + s.y + s.t) & 1);
@@ -225,8 +230,8 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
     __syncthreads();
 
     long long w = 0;
-    const int n_total = n_therm + n_step * n_sweep;
-    for (int sw = 0; sw < n_total; ++sw) {
+    const int sw_end = n_therm + k_end * n_sweep;
+    for (int sw = k_begin > 0 ? n_therm + k_begin * n_sweep : 0; sw < sw_end; ++sw) {
         const int k = sw < n_therm ? -1 : (sw - n_therm) / n_sweep;
         const bool step_start = k >= 0 && (sw - n_therm) % n_sweep == 0;
         // protocol 2: only column y = ya moves at step k; columns before it sit
@@ -421,7 +426,9 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) J.w_out[local] = (dir > 0 ? w : -w) * (prot == 2 ? g.Ly : 1);
+    if (threadIdx.x == 0)
+        J.w_out[local] = (k_begin > 0 ? J.w_in[local] : 0) +
+                         (dir > 0 ? w : -w) * (prot == 2 ? g.Ly : 1);
     int8_t* so = J.spins_out;
     if (so != nullptr) {
         so += local * (long long)g.V;

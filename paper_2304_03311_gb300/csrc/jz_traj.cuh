@@ -67,6 +67,7 @@ __device__ __forceinline__ uint32_t word8(const uint4& ua, const uint4& ub, int 
 // Per-job values a team needs (read from the job descriptor once).
 struct TeamJob {
     int l, n_step, n_sweep, n_therm, dir;
+    int k_begin, k_end;   // protocol steps run; k_begin > 0 resumes from stored spins
     int g0, g1;   // columns x < g0 glued, g0 <= x < g1 switching, x >= g1 self
     int prot;     // 1: every switched column together; 2: one column y at a time
     int den;      // steps of one column's run: N (protocol 1), N / L_y (protocol 2)
@@ -252,6 +253,30 @@ struct Traj {
         }
     }
 
+    // Loads a stored configuration (int8 +-1, natural order [r][t][y][x]) into
+    // this thread's words: site j of word (c, R, q) has x = 2 (8q + j) + p.
+    __device__ __forceinline__ void import_spins(const int8_t* src) const
+    {
+        const int rw = rowW();
+        const int cw = g.nrep * g.Lt * rw;
+        for (int c = 0; c < 2; ++c) {
+            uint32_t* base = S + c * cw;
+            for (int r = 0; r < g.nrep; ++r) {
+                int w = (r * g.Lt + t0) * rw + y * W() + q;
+                for (int t = t0; t < g.Lt; t += TS, w += TS * rw) {
+                    const int p = (c + t + y) & 1;
+                    const long long row0 = ((long long)(r * g.Lt + t) * Ly() + y) * g.L;
+                    uint32_t v = 0;
+                    for (int j = 0; j < 8; ++j) {
+                        const int x = 2 * (8 * q + j) + p;
+                        if (x < g.L && src[row0 + x] < 0) v |= 1u << (4 * j);
+                    }
+                    base[w] = v;
+                }
+            }
+        }
+    }
+
     __device__ __forceinline__ void hot_start() const
     {
         const int rw = rowW();
@@ -289,27 +314,35 @@ struct WarpBarrier {
 // marks a thread without sites.  Returns this thread's share of sum_k dE_k
 // (the caller applies the direction's sign and, in protocol 2, the factor L_y
 // that makes W = (beta/N) W_int).
+// sin: the stored state to resume from when J.k_begin > 0 (else unused).
 template <int D, bool FAST, int CW, int CLY, class Bar>
 __device__ __forceinline__ int run_trajectory(const Geom& g, const PhiloxKeys& K, const TeamJob& J,
                                               long long traj, uint32_t* S_team,
-                                              const uint32_t* tab, int tid, int nthr, Bar bar)
+                                              const uint32_t* tab, int tid, int nthr, Bar bar,
+                                              const int8_t* sin = nullptr)
 {
     const Traj<D, FAST, CW, CLY> tr(g, S_team, tab, K, (uint32_t)traj,
                                     ((uint32_t)(J.dir < 0) << 1) | ((uint32_t)J.l << 2), tid, nthr);
-    tr.hot_start();
-    bar();
     int dE = 0;
-    // thermalisation at the start geometry: forward lambda = 0 (x < g0 glued),
-    // reverse lambda = 1 (x < g1 glued)
-    const int lg_therm = J.dir > 0 ? J.g0 : J.g1;
-    for (int s = 0; s < J.n_therm; ++s) {
-        tr.half_sweep(0, (uint32_t)s, -1, lg_therm, J, 0, 0, false, dE);
+    if (J.k_begin > 0) {
+        if (tid >= 0) tr.import_spins(sin);
         bar();
-        tr.half_sweep(1, (uint32_t)s, -1, lg_therm, J, 0, 0, false, dE);
+    } else {
+        tr.hot_start();
         bar();
+        // thermalisation at the start geometry: forward lambda = 0 (x < g0
+        // glued), reverse lambda = 1 (x < g1 glued)
+        const int lg_therm = J.dir > 0 ? J.g0 : J.g1;
+        for (int s = 0; s < J.n_therm; ++s) {
+            tr.half_sweep(0, (uint32_t)s, -1, lg_therm, J, 0, 0, false, dE);
+            bar();
+            tr.half_sweep(1, (uint32_t)s, -1, lg_therm, J, 0, 0, false, dE);
+            bar();
+        }
     }
-    uint32_t s = (uint32_t)J.n_therm;
-    for (int k = 0; k < J.n_step; ++k) {
+    // the global sweep index: protocol sweep i of step k is n_therm + k n_sweep + i
+    uint32_t s = (uint32_t)J.n_therm + (uint32_t)J.k_begin * (uint32_t)J.n_sweep;
+    for (int k = J.k_begin; k < J.k_end; ++k) {
         // protocol 2: only column y = k / den moves; the columns before it sit
         // at the end geometry, the ones after it at the start geometry
         const int ya = k / J.den;
@@ -360,6 +393,8 @@ __device__ __forceinline__ TeamJob team_job(const JobDesc& J, int ly)
     t.n_therm = __ldg(&J.n_therm);
     t.dir = __ldg(&J.dir);
     t.prot = __ldg(&J.prot);
+    t.k_begin = __ldg(&J.k_begin);
+    t.k_end = __ldg(&J.k_end);
     t.g0 = __ldg(&J.g0);
     t.g1 = __ldg(&J.g1);
     t.den = t.prot == 2 ? t.n_step / ly : t.n_step;

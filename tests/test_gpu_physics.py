@@ -6,6 +6,7 @@
   jackknife error, and its c-function follows the transfer matrix's.
 * Direct (l+1 -> l) and reverse (l -> l+1) protocols agree (Appendix A, eq.
   equality_of_direct_reverse_protocols).
+* The same scan with Swendsen-Wang clusters matches the transfer matrix too.
 """
 import math
 
@@ -32,12 +33,14 @@ def ctx():
     jz.ising_replica_free(c)
 
 
-def _scan(ctx, L, L_t, n_step, n_traj, direction=1, seed=1):
-    jobs = [wl.Job(2, L, L_t, wl.BETA_C_2D, l, n_step, 1, n_traj, seed=seed, direction=direction)
+def _scan(ctx, L, L_t, n_step, n_traj, direction=1, seed=1, update=0, n_therm=1000):
+    jobs = [wl.Job(2, L, L_t, wl.BETA_C_2D, l, n_step, 1, n_traj, seed=seed, direction=direction,
+                   n_therm=n_therm)
             for l in range(L)]
     outs = [torch.empty(j.n_traj, dtype=torch.int64, device="cuda") for j in jobs]
     params = [jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj, j.seed,
-                             n_therm=j.n_therm, direction=j.direction) for j in jobs]
+                             n_therm=j.n_therm, direction=j.direction, update=update)
+              for j in jobs]
     jz.jarzynski_run_batch(ctx, params, outs)
     jz.ising_sync(ctx)
     res = []
@@ -70,3 +73,14 @@ def test_direct_and_reverse_agree_on_gpu(ctx):
     pulls = [(a - b) / math.hypot(ea, eb) for (a, ea), (b, eb) in zip(fwd, rev)]
     assert max(abs(p) for p in pulls) < 4.5, pulls
     assert sum(p * p for p in pulls) < 45.0
+
+
+def test_swendsen_wang_scan_matches_exact_transfer_matrix(ctx):
+    """The paper's own update: a Swendsen-Wang c-function scan at L = 10,
+    L_t = 8L against the exact transfer matrix, every l within 4.5 sigma."""
+    L, L_t = 10, 80
+    exact = ex.delta_s2_transfer(2, L, L_t, wl.BETA_C_2D)
+    res = _scan(ctx, L, L_t, 200, 2048, update=1, n_therm=100, seed=4)
+    pulls = [(ds - e) / err for (ds, err), e in zip(res, exact)]
+    assert max(abs(p) for p in pulls) < 4.5, pulls
+    assert sum(p * p for p in pulls) < 30.0
