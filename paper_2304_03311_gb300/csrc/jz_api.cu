@@ -243,9 +243,12 @@ jz::LaunchShape shape_for(const jz::Geom& g, int cta_threads)
         s.teams = warps * per_warp;
         s.cta_threads = warps * 32;
     } else {
-        int ts = (cta_threads > 0 ? cta_threads : 256) / col;
+        // lattices in HBM wait on L2 and take the widest team by default
+        // (3D L = 48, L_t = 4L: 432 threads 9.3e11, 144 threads 6.7e11)
+        const bool in_hbm = lat > jz::kMaxSmemPerCta;
+        int ts = (cta_threads > 0 ? cta_threads : (in_hbm ? 512 : 256)) / col;
         if (ts < 1) ts = 1;
-        if (cta_threads == 0 && ts > 1 && (ts & 1)) ts -= 1;
+        if (cta_threads == 0 && !in_hbm && ts > 1 && (ts & 1)) ts -= 1;
         if (ts > g.Lt) ts = g.Lt;
         while (ts > 1 && col * ts > 512) --ts;
         s.team_threads = col * ts;

@@ -84,3 +84,22 @@ def test_swendsen_wang_scan_matches_exact_transfer_matrix(ctx):
     pulls = [(ds - e) / err for (ds, err), e in zip(res, exact)]
     assert max(abs(p) for p in pulls) < 4.5, pulls
     assert sum(p * p for p in pulls) < 30.0
+
+
+def test_2d_c_function_fit_at_zero_temperature(ctx):
+    """Section 4's fit on a GPU scan of the 2D critical model at L = 32,
+    L_t = 8L: the c-function follows cos(pi x)/16 + k cot(pi x)/(2L) with k
+    near the paper's 0.162(10) at this size, and a good chi^2 once the two
+    points at each end are dropped (as in the paper's table)."""
+    from paper_2304_03311_gb300 import analysis as an
+    L, L_t = 32, 256
+    # 1000 Metropolis sweeps do not thermalise the critical L = 32 lattice
+    # from a hot start (z ~ 2.17); 4000 do
+    res = _scan(ctx, L, L_t, 400, 2048, n_therm=4000, seed=11)
+    ds = np.array([r[0] for r in res])
+    err = np.array([r[1] for r in res])
+    l = np.arange(L)
+    c, ce = an.c_function(ds, 2, L, l, err=err)
+    fit = an.fit_2d(an.midpoint_x(l, L), c, ce, L, drop_ends=2)
+    assert 0.08 < fit.params[0] < 0.25, fit
+    assert fit.chi2_per_dof < 4.0, fit
