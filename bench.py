@@ -90,6 +90,9 @@ def parse_args():
                     help="run the scan with Metropolis (n_therm 1000, 4000, 16000) and "
                          "Swendsen-Wang (n_therm 100, 1000) and print the c-function pulls "
                          "against Swendsen-Wang at n_therm 1000 (thermalisation bias)")
+    ap.add_argument("--fit-2d", type=int, default=0, metavar="L",
+                    help="section 4's study: the 2D critical scan at this L with L_t = 8L, "
+                         "fitted with cos(pi x)/16 + k cot(pi x)/(2L); prints k and chi^2")
     ap.add_argument("--no-compare", action="store_true",
                     help="sw: skip the equal-error comparison with Metropolis")
     ap.add_argument("--plain", type=int, default=0,
@@ -420,7 +423,7 @@ def run_ours(args):
     # end to end through the C ABI with host buffers: work arrays copied back
     # each step, the estimator fed from host memory
     e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(1, args.steps // 2)
-    host_outs = [np.empty(j.n_traj, dtype=np.int64) for j in w.jobs]
+    host_outs = [torch.empty(j.n_traj, dtype=torch.int64, pin_memory=True) for j in w.jobs]
     stream.synchronize()
     if world > 1:
         dist.barrier()
@@ -431,8 +434,9 @@ def run_ours(args):
             if world > 1:
                 gathered = []
                 for h in host_outs:
-                    parts = [torch.empty(len(h), dtype=torch.int64) for _ in range(world)]
-                    dist.all_gather(parts, torch.from_numpy(h).to(dev))
+                    parts = [torch.empty(len(h), dtype=torch.int64, device=dev)
+                             for _ in range(world)]
+                    dist.all_gather(parts, h.to(dev))
                     gathered.append(torch.cat([p.cpu() for p in parts]).numpy())
             else:
                 gathered = host_outs
@@ -688,10 +692,60 @@ def run_therm_study(args):
                       "n_traj_per_l": n, "reference": "sw_therm1000"}), flush=True)
 
 
+def run_fit_2d(args):
+    """Section 4 on the GPU: every l -> l+1 of the critical 2D model at L,
+    L_t = 8L, the c-function from Delta S_2, and the paper's fit with and
+    without the two points at each end (its table of chi^2 and k)."""
+    import numpy as np
+    import torch
+    from paper_2304_03311_gb300 import build as jzbuild
+    from paper_2304_03311_gb300 import analysis as an
+    jzbuild.build()
+    import paper_2304_03311_gb300 as jz
+    L = args.fit_2d
+    L_t = 8 * L
+    n_traj = args.traj_per_l or 4096
+    N = args.n_step or 2000
+    upd = 1 if args.update == "sw" else 0
+    # Metropolis needs of order L^2.17 sweeps from a hot start at criticality
+    n_therm = args.n_therm or (100 if upd else int(4 * L ** 2.17) + 1000)
+    jobs = [wl.Job(2, L, L_t, wl.BETA_C_2D, l, N, 1, n_traj, seed=l, n_therm=n_therm, update=upd)
+            for l in range(L)]
+    ctx = jz.ising_replica_init(0, 0, None)
+    outs = [torch.empty(n_traj, dtype=torch.int64, device="cuda") for _ in jobs]
+    ps = [jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj, j.seed,
+                         n_therm=j.n_therm, update=upd) for j in jobs]
+    t0 = time.perf_counter()
+    jz.jarzynski_run_batch(ctx, ps, outs)
+    jz.ising_sync(ctx)
+    dt = time.perf_counter() - t0
+    ds, err = [], []
+    for j, o in zip(jobs, outs):
+        _, d, e = jz.estimator_reduce(ctx, o, n_traj, j.beta, N, 1, 32)
+        ds.append(d)
+        err.append(e)
+    jz.ising_replica_free(ctx)
+    l = np.arange(L)
+    x = an.midpoint_x(l, L)
+    c, ce = an.c_function(np.array(ds), 2, L, l, err=np.array(err))
+    out = {"fit_2d": {"L": L, "L_t": L_t, "n_step": N, "n_traj_per_l": n_traj,
+                      "n_therm": n_therm, "update": args.update, "seconds": dt}}
+    for drop in (0, 2):
+        f = an.fit_2d(x, c, ce, L, drop_ends=drop)
+        sf = an.chi2_scaling_function_2d(x, c, ce, drop_ends=drop)
+        out["fit_2d"][f"drop_{drop}"] = {"k": float(f.params[0]), "k_err": float(f.errors[0]),
+                                         "chi2_per_dof": f.chi2_per_dof,
+                                         "scaling_function_chi2_per_dof": sf.chi2_per_dof}
+    out["fit_2d"]["c_function"] = [[float(a), float(b), float(e)] for a, b, e in zip(x, c, ce)]
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     if args.probe:
         run_probe()
+    elif args.fit_2d:
+        run_fit_2d(args)
     elif args.therm_study:
         run_therm_study(args)
     elif args.impl == "reference":
