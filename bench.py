@@ -93,6 +93,9 @@ def parse_args():
     ap.add_argument("--fit-2d", type=int, default=0, metavar="L",
                     help="section 4's study: the 2D critical scan at this L with L_t = 8L, "
                          "fitted with cos(pi x)/16 + k cot(pi x)/(2L); prints k and chi^2")
+    ap.add_argument("--small-x-3d", type=int, default=0, metavar="L",
+                    help="section 5's study: 2 C_2 at small x of the 3D critical model at this "
+                         "L with L_t = 4L (l = 1..4 for L = 24, 2..5 for L = 48)")
     ap.add_argument("--no-compare", action="store_true",
                     help="sw: skip the equal-error comparison with Metropolis")
     ap.add_argument("--plain", type=int, default=0,
@@ -740,10 +743,48 @@ def run_fit_2d(args):
     print(json.dumps(out), flush=True)
 
 
+def run_small_x_3d(args):
+    """Section 5's table of 2 C_2 at small x (3D critical model, L_t = 4L),
+    with the paper's N for x near 0 by default."""
+    import torch
+    from paper_2304_03311_gb300 import build as jzbuild
+    from paper_2304_03311_gb300 import analysis as an
+    jzbuild.build()
+    import paper_2304_03311_gb300 as jz
+    L = args.small_x_3d
+    L_t = 4 * L
+    ls = [1, 2, 3, 4] if L <= 24 else [2, 3, 4, 5]
+    n_traj = args.traj_per_l or 256
+    N = args.n_step or (25000 if L <= 24 else 40000)
+    n_therm = args.n_therm or 8000
+    jobs = [wl.Job(3, L, L_t, wl.BETA_C_3D, l, N, 1, n_traj, seed=40 + l, n_therm=n_therm)
+            for l in ls]
+    ctx = jz.ising_replica_init(0, 0, None)
+    outs = [torch.empty(n_traj, dtype=torch.int64, device="cuda") for _ in jobs]
+    t0 = time.perf_counter()
+    jz.jarzynski_run_batch(ctx, [jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step,
+                                                j.n_sweep, j.n_traj, j.seed, n_therm=j.n_therm)
+                                 for j in jobs], outs)
+    jz.ising_sync(ctx)
+    dt = time.perf_counter() - t0
+    rows = []
+    for j, o in zip(jobs, outs):
+        _, ds, err = jz.estimator_reduce(ctx, o, n_traj, j.beta, N, 1, 32)
+        c, ce = an.c_function(ds, 3, L, j.l, err=err)
+        rows.append({"x": float(an.midpoint_x(j.l, L)), "two_C2": float(2 * c),
+                     "err": float(2 * ce)})
+    jz.ising_replica_free(ctx)
+    print(json.dumps({"small_x_3d": {"L": L, "L_t": L_t, "n_step": N, "n_traj_per_l": n_traj,
+                                     "n_therm": n_therm, "seconds": dt, "rows": rows}}),
+          flush=True)
+
+
 def main():
     args = parse_args()
     if args.probe:
         run_probe()
+    elif args.small_x_3d:
+        run_small_x_3d(args)
     elif args.fit_2d:
         run_fit_2d(args)
     elif args.therm_study:

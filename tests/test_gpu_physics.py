@@ -7,8 +7,12 @@
 * Direct (l+1 -> l) and reverse (l -> l+1) protocols agree (Appendix A, eq.
   equality_of_direct_reverse_protocols).
 * The same scan with Swendsen-Wang clusters matches the transfer matrix too.
+* Section 4's fit at L = 32, L_t = 8L gives the paper's k, and section 5's
+  small-x values of 2 C_2 at L = 24 and 48 are reproduced (fixtures in
+  tests/golden/, each citing its table).
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -103,3 +107,35 @@ def test_2d_c_function_fit_at_zero_temperature(ctx):
     fit = an.fit_2d(an.midpoint_x(l, L), c, ce, L, drop_ends=2)
     assert 0.08 < fit.params[0] < 0.25, fit
     assert fit.chi2_per_dof < 4.0, fit
+    # the paper's k at L = 32 (section 4 table, tests/golden/paper_2d_fit_table.txt)
+    rows = _golden("paper_2d_fit_table.txt")
+    k_paper, k_err = next((r[4], r[5]) for r in rows if int(r[0]) == L)
+    assert abs(fit.params[0] - k_paper) < 4 * math.hypot(fit.errors[0], k_err)
+
+
+def _golden(name):
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    return [[float(v) for v in line.split()] for line in open(path)
+            if line.strip() and not line.startswith("#")]
+
+
+@pytest.mark.parametrize("L,n_traj,n_step", [(24, 256, 25000), (48, 128, 40000)])
+def test_3d_small_x_c_function_matches_the_paper(ctx, L, n_traj, n_step):
+    """Section 5's table of 2 C_2 at small x for the 3D critical model at
+    L_t = 4L (the L = 48 lattice runs from HBM), reproduced within errors with
+    the paper's N for x near 0."""
+    L_t = 4 * L
+    rows = [r for r in _golden("paper_3d_2c2_small_x.txt") if int(r[0]) == L]
+    ls = [int(round(r[1] * L - 0.5)) for r in rows]
+    jobs = [wl.Job(3, L, L_t, wl.BETA_C_3D, l, n_step, 1, n_traj, seed=40 + l, n_therm=8000)
+            for l in ls]
+    outs = [torch.empty(j.n_traj, dtype=torch.int64, device="cuda") for j in jobs]
+    jz.jarzynski_run_batch(ctx, [jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step,
+                                                j.n_sweep, j.n_traj, j.seed, n_therm=j.n_therm)
+                                 for j in jobs], outs)
+    jz.ising_sync(ctx)
+    for j, o, r in zip(jobs, outs, rows):
+        _, ds, err = jz.estimator_reduce(ctx, o, j.n_traj, j.beta, j.n_step, 1, 32)
+        two_c = 2 * oest.c_function(ds, 3, L, j.l)
+        two_c_err = 2 * oest.c_function(err, 3, L, j.l)
+        assert abs(two_c - r[2]) < 4 * math.hypot(two_c_err, r[3]), (L, j.l, two_c, r)
