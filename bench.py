@@ -258,27 +258,36 @@ def cpu_oracle_rate(w, seconds: float):
     return updates / dt, len(jobs) * n_per_job / dt, threads, sample
 
 
-def traffic_from_profile(src_hash: str, workload: str):
-    """DRAM bytes (read + write) of one launch of this workload's dominant
-    kernel, from the ncu capture recorded in profiles/dram_traffic.json; None
-    when there is none or the kernel sources changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
-    try:
-        rec = json.load(open(path))
-    except (OSError, ValueError):
-        return None
-    if rec.get("source_sha256") != src_hash:
-        return None
-    return (rec.get("launches", {}).get(workload) or {}).get("dram_bytes_per_launch")
+# Sources of each timed kernel: a recorded DRAM traffic figure stands only
+# while these files are unchanged.
+KERNEL_SOURCES = {
+    "traj_kernel": ("jz_kernels.cu", "jz_traj.cuh", "jz_device.cuh"),
+    "persistent_kernel": ("jz_batch.cu", "jz_traj.cuh", "jz_device.cuh"),
+    "sw_kernel": ("jz_sw.cu", "jz_device.cuh"),
+}
 
 
-def kernel_source_hash():
+def kernel_source_hash(kernel: str) -> str:
+    """sha256 over the sources of one kernel, in the order listed."""
     csrc = os.path.join(ROOT, "paper_2304_03311_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()
+
+
+def traffic_from_profile(kernel: str, workload: str):
+    """DRAM bytes (read + write) of one launch of this workload's dominant
+    kernel, from the ncu capture recorded in profiles/dram_traffic.json; None
+    when there is none or the kernel's sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        rec = (json.load(open(path)).get("launches", {}).get(workload)) or {}
+    except (OSError, ValueError, AttributeError):
+        return None
+    if rec.get("source_sha256") != kernel_source_hash(kernel):
+        return None
+    return rec.get("dram_bytes_per_launch")
 
 
 def c_function_errors(w, results):
@@ -461,12 +470,12 @@ def run_ours(args):
     n_alg = (N_ALG_SW if sw else N_ALG)[d]
     achieved = n_alg * updates_per_launch / (kernel_ms / 1e3) / 1e12
     peak = SM_COUNT * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-    src_hash = kernel_source_hash()
+    kbase = "sw_kernel" if sw else "persistent_kernel" if plan is not None else "traj_kernel"
     kname = (f"sw_kernel<{d}>" if sw else
              "persistent_kernel" if plan is not None else f"traj_kernel<{d},...>")
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved,
                 "peak": peak, "unit": "Tintop/s", "frac": achieved / peak,
-                "traffic": traffic_from_profile(src_hash, w.name),
+                "traffic": traffic_from_profile(kbase, w.name),
                 "ops_per_update": n_alg, "kernel_ms": kernel_ms,
                 "peak_basis": "152 SMs x 128 int lanes/clk x 2070 MHz (derived)"}
 

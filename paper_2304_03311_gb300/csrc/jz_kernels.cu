@@ -23,14 +23,18 @@ constexpr int kMaxTeams = 64;
 // One CTA runs `teams` trajectories of the job that owns it (sh.teams per
 // CTA; warp teams sync with __syncwarp, a CTA team with __syncthreads).  The
 // lattices live in shared memory, or, when they do not fit there (gS !=
-// nullptr), in this CTA's own slice of an HBM buffer (L1/L2-cached).
-template <int D, bool FAST, int CW, int CLY, bool WARP>
-__global__ void __launch_bounds__(512)
+// nullptr), in this CTA's own slice of an HBM buffer (L1/L2-cached).  HBM
+// is a compile-time choice so that the shared-memory variant keeps 32-bit
+// shared addressing.  The specialised variants (CW > 0) are capped at 64
+// registers so that two 512-thread CTAs fit on an SM; the generic variant
+// keeps the full register file of one CTA.
+template <int D, bool FAST, int CW, int CLY, bool WARP, bool HBM>
+__global__ void __launch_bounds__(512, CW > 0 ? 2 : 1)
 traj_kernel(const Geom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, int n_jobs,
             const LaunchShape sh, uint32_t* __restrict__ gS)
 {
     extern __shared__ uint32_t S_shared[];
-    uint32_t* S = gS ? gS + (size_t)blockIdx.x * sh.teams * (2 * g.NR * g.GW) : S_shared;
+    uint32_t* S = HBM ? gS + (size_t)blockIdx.x * sh.teams * (2 * g.NR * g.GW) : S_shared;
     __shared__ int s_work[kMaxTeams];
     __shared__ uint32_t s_tab[8];
 
@@ -137,7 +141,10 @@ static cudaError_t launch_traj_t(const Geom& g, const PhiloxKeys& K, const JobDe
                                  cudaStream_t st, uint32_t* gS)
 {
     const size_t smem = gS ? 0 : traj_smem_bytes(g) * sh.teams;
-    auto kern = sh.warp ? traj_kernel<D, FAST, CW, CLY, true> : traj_kernel<D, FAST, CW, CLY, false>;
+    auto kern = gS ? (sh.warp ? traj_kernel<D, FAST, CW, CLY, true, true>
+                              : traj_kernel<D, FAST, CW, CLY, false, true>)
+                   : (sh.warp ? traj_kernel<D, FAST, CW, CLY, true, false>
+                              : traj_kernel<D, FAST, CW, CLY, false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
