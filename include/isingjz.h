@@ -198,7 +198,10 @@ int jarzynski_run_batch(ising_ctx* ctx, const jz_params* jobs, int n_jobs,
 
 /* Uneven batches (section 3 protocol for every job; lattices of different
  * d, L, L_t and any l) as ONE persistent launch, captured with the batched
- * FP64 estimator into a CUDA graph that jz_plan_launch replays.
+ * FP64 estimator into a CUDA graph that jz_plan_launch replays.  Swendsen-Wang
+ * jobs (update = 1) join the same graph as one launch per lattice shape (one
+ * CTA per trajectory) after the persistent kernel; every job's lattice must
+ * fit one CTA's shared memory (ISING_ERR_UNSUPPORTED otherwise).
  *   jobs, n_jobs  the transformations; all must share one seed
  *   work_outs     n_jobs caller-owned DEVICE buffers, jobs[j].n_traj int64 each
  *   est_out       caller-owned DEVICE buffer of 3 n_jobs doubles (nullable):
@@ -216,10 +219,12 @@ int jz_plan_create(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* c
                    double* est_out, int cta_threads, jz_plan** out);
 
 /* Enqueues one replay of the plan's graph on the context's stream (counter
- * reset, persistent kernel, batched estimator); use ising_sync to wait. */
+ * reset, persistent kernel, Swendsen-Wang launches, batched estimator); use
+ * ising_sync to wait. */
 int jz_plan_launch(jz_plan* plan);
 
-/* Chosen launch shape of a plan: CTA size, grid size, work items. */
+/* Chosen launch shape of the plan's persistent kernel: CTA size, grid size,
+ * work items (0 items and grid 0 when every job is Swendsen-Wang). */
 int jz_plan_info(const jz_plan* plan, int* cta_threads, int* grid, int* n_items);
 
 /* Releases the plan (waits for its queued replays). */
@@ -291,17 +296,21 @@ int jarzynski_run_plain(ising_ctx* ctx, const jz_params* p, int64_t* work_int_ou
  * whose allocator has already reserved the GPU's memory, or a loop that must
  * not stall in cudaMalloc / cudaFree (both can synchronise the device).
  * This call makes no cudaMalloc, cudaFree or other allocating call.  Its
- * scratch (one job descriptor and the N x 8d switched-site thresholds) lives
- * in a single file-scope device array of 1 MiB, which every GPU that loads
- * the library keeps until the process exits.
+ * scratch (one job descriptor and the N x 8d switched-site thresholds, or
+ * N x 2 bond thresholds for Swendsen-Wang) lives in a single file-scope device
+ * array of 1 MiB, which every GPU that loads the library keeps until the
+ * process exits.  Both updates are served; lattices beyond one CTA's shared
+ * memory (which jarzynski_run_ex runs from an HBM slice) are not.
  *   p             the transformation; final spins are not returned
  *   work_int_out  caller-owned DEVICE memory, p->n_traj int64 entries
  *   cuda_stream   cudaStream_t to enqueue on (NULL = the legacy default stream)
  * Returns once the work is enqueued: synchronise the stream before reading
  * work_int_out.  Results are bit-identical to jarzynski_run_ex.
- * Limit: p->n_step * 8 * p->d <= 262080 threshold words (N <= 16380 in 2D,
- * N <= 10920 in 3D); larger protocols return ISING_ERR_SCRATCH_LIMIT, host
- * output memory returns ISING_ERR_ARG, other errors as jarzynski_run_ex.
+ * Limit: 262080 threshold words, p->n_step * 8 * p->d for Metropolis (N <=
+ * 16380 in 2D, N <= 10920 in 3D) and p->n_step * 2 for Swendsen-Wang;
+ * larger protocols return ISING_ERR_SCRATCH_LIMIT, lattices beyond shared
+ * memory ISING_ERR_UNSUPPORTED, host output memory ISING_ERR_ARG, other
+ * errors as jarzynski_run_ex.
  * The first call on a device (the calling thread's current device) looks up
  * the array's device address once; make that first call before any stream
  * capture.  All calls share the one array and leave their contents in it;
@@ -337,7 +346,9 @@ int ising_set_threads(ising_ctx* ctx, int d, int L, int L_t, int threads);
  * transformation p -- same shape, coupling and l, n_therm = 16, N = 16,
  * n_sweep = 1, min(p->n_traj, 4864) trajectories -- keeps the fastest for p's
  * shape in the context (as ising_set_threads would) and writes it to
- * *threads (nullable).  Synchronises the context's stream.
+ * *threads (nullable).  Synchronises the context's stream.  Swendsen-Wang
+ * (p->update = 1) runs one trajectory per CTA of a fixed size: nothing is
+ * timed or stored and *threads receives that size (256 in 2D, 512 in 3D).
  * Errors: as jarzynski_run_ex. */
 int ising_autotune(ising_ctx* ctx, const jz_params* p, int* threads);
 

@@ -339,8 +339,9 @@ static void sweep(const run_t *R, int8_t *s, long long traj, int sweep_index, in
  *           towards +x, +t in the same replica, +y and +t into replica r+1 use
  *           words 0, 1, 2, 3 of Philox block (i, s, traj, dir<<1 | l<<2 | 2<<30);
  *   flips   a cluster's representative is its smallest site index; the
- *           cluster flips iff the top bit of word 0 of Philox block
- *           (root, s, traj, dir<<1 | l<<2 | 3<<30) is set. */
+ *           cluster flips iff bit (root & 31) of word (root >> 5) & 3 of Philox
+ *           block (root >> 7, s, traj, dir<<1 | l<<2 | 3<<30) is set (one block
+ *           holds the flip bits of 128 consecutive sites). */
 static int uf_find(int *parent, int a)
 {
     while (parent[a] != a) a = parent[a];
@@ -416,7 +417,9 @@ static void sw_sweep(const run_t *R, int8_t *s, int *parent, long long traj, int
     }
     for (int i = 0; i < V; ++i) {
         int root = ORACLE_MUTANT == 10 ? i : uf_find(parent, i);
-        if (philox_word(R, (uint32_t)root, (uint32_t)sweep_index, traj, 3, 0) >> 31)
+        uint32_t word = philox_word(R, (uint32_t)(root >> 7), (uint32_t)sweep_index, traj, 3,
+                                    (root >> 5) & 3);
+        if ((word >> (root & 31)) & 1u)
             s[i] = (int8_t)(-s[i]);
     }
 }

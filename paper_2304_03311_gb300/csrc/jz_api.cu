@@ -577,7 +577,10 @@ int ising_autotune(ising_ctx* ctx, const jz_params* p, int* threads)
     if (!ctx || !p) return ISING_ERR_ARG;
     int rc = check_params(p);
     if (rc) return rc;
-    if (p->update != 0) return ISING_ERR_UNSUPPORTED;
+    if (p->update == 1) {   // Swendsen-Wang: a fixed CTA per trajectory, nothing to tune
+        if (threads) *threads = jz::sw_cta_threads(p->d);
+        return ISING_OK;
+    }
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
     const jz::Geom g = make_geom(p->d, p->L, p->L_t, nrep_of(*p));
     if (!shape_fits(g)) return ISING_ERR_UNSUPPORTED;
@@ -825,10 +828,11 @@ extern "C" int jarzynski_run_noalloc(const jz_params* p, int64_t* work_int_out, 
     if (!p || !work_int_out) return ISING_ERR_ARG;
     int rc = check_params(p);
     if (rc) return rc;
-    if (p->update != 0) return ISING_ERR_UNSUPPORTED;
-    if ((size_t)p->n_step * 8 * (size_t)p->d > kNoAllocMaxThresholds) return ISING_ERR_SCRATCH_LIMIT;
+    const bool sw = p->update == 1;   // Swendsen-Wang: one trajectory per CTA
+    const size_t n_tcut = (size_t)p->n_step * (sw ? 2 : 8 * (size_t)p->d);
+    if (n_tcut > kNoAllocMaxThresholds) return ISING_ERR_SCRATCH_LIMIT;
     const jz::Geom g = make_geom(p->d, p->L, p->L_t, nrep_of(*p));
-    if (!shape_fits(g)) return ISING_ERR_UNSUPPORTED;
+    if (sw ? !sw_fits(g) : !shape_fits(g)) return ISING_ERR_UNSUPPORTED;
     if (!is_device_ptr(work_int_out)) return ISING_ERR_ARG;
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess) {
@@ -854,11 +858,11 @@ extern "C" int jarzynski_run_noalloc(const jz_params* p, int64_t* work_int_out, 
     J.n_traj = p->n_traj;
     J.traj0 = p->traj0;
     J.cta0 = 0;
-    build_tables(*p, J.tb, g_noalloc_host_tcut, 0);
+    if (sw) build_bond_tables(*p, J.tb, g_noalloc_host_tcut, 0);
+    else build_tables(*p, J.tb, g_noalloc_host_tcut, 0);
     J.tcut = d_tcut;
     J.w_out = (long long*)work_int_out;
     J.spins_out = nullptr;
-    const size_t n_tcut = (size_t)p->n_step * 8 * p->d;
     // pageable sources: each copy returns once its bytes are staged, so the
     // host buffers may be reused as soon as the call returns
     if ((rc = cuda_err(cudaMemcpyAsync(d_tcut, g_noalloc_host_tcut.data(),
@@ -867,6 +871,7 @@ extern "C" int jarzynski_run_noalloc(const jz_params* p, int64_t* work_int_out, 
     if ((rc = cuda_err(cudaMemcpyAsync(base, &J, sizeof J, cudaMemcpyHostToDevice, st))))
         return rc;
     const jz::PhiloxKeys K = key_schedule(p->seed);
+    if (sw) return cuda_err(jz::launch_sw(p->d, g, K, (const jz::JobDesc*)base, 1, p->n_traj, st));
     const jz::LaunchShape sh = shape_for(g, 0);
     return cuda_err(jz::launch_traj(p->d, g, K, (const jz::JobDesc*)base, 1,
                                     (p->n_traj + sh.teams - 1) / sh.teams, sh, st));
@@ -888,6 +893,18 @@ struct jz_plan {
     jz::PhiloxKeys K{};
     DevBuf jobs, items, tcut, counter, est_jobs;
     double* est_out = nullptr;
+    // Swendsen-Wang jobs: one launch per lattice shape after the persistent
+    // kernel (one CTA per trajectory, no work items)
+    struct SwGroup {
+        jz::Geom g{};
+        int d = 0, n_jobs = 0;
+        long long n_cta = 0;
+        DevBuf jobs;
+        std::vector<jz::JobDesc> h_jobs;
+        std::vector<size_t> toff;
+    };
+    std::vector<SwGroup> sw;
+    DevBuf sw_tcut;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -900,7 +917,10 @@ void plan_release(jz_plan* pl)
     ising_ctx* ctx = pl->ctx;
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     if (pl->graph) cudaGraphDestroy(pl->graph);
-    for (DevBuf* b : {&pl->jobs, &pl->items, &pl->tcut, &pl->counter, &pl->est_jobs})
+    std::vector<DevBuf*> bufs = {&pl->jobs, &pl->items, &pl->tcut, &pl->counter, &pl->est_jobs,
+                                 &pl->sw_tcut};
+    for (auto& G : pl->sw) bufs.push_back(&G.jobs);
+    for (DevBuf* b : bufs)
         if (b->ptr) {
             cudaFree(b->ptr);
             ctx->used -= b->bytes;
@@ -923,9 +943,51 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
     std::vector<uint32_t> tcut;
     std::vector<size_t> toff(n_jobs);
     std::vector<std::pair<double, int2>> items;
+    std::vector<uint32_t> sw_tcut;
     size_t smem = 0;
     for (int j = 0; j < n_jobs; ++j) {
         const jz_params& p = jobs[j];
+        if (p.update == 1) {   // Swendsen-Wang: grouped by lattice shape
+            const jz::Geom g = make_geom(p.d, p.L, p.L_t, nrep_of(p));
+            if (!sw_fits(g)) {
+                plan_release(pl);
+                return ISING_ERR_UNSUPPORTED;
+            }
+            size_t gi = 0;
+            while (gi < pl->sw.size() &&
+                   !(pl->sw[gi].d == p.d && pl->sw[gi].g.L == g.L && pl->sw[gi].g.Lt == g.Lt &&
+                     pl->sw[gi].g.nrep == g.nrep))
+                ++gi;
+            if (gi == pl->sw.size()) {
+                pl->sw.emplace_back();
+                pl->sw.back().g = g;
+                pl->sw.back().d = p.d;
+            }
+            jz_plan::SwGroup& G = pl->sw[gi];
+            jz::JobDesc J{};
+            J.l = p.l;
+            J.n_step = p.n_step;
+            J.n_sweep = p.n_sweep;
+            J.n_therm = p.n_therm;
+            J.dir = p.direction;
+            J.prot = p.protocol == 2 ? 2 : 1;
+            cut_range(p, &J.g0, &J.g1);
+            J.k_begin = 0;
+            J.k_end = p.n_step;
+            J.n_traj = p.n_traj;
+            J.traj0 = p.traj0;
+            J.cta0 = G.n_cta;
+            const size_t off = sw_tcut.size();
+            sw_tcut.resize(off + (size_t)p.n_step * 2);
+            build_bond_tables(p, J.tb, sw_tcut, off);
+            J.w_out = (long long*)work_outs[j];
+            J.spins_out = nullptr;
+            G.h_jobs.push_back(J);
+            G.toff.push_back(off);
+            G.n_cta += p.n_traj;
+            ++G.n_jobs;
+            continue;
+        }
         jz::BatchJob& B = bj[j];
         B.g = make_geom(p.d, p.L, p.L_t, nrep_of(p));
         B.D = p.d;
@@ -985,6 +1047,20 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
     }
     uint32_t* d_tcut = (uint32_t*)pl->tcut.ptr;
     for (int j = 0; j < n_jobs; ++j) bj[j].J.tcut = d_tcut + toff[j];
+    if (!pl->sw.empty()) {
+        if ((rc = ensure(ctx, pl->sw_tcut, sw_tcut.size() * sizeof(uint32_t)))) {
+            plan_release(pl);
+            return rc;
+        }
+        for (auto& G : pl->sw) {
+            for (size_t i = 0; i < G.h_jobs.size(); ++i)
+                G.h_jobs[i].tcut = (uint32_t*)pl->sw_tcut.ptr + G.toff[i];
+            if ((rc = ensure(ctx, G.jobs, G.h_jobs.size() * sizeof(jz::JobDesc)))) {
+                plan_release(pl);
+                return rc;
+            }
+        }
+    }
     std::vector<int2> it(items.size());
     for (size_t i = 0; i < items.size(); ++i) it[i] = items[i].second;
     std::vector<jz::EstJob> ej(n_jobs);
@@ -996,15 +1072,24 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
         ej[j].scale = jobs[j].beta / (double)jobs[j].n_step;
     }
     cudaStream_t st = ctx->stream;
-    if ((rc = cuda_err(cudaMemcpyAsync(pl->tcut.ptr, tcut.data(), tcut.size() * sizeof(uint32_t),
-                                       cudaMemcpyHostToDevice, st))) ||
-        (rc = cuda_err(cudaMemcpyAsync(pl->jobs.ptr, bj.data(), bj.size() * sizeof(jz::BatchJob),
-                                       cudaMemcpyHostToDevice, st))) ||
-        (rc = cuda_err(cudaMemcpyAsync(pl->items.ptr, it.data(), it.size() * sizeof(int2),
-                                       cudaMemcpyHostToDevice, st))) ||
-        (rc = cuda_err(cudaMemcpyAsync(pl->est_jobs.ptr, ej.data(), ej.size() * sizeof(jz::EstJob),
-                                       cudaMemcpyHostToDevice, st))) ||
-        (rc = cuda_err(cudaStreamSynchronize(st)))) {
+    // host -> device copies of the tables (empty ones skipped)
+    std::vector<std::tuple<void*, const void*, size_t>> copies = {
+        {pl->tcut.ptr, tcut.data(), tcut.size() * sizeof(uint32_t)},
+        {pl->jobs.ptr, bj.data(), bj.size() * sizeof(jz::BatchJob)},
+        {pl->items.ptr, it.data(), it.size() * sizeof(int2)},
+        {pl->est_jobs.ptr, ej.data(), ej.size() * sizeof(jz::EstJob)},
+        {pl->sw_tcut.ptr, sw_tcut.data(), sw_tcut.size() * sizeof(uint32_t)}};
+    for (auto& G : pl->sw)
+        copies.emplace_back(G.jobs.ptr, G.h_jobs.data(), G.h_jobs.size() * sizeof(jz::JobDesc));
+    for (const auto& c : copies) {
+        if (std::get<2>(c) == 0) continue;
+        if ((rc = cuda_err(cudaMemcpyAsync(std::get<0>(c), std::get<1>(c), std::get<2>(c),
+                                           cudaMemcpyHostToDevice, st)))) {
+            plan_release(pl);
+            return rc;
+        }
+    }
+    if ((rc = cuda_err(cudaStreamSynchronize(st)))) {
         plan_release(pl);
         return rc;
     }
@@ -1015,7 +1100,7 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
         plan_release(pl);
         return rc;
     }
-    if (per_sm < 1) {
+    if (per_sm < 1 && pl->n_items > 0) {
         plan_release(pl);
         return ISING_ERR_UNSUPPORTED;
     }
@@ -1029,12 +1114,19 @@ int plan_enqueue(jz_plan* pl)
 {
     cudaStream_t st = pl->ctx->stream;
     int rc;
-    if ((rc = cuda_err(cudaMemsetAsync(pl->counter.ptr, 0, sizeof(unsigned int), st)))) return rc;
-    if ((rc = cuda_err(jz::launch_persistent((const jz::BatchJob*)pl->jobs.ptr,
-                                             (const int2*)pl->items.ptr, pl->n_items,
-                                             (unsigned int*)pl->counter.ptr, pl->K, pl->grid,
-                                             pl->threads, pl->smem, st))))
-        return rc;
+    if (pl->n_items > 0) {
+        if ((rc = cuda_err(cudaMemsetAsync(pl->counter.ptr, 0, sizeof(unsigned int), st))))
+            return rc;
+        if ((rc = cuda_err(jz::launch_persistent((const jz::BatchJob*)pl->jobs.ptr,
+                                                 (const int2*)pl->items.ptr, pl->n_items,
+                                                 (unsigned int*)pl->counter.ptr, pl->K, pl->grid,
+                                                 pl->threads, pl->smem, st))))
+            return rc;
+    }
+    for (const auto& G : pl->sw)
+        if ((rc = cuda_err(jz::launch_sw(G.d, G.g, pl->K, (const jz::JobDesc*)G.jobs.ptr,
+                                         G.n_jobs, G.n_cta, st))))
+            return rc;
     if (pl->est_out)
         return cuda_err(jz::launch_estimator_batch((const jz::EstJob*)pl->est_jobs.ptr, pl->n_jobs,
                                                    pl->est_out, st));
@@ -1080,13 +1172,15 @@ int jz_plan_create(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* c
     for (int j = 0; j < n_jobs; ++j) {
         const int rc = check_params(&jobs[j]);
         if (rc) return rc;
-        if (jobs[j].update != 0) return ISING_ERR_UNSUPPORTED;
         if (jobs[j].seed != jobs[0].seed || !work_outs[j] || !is_device_ptr(work_outs[j]))
             return ISING_ERR_ARG;
     }
     if (est_out && !is_device_ptr(est_out)) return ISING_ERR_ARG;
     int rc;
     int cta = cta_threads;
+    bool any_metropolis = false;
+    for (int j = 0; j < n_jobs; ++j) any_metropolis |= jobs[j].update == 0;
+    if (cta == 0 && !any_metropolis) cta = 256;   // nothing runs in the persistent kernel
     if (cta == 0) {
         // autotune on a reduced copy: 1/16 of the trajectories, 8 + 8 sweeps
         std::vector<jz_params> small(jobs, jobs + n_jobs);

@@ -23,6 +23,8 @@ cudaError_t launch_traj(int D, const Geom& g, const PhiloxKeys& K, const JobDesc
 cudaError_t launch_estimator(const long long* w_int, int n, double scale, int direction,
                              int n_blocks, double* out, cudaStream_t st);
 size_t sw_smem_bytes(const Geom& g);
+// Threads of one Swendsen-Wang CTA (one trajectory) for dimension D.
+int sw_cta_threads(int D);
 // gS: nullptr to keep each trajectory's state in shared memory, else an HBM
 // buffer of n_cta * sw_smem_bytes(g) bytes, one slice per CTA.
 cudaError_t launch_sw(int D, const Geom& g, const PhiloxKeys& K, const JobDesc* jobs,

@@ -6,27 +6,26 @@
 //   lab[V]   int32 cluster labels (lab[i] <= i always: a forest whose roots are
 //            the smallest site index of their cluster)
 //   sp[VW]   spin bits, bit i of the lattice = 1 for spin -1
-//   bx, bt, bg, by [VW]  bond bits of the current sweep by direction; bt
-//            doubles as the warps' rings of 32 queued cluster roots, bg as the
-//            roots' flip bits
+//   bx, bt, bg, by [VW]  bond bits of the current sweep by direction
+//   fz[VW]   flip bits of the current sweep, bit i for site i
 //   bq       per warp 32 queued bonds
-// Warps work on chunks of 32 consecutive sites.  One sweep is four phases
+// Warps work on chunks of 32 consecutive sites.  One sweep is three phases
 // separated by CTA barriers:
 //   B1 every site draws one Philox block (i, s, traj, dir<<1 | l<<2 | 2<<30);
 //      word w in {+x, +t same replica, +y, +t into replica r+1} activates that
 //      forward link when both spins are equal and the word is below the link's
 //      bond threshold floor(2^32 (1 - e^{-2K})).  +x bonds between lanes of
 //      one chunk form runs found by one ballot; each site's label is set to
-//      its run's first site.  The other active bonds become bits.
+//      its run's first site.  The other active bonds become bits.  Block b
+//      of the flip stream (b, s, traj, dir<<1 | l<<2 | 3<<30) gives the flip
+//      bits of sites 128 b ... 128 b + 127 (words 0..3, bit i & 31).
 //   B2 the recorded bonds, queued per warp and taken 32 at a time, merge
-//      clusters by lock-free union with atomicMin (the larger root is hooked
-//      under the smaller one, so the root of a cluster is its smallest site
-//      index);
-//   C  every site stores its root; the roots, queued 32 at a time, draw
-//      Philox block (root, s, traj, dir<<1 | l<<2 | 3<<30) and a cluster
-//      flips iff the top bit of its root's word 0 is set;
-//   D  every site flips iff its root's flip bit is set (a ballot assembles
-//      32 sites into one spin word).
+//      clusters by lock-free union (the larger root is hooked under the
+//      smaller one, so the root of a cluster is its smallest site index);
+//   CD every site finds its root (read only) and flips iff the root's flip
+//      bit is set: each cluster flips with probability 1/2, independently of
+//      the others and of its bonds (a ballot assembles 32 sites into one spin
+//      word).
 // The cluster partition, hence the minimum-index root of every cluster, does
 // not depend on the order of the unions, so the result is the same bit for bit
 // as a sequential union-find over the same bonds.
@@ -47,6 +46,15 @@ namespace {
 // Threads per CTA (one trajectory): 256 in 2D, 512 in 3D, whose extra +y
 // bonds make the union phase longer (measured on 2D 64^2 and 3D 16^3).
 __host__ __device__ constexpr int sw_threads(int D) { return D == 3 ? 512 : 256; }
+
+// Minimum CTAs per SM for the register allocation.  0 for the shared-memory
+// variants leaves the choice to the compiler (40 registers; on the 2D L = 64
+// scan 7.5e10 site updates/s against 7.0e10 when sized for five CTAs, 48
+// registers); the HBM variants are sized so that they do not spill.
+__host__ __device__ constexpr int sw_min_ctas(int D, bool hbm)
+{
+    return hbm ? (D == 3 ? 3 : 5) : 0;
+}
 
 // Division by a fixed divisor d >= 1 for numerators n < 2^31 (Granlund and
 // Montgomery, PLDI'94): with s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d)
@@ -78,13 +86,6 @@ struct SwGeom {
     int G;        // Philox blocks per colour row of the hot start, ceil(L / 8)
     FastDiv dL, dLy, dLt;
 };
-
-// Words of the region holding bt in phases B1, B2 and the warps' root rings
-// (32 per warp) in phase C.
-__host__ __device__ inline int ring_words(int VW, int threads)
-{
-    return VW > threads ? VW : threads;
-}
 
 struct Site {
     int x, y, t, r, row;
@@ -134,9 +135,9 @@ __device__ __forceinline__ int find_root(volatile int* lab, int a)
     }
 }
 
-// Root of a without writes: in the compression phase only a node's owner may
-// store to it (a halving store racing with the owner's root store could leave
-// a non-root ancestor behind).
+// Root of a without writes: in the flip phase only a node's owner may store
+// to it (a halving store racing with the owner's root store could leave a
+// non-root ancestor behind).
 __device__ __forceinline__ int find_root_ro(const volatile int* lab, int a)
 {
     int p;
@@ -162,24 +163,24 @@ __device__ __forceinline__ void merge(int* lab, int a, int b)
     }
 }
 
-template <int D>
-__global__ void __launch_bounds__(sw_threads(D))
+template <int D, bool HBM>
+__global__ void __launch_bounds__(sw_threads(D), sw_min_ctas(D, HBM))
 sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, int n_jobs,
           uint32_t* __restrict__ gS, size_t g_words)
 {
     // the trajectory's state: shared memory, or this CTA's slice of an HBM
-    // buffer when it does not fit (gS != nullptr)
+    // buffer when it does not fit (HBM, a compile-time choice so that the
+    // shared-memory variant keeps 32-bit shared addressing)
     extern __shared__ uint32_t smem_shared[];
-    uint32_t* smem = gS ? gS + (size_t)blockIdx.x * g_words : smem_shared;
+    uint32_t* smem = HBM ? gS + (size_t)blockIdx.x * g_words : smem_shared;
     int* lab = (int*)smem;
     uint32_t* sp = smem + g.V;
     uint32_t* bx = sp + g.VW;       // +x bonds leaving a warp chunk or its row
     uint32_t* bt = bx + g.VW;       // +t bonds inside one replica
-    uint32_t* bg = bt + ring_words(g.VW, sw_threads(D));   // +t bonds into replica r+1
+    uint32_t* bg = bt + g.VW;       // +t bonds into replica r+1
     uint32_t* by = bg + g.VW;       // +y bonds (3D)
-    uint32_t* fb = bg;              // root flip bits (phases C, D)
-    int* s_ring = (int*)bt;         // per warp a ring of 32 queued roots (phase C)
-    int* s_bq = (int*)(by + (D == 3 ? g.VW : 0));   // per warp 32 queued bonds (phase B2)
+    uint32_t* fz = by + (D == 3 ? g.VW : 0);   // flip bits
+    int* s_bq = (int*)(fz + g.VW);  // per warp 32 queued bonds (phase B2)
 
     // the job owning this CTA: the last j with jobs[j].cta0 <= blockIdx.x
     int lo = 0, hi = n_jobs - 1;
@@ -265,6 +266,15 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
             t_glue = __ldg(&bonds[2 * k + 1]);
         }
         const uint32_t cb = c3 | (2u << 30);
+        // the sweep's flip bits: one Philox block per 128 sites, spread over
+        // the lanes of every warp so that each warp runs one Philox pass
+        for (int b = warp + lane * n_warps; 4 * b < g.VW; b += 32 * n_warps) {
+            const uint4 u = philox_r0((uint32_t)b, (uint32_t)sw, hi1, lo1, c3 | (3u << 30), K);
+            fz[4 * b] = u.x;
+            if (4 * b + 1 < g.VW) fz[4 * b + 1] = u.y;
+            if (4 * b + 2 < g.VW) fz[4 * b + 2] = u.z;
+            if (4 * b + 3 < g.VW) fz[4 * b + 3] = u.w;
+        }
         // phase B1: bond draws.  A +x bond between two lanes of one warp
         // chunk joins a run of consecutive sites; every site of a run gets the
         // run's first site as its label (a star).  All other active bonds are
@@ -367,7 +377,6 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
                 const uint32_t wx = bx[q], wt = bt[q], wg = bg[q];
                 const uint32_t wy = D == 3 ? by[q] : 0u;
                 __syncwarp();
-                if (lane == 0) bg[q] = 0u;      // bg doubles as the flip bits of phase C
                 push(wx, i << 2);
                 push(wt, (i << 2) | 1);
                 push(wg, (i << 2) | 2);
@@ -377,49 +386,17 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
             if (lane < nb) merge_entry(bq[lane]);
         }
         __syncthreads();
-        // phase C: every site stores its root; the roots are queued per warp
-        // and draw their flip bits 32 at a time
-        const uint32_t cf = c3 | (3u << 30);
-        int* ring = s_ring + warp * 32;
-        int n_pend = 0;
-        for (int base = warp * 32; base < g.V; base += chunk) {
-            const int i = base + lane;
-            bool is_root = false;
-            if (i < g.V) {
-                const int root = find_root_ro((volatile int*)lab, i);
-                is_root = root == i;
-                if (!is_root) lab[i] = root;
-            }
-            const uint32_t m = __ballot_sync(0xFFFFFFFFu, is_root);
-            const int rank = __popc(m & ((1u << lane) - 1u));
-            const int room = 32 - n_pend;
-            if (is_root && rank < room) ring[n_pend + rank] = i;
-            n_pend += __popc(m);
-            if (n_pend >= 32) {
-                __syncwarp();
-                const int r = ring[lane];
-                const uint4 u = philox_r0((uint32_t)r, (uint32_t)sw, hi1, lo1, cf, K);
-                if (u.x >> 31) atomicOr(&fb[r >> 5], 1u << (r & 31));
-                __syncwarp();
-                if (is_root && rank >= room) ring[rank - room] = i;
-                n_pend -= 32;
-            }
-        }
-        __syncwarp();
-        if (lane < n_pend) {
-            const int r = ring[lane];
-            const uint4 u = philox_r0((uint32_t)r, (uint32_t)sw, hi1, lo1, cf, K);
-            if (u.x >> 31) atomicOr(&fb[r >> 5], 1u << (r & 31));
-        }
-        __syncthreads();
-        // phase D: flip the clusters
+        // phase CD: every site flips iff its cluster's root drew a set flip
+        // bit.  Each site stores its root as it goes, which shortens the walks
+        // of later sites through it (a concurrent reader sees the old parent
+        // or the root, both ancestors)
         for (int base = warp * 32; base < g.V; base += chunk) {
             const int i = base + lane;
             int f = 0;
             if (i < g.V) {
-                // fb was written by atomics: read it past L1 when it lives in HBM
-                const int root = lab[i];
-                f = (int)((((volatile uint32_t*)fb)[root >> 5] >> (root & 31)) & 1);
+                const int root = find_root_ro((volatile int*)lab, i);
+                if (root != i) lab[i] = root;
+                f = (int)((fz[root >> 5] >> (root & 31)) & 1u);
             }
             const uint32_t m = __ballot_sync(0xFFFFFFFFu, f);
             if (lane == 0) sp[base >> 5] ^= m;
@@ -458,13 +435,14 @@ SwGeom make_swgeom(int D, const Geom& geo)
 
 }  // namespace
 
+int sw_cta_threads(int D) { return sw_threads(D); }
+
 size_t sw_smem_bytes(const Geom& geo)
 {
     const size_t V = (size_t)geo.nrep * geo.Lt * geo.Ly * geo.L;
     const int VW = (int)((V + 31) / 32);
     const int threads = sw_threads(geo.Ly > 1 ? 3 : 2);
-    const size_t words = 3 * (size_t)VW + ring_words(VW, threads) + (geo.Ly > 1 ? VW : 0) +
-                         (size_t)threads;
+    const size_t words = (geo.Ly > 1 ? 6 : 5) * (size_t)VW + (size_t)threads;
     return V * sizeof(int) + words * sizeof(uint32_t);
 }
 
@@ -474,7 +452,8 @@ cudaError_t launch_sw(int D, const Geom& geo, const PhiloxKeys& K, const JobDesc
     const SwGeom g = make_swgeom(D, geo);
     const size_t bytes = sw_smem_bytes(geo);
     const size_t smem = gS ? 0 : bytes;
-    auto kern = D == 3 ? sw_kernel<3> : sw_kernel<2>;
+    auto kern = D == 3 ? (gS ? sw_kernel<3, true> : sw_kernel<3, false>)
+                       : (gS ? sw_kernel<2, true> : sw_kernel<2, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;

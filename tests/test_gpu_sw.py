@@ -1,14 +1,16 @@
 """GPU parity of the Swendsen-Wang update (update = 1) against the CPU oracle.
 
 Bit-exact: W_int per trajectory and the final spins.  The cluster partition of
-a sweep is unique, and so is its smallest site index, the root whose Philox
-draw decides the cluster's flip; so the concurrent union-find of the GPU and
+a sweep is unique, and so is its smallest site index, the root whose bit in
+the sweep's flip stream decides the cluster's flip; so the concurrent union-find of the GPU and
 the sequential one of the oracle must give the same configuration after every
 sweep.  Cases span several warps of sites and ragged tails (V not a multiple of
 32), both directions, 2D and 3D, l = 0 and l = L-1, beta = 0 (no bonds) and a
 deep ordered phase (one big cluster), L_t = 2 and L = 2, several sweeps per
 step, large traj0 and seeds; the full 2D L = 64 scan workload is checked on
-trajectories sampled from one batched launch.
+trajectories sampled from one batched launch.  The allocation-free entry
+point and persistent plans (alone and mixed with Metropolis jobs) give the
+same bits.
 """
 import numpy as np
 import pytest
@@ -149,21 +151,83 @@ def test_server_runs_the_cluster_update(ctx):
         jz.jz_server_free(server)
 
 
-@pytest.mark.parametrize("entry", ["autotune", "plain", "noalloc", "plan"])
-def test_other_entry_points_refuse_the_cluster_update(ctx, entry):
+def test_plain_baseline_refuses_the_cluster_update(ctx):
     job = SMALL[0]
-    p = params(job)
     w = torch.empty(job.n_traj, dtype=torch.int64, device="cuda")
     with pytest.raises(jz.IsingError) as e:
-        if entry == "autotune":
-            jz.ising_autotune(ctx, p)
-        elif entry == "plain":
-            jz.jarzynski_run_plain(ctx, p, w)
-        elif entry == "noalloc":
-            jz.jarzynski_run_noalloc(p, w)
-        else:
-            jz.jz_plan_create(ctx, [p], [w])
+        jz.jarzynski_run_plain(ctx, params(job), w)
     assert e.value.code == jz.ISING_ERR_UNSUPPORTED
+
+
+def test_autotune_reports_the_fixed_cta(ctx):
+    assert jz.ising_autotune(ctx, params(SMALL[0])) == 256
+    assert jz.ising_autotune(ctx, params(SMALL[9])) == 512
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 6, 10, 13])
+def test_noalloc_equals_the_oracle(k):
+    job = SMALL[k]
+    w = torch.full((job.n_traj,), -7, dtype=torch.int64, device="cuda")
+    jz.jarzynski_run_noalloc(params(job), w)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(w.cpu().numpy(), oracle_run(job)[0])
+
+
+def test_noalloc_refuses_hbm_lattices():
+    job = wl.Job(2, 64, 512, BC2, 20, 2, 1, 4, seed=31, n_therm=2)   # beyond shared memory
+    w = torch.empty(job.n_traj, dtype=torch.int64, device="cuda")
+    with pytest.raises(jz.IsingError) as e:
+        jz.jarzynski_run_noalloc(params(job), w)
+    assert e.value.code == jz.ISING_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("cta", [256, 0])
+def test_plan_with_cluster_and_metropolis_jobs(ctx, cta):
+    """A plan mixing Swendsen-Wang jobs of three shapes with Metropolis jobs:
+    one graph replay gives every job the bits of the oracle, and the batched
+    estimator the oracle's Delta S_2."""
+    import oracle.estimator as oest
+    sw_jobs = [SMALL[i] for i in (0, 1, 6, 9, 10)]
+    me_jobs = [wl.Job(2, 16, 16, BC2, 3, 12, 1, 40, seed=0, n_therm=5),
+               wl.Job(3, 8, 8, BC3, 2, 10, 1, 20, seed=0, n_therm=4, direction=-1)]
+    sw_jobs = [j.with_(seed=0) for j in sw_jobs]
+    ps = [params(j) for j in sw_jobs]
+    for j in me_jobs:
+        ps.append(jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj,
+                                 j.seed, n_therm=j.n_therm, direction=j.direction))
+    jobs = sw_jobs + me_jobs
+    outs = [torch.full((j.n_traj,), -9, dtype=torch.int64, device="cuda") for j in jobs]
+    est = torch.zeros(3 * len(jobs), dtype=torch.float64, device="cuda")
+    plan = jz.jz_plan_create(ctx, ps, outs, est, cta)
+    try:
+        jz.jz_plan_launch(plan)
+        jz.ising_sync(ctx)
+    finally:
+        jz.jz_plan_free(plan)
+    e = est.cpu().numpy().reshape(-1, 3)
+    for i, (j, o) in enumerate(zip(jobs, outs)):
+        W = o.cpu().numpy()
+        upd = SW if i < len(sw_jobs) else 0
+        ref, _ = oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj, j.seed,
+                            n_therm=j.n_therm, direction=j.direction, traj0=j.traj0, update=upd)
+        np.testing.assert_array_equal(W, ref)
+        ref_ds, _ = oest.delta_s2_with_error(ref, j.beta, j.n_step, j.direction, 32)
+        assert abs(e[i, 1] - ref_ds) <= 1e-12 * max(abs(ref_ds), 1.0)
+
+
+def test_plan_of_cluster_jobs_only(ctx):
+    jobs = [SMALL[i].with_(seed=0) for i in (3, 7)]
+    outs = [torch.empty(j.n_traj, dtype=torch.int64, device="cuda") for j in jobs]
+    plan = jz.jz_plan_create(ctx, [params(j) for j in jobs], outs, None, 0)
+    try:
+        _, _, n_items = jz.jz_plan_info(plan)
+        assert n_items == 0   # no Metropolis work items
+        jz.jz_plan_launch(plan)
+        jz.ising_sync(ctx)
+    finally:
+        jz.jz_plan_free(plan)
+    for j, o in zip(jobs, outs):
+        np.testing.assert_array_equal(o.cpu().numpy(), oracle_run(j)[0])
 
 
 @pytest.mark.parametrize("job", [
