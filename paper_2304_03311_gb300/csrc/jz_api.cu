@@ -232,7 +232,14 @@ jz::LaunchShape shape_for(const jz::Geom& g, int cta_threads)
     if (col <= 32 && !big) {
         int ts = 32 / col;
         if (ts > g.Lt) ts = g.Lt;
-        s.team_threads = col * ts;
+        // a whole time column per thread slot leaves room in the warp: split
+        // the replicas over more slots (more warps per trajectory, the same
+        // lanes in use), rs a power of two dividing n
+        int rs = 1;
+        if (ts == g.Lt && 32 % (col * ts) == 0)
+            for (int r = 2; col * ts * r <= 32 && r <= g.nrep; r *= 2)
+                if (g.nrep % r == 0) rs = r;
+        s.team_threads = col * ts * rs;
         s.warp = 1;
         const int per_warp = 32 / s.team_threads;
         int warps = (cta_threads > 0 ? cta_threads : 128) / 32;

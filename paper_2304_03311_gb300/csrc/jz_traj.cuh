@@ -14,9 +14,11 @@
 // Nibble-wise sums of XORs give the anti-aligned neighbour count of all eight
 // sites at once (at most 6 < 16, so no carries cross nibbles).
 //
-// Team mapping: a team of GW * L_y * TS threads; thread (t0, y, q) owns word q
-// of row y of the time slices t0, t0 + TS, ... in both replicas and colours,
-// so all its index and wrap arithmetic is fixed.  Rows t >= 2 take the bulk
+// Team mapping: a team of GW * L_y * TS * RS threads; thread (r0, t0, y, q)
+// owns word q of row y of the time slices t0, t0 + TS, ... in the replicas
+// r0, r0 + RS, ... and both colours, so all its index and wrap arithmetic is
+// fixed.  RS > 1 only when TS = L_t (a whole time column per thread slot):
+// lattices so small that one replica's words leave most of a warp idle.  Rows t >= 2 take the bulk
 // path; the rows t = 0, 1 next to the cut blend in the glued replica and
 // handle the switched column x = l.  CW, CLY > 0 fix GW and L_y at compile
 // time (neighbour loads then use immediate offsets); 0 reads them from Geom.
@@ -83,6 +85,7 @@ struct Traj {
     uint32_t hi1, lo1;        // M1 * traj: round 0 of Philox for counter word 2
     uint32_t c3base;          // dir bit << 1 | l << 2
     int q, y, t0, TS;         // this thread's word, row y, first slice and slice step
+    int r0, RS;               // first replica and replica step
     int d_qm, d_qp;           // word offset of the x-shift neighbour word (p = 0 / 1)
     int d_ym, d_yp;           // word offsets of the rows y-1 / y+1 (3D)
     uint32_t vmask;           // nibbles of word q that hold sites (ragged rows)
@@ -103,14 +106,18 @@ struct Traj {
         hi1 = (uint32_t)(p1 >> 32);
         lo1 = (uint32_t)p1;
         const int col = W() * Ly();
-        TS = nthr / col;
-        if (tid < 0) {
+        const int slots = nthr / col;   // threads per word column
+        TS = slots < g.Lt ? slots : g.Lt;
+        RS = slots / TS;
+        if (tid < 0 || tid / col >= TS * RS) {
             q = y = 0;
             t0 = g.Lt;
+            r0 = g.nrep;
         } else {
             q = tid % W();
             y = (tid / W()) % Ly();
-            t0 = tid / col;
+            t0 = (tid / col) % TS;
+            r0 = (tid / col) / TS;
         }
         d_qm = (q == 0 ? W() - 1 : q - 1) - q;
         d_qp = (q == W() - 1 ? 0 : q + 1) - q;
@@ -232,7 +239,7 @@ struct Traj {
         const int pc = (c + y) & 1;
         const int wrap_up = -(Lt - 1) * rw;
 #pragma unroll 1
-        for (int r = 0; r < g.nrep; ++r) {
+        for (int r = r0; r < g.nrep; r += RS) {
             int t = t0;
             int w = (r * Lt + t0) * rw + y * W() + q;
             uint32_t c0 = (uint32_t)(((r * Lt + t0) * Ly() + y) * g.G + 2 * q);
@@ -261,7 +268,7 @@ struct Traj {
         const int cw = g.nrep * g.Lt * rw;
         for (int c = 0; c < 2; ++c) {
             uint32_t* base = S + c * cw;
-            for (int r = 0; r < g.nrep; ++r) {
+            for (int r = r0; r < g.nrep; r += RS) {
                 int w = (r * g.Lt + t0) * rw + y * W() + q;
                 for (int t = t0; t < g.Lt; t += TS, w += TS * rw) {
                     const int p = (c + t + y) & 1;
@@ -285,7 +292,7 @@ struct Traj {
         for (int c = 0; c < 2; ++c) {
             uint32_t* base = S + c * cw;
             const uint32_t c3 = (uint32_t)c | c3base | (1u << 30);
-            for (int r = 0; r < g.nrep; ++r) {
+            for (int r = r0; r < g.nrep; r += RS) {
                 int w = (r * g.Lt + t0) * rw + y * W() + q;
                 uint32_t c0 = (uint32_t)(((r * g.Lt + t0) * Ly() + y) * g.G + 2 * q);
                 for (int t = t0; t < g.Lt; t += TS, w += TS * rw, c0 += cstride) {
