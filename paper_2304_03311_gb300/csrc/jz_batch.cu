@@ -94,6 +94,7 @@ estimator_batch_kernel(const EstJob* __restrict__ jobs, double* __restrict__ out
 {
     __shared__ double s_max[kMaxJackBlocksB], s_sum[kMaxJackBlocksB];
     __shared__ int s_lo[kMaxJackBlocksB + 1];
+    __shared__ double s_theta[kMaxJackBlocksB + 1];
     const EstJob E = jobs[blockIdx.x];
     const int B = E.n_blocks, n = E.n;
     const int size = n / B;
@@ -114,32 +115,7 @@ estimator_batch_kernel(const EstJob* __restrict__ jobs, double* __restrict__ out
         if (lane == 0) { s_max[b] = m; s_sum[b] = acc; }
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    const double sign = E.direction > 0 ? -1.0 : 1.0;
-    auto lse_without = [&](int skip, int count) {
-        double M = -INFINITY;
-        for (int b = 0; b < B; ++b) if (b != skip) M = fmax(M, s_max[b]);
-        double tot = 0.0;
-        for (int b = 0; b < B; ++b) if (b != skip) tot += s_sum[b] * exp(s_max[b] - M);
-        return M + log(tot) - log((double)count);
-    };
-    const double full = lse_without(-1, n);
-    double err = 0.0;
-    if (B >= 2) {
-        double theta[kMaxJackBlocksB];
-        double mean = 0.0;
-        for (int b = 0; b < B; ++b) {
-            theta[b] = sign * lse_without(b, n - (s_lo[b + 1] - s_lo[b]));
-            mean += theta[b];
-        }
-        mean /= B;
-        double ss = 0.0;
-        for (int b = 0; b < B; ++b) ss += (theta[b] - mean) * (theta[b] - mean);
-        err = sqrt((double)(B - 1) / B * ss);
-    }
-    out[3 * blockIdx.x + 0] = full;
-    out[3 * blockIdx.x + 1] = sign * full;
-    out[3 * blockIdx.x + 2] = err;
+    estimator_finish(s_max, s_sum, s_lo, B, n, E.direction, s_theta, out + 3 * blockIdx.x);
 }
 
 // ------------------------------------------------------------------ launchers --

@@ -132,6 +132,48 @@ __device__ __forceinline__ uint4 philox_r0(uint32_t c0, uint32_t c1, uint32_t hi
     return make_uint4(c0, c1, c2, c3);
 }
 
+// The last stage of the FP64 estimator of one job (Appendix A, eq.
+// Jarzynski_theorem; blocked jackknife), given each jackknife block's maximum
+// m_b of -W_i and shifted sum s_b = sum_i e^{-W_i - m_b} (rows lo[b] ..
+// lo[b+1] - 1).  Thread b < B forms the estimate without block b, thread B
+// the full one, both as max-shifted log-sum-exps over the blocks; thread 0
+// then writes out[0] = ln <e^-W>, out[1] = Delta S, out[2] = the jackknife
+// error.  Every thread of the CTA calls it (it holds a barrier).
+__device__ __forceinline__ void estimator_finish(const double* s_max, const double* s_sum,
+                                                 const int* s_lo, int B, int n, int direction,
+                                                 double* s_theta, double* out)
+{
+    const int t = (int)threadIdx.x;
+    if (t == B || (t < B && B >= 2)) {
+        const int skip = t < B ? t : -1;
+        const int count = t < B ? n - (s_lo[t + 1] - s_lo[t]) : n;
+        double M = -INFINITY;
+        for (int b = 0; b < B; ++b) if (b != skip) M = fmax(M, s_max[b]);
+        double tot = 0.0;
+        for (int b = 0; b < B; ++b) if (b != skip) tot += s_sum[b] * exp(s_max[b] - M);
+        s_theta[t] = M + log(tot) - log((double)count);
+    }
+    __syncthreads();
+    if (t != 0) return;
+    const double sign = direction > 0 ? -1.0 : 1.0;
+    const double full = s_theta[B];
+    double err = 0.0;
+    if (B >= 2) {
+        double mean = 0.0;
+        for (int b = 0; b < B; ++b) mean += sign * s_theta[b];
+        mean /= B;
+        double ss = 0.0;
+        for (int b = 0; b < B; ++b) {
+            const double d = sign * s_theta[b] - mean;
+            ss += d * d;
+        }
+        err = sqrt((double)(B - 1) / B * ss);
+    }
+    out[0] = full;
+    out[1] = sign * full;
+    out[2] = err;
+}
+
 __device__ __forceinline__ uint32_t word_of(const uint4& u, int j)
 {
     return j == 0 ? u.x : j == 1 ? u.y : j == 2 ? u.z : u.w;

@@ -27,9 +27,10 @@ constexpr int kMaxTeams = 64;
 // is a compile-time choice so that the shared-memory variant keeps 32-bit
 // shared addressing.  The specialised variants (CW > 0) are capped at 64
 // registers so that two 512-thread CTAs fit on an SM; the generic variant
-// keeps the full register file of one CTA.
+// keeps the full register file of one CTA, and so does the 2D GW = 1 variant,
+// whose one-row pipeline holds the next half-sweep's Philox blocks.
 template <int D, bool FAST, int CW, int CLY, bool WARP, bool HBM>
-__global__ void __launch_bounds__(512, CW > 0 ? 2 : 1)
+__global__ void __launch_bounds__(512, (CW > 1 || (CW == 1 && D == 3)) ? 2 : 1)
 traj_kernel(const Geom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, int n_jobs,
             const LaunchShape sh, uint32_t* __restrict__ gS)
 {
@@ -56,7 +57,13 @@ traj_kernel(const Geom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
     const long long V = (long long)g.nrep * g.Lt * g.Ly * g.L;
     const int8_t* sin = (has && tj.k_begin > 0) ? J.spins_in + local * V : nullptr;
     int dE;
-    if (WARP)
+    // The one-row pipeline is compiled into the 2D GW = 1 variant (L <= 16),
+    // the only lattice whose warp team can hold a thread per word.
+    constexpr bool kRow = D == 2 && CW == 1 && WARP;
+    if (kRow && sh.team_threads == g.NR * g.GW)
+        dE = run_trajectory<D, FAST, CW, CLY, kRow>(g, K, tj, traj, St, s_tab, tid,
+                                                    sh.team_threads, WarpBarrier{}, sin);
+    else if (WARP)
         dE = run_trajectory<D, FAST, CW, CLY>(g, K, tj, traj, St, s_tab, tid, sh.team_threads,
                                               WarpBarrier{}, sin);
     else
@@ -85,6 +92,7 @@ estimator_kernel(const long long* __restrict__ w_int, int n, double scale, int d
 {
     __shared__ double s_max[kMaxJackBlocks], s_sum[kMaxJackBlocks];
     __shared__ int s_lo[kMaxJackBlocks + 1];
+    __shared__ double s_theta[kMaxJackBlocks + 1];
     const int B = n_blocks;
     const int size = n / B;
     if (threadIdx.x <= B) s_lo[threadIdx.x] = threadIdx.x == B ? n : threadIdx.x * size;
@@ -104,32 +112,7 @@ estimator_kernel(const long long* __restrict__ w_int, int n, double scale, int d
         if (lane == 0) { s_max[b] = m; s_sum[b] = acc; }
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    const double sign = direction > 0 ? -1.0 : 1.0;
-    auto lse_without = [&](int skip, int count) {
-        double M = -INFINITY;
-        for (int b = 0; b < B; ++b) if (b != skip) M = fmax(M, s_max[b]);
-        double tot = 0.0;
-        for (int b = 0; b < B; ++b) if (b != skip) tot += s_sum[b] * exp(s_max[b] - M);
-        return M + log(tot) - log((double)count);
-    };
-    const double full = lse_without(-1, n);
-    double err = 0.0;
-    if (B >= 2) {
-        double theta[kMaxJackBlocks];
-        double mean = 0.0;
-        for (int b = 0; b < B; ++b) {
-            theta[b] = sign * lse_without(b, n - (s_lo[b + 1] - s_lo[b]));
-            mean += theta[b];
-        }
-        mean /= B;
-        double ss = 0.0;
-        for (int b = 0; b < B; ++b) ss += (theta[b] - mean) * (theta[b] - mean);
-        err = sqrt((double)(B - 1) / B * ss);
-    }
-    out[0] = full;
-    out[1] = sign * full;
-    out[2] = err;
+    estimator_finish(s_max, s_sum, s_lo, B, n, direction, s_theta, out);
 }
 
 // ------------------------------------------------------------ host launchers --

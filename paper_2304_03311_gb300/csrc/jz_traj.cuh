@@ -156,6 +156,15 @@ struct Traj {
     __device__ __forceinline__ void bulk_item(uint32_t* own_b, const uint32_t* oth, int w, int up,
                                               int p, uint32_t c0, uint32_t sweep, uint32_t c3) const
     {
+        const uint4 ua = philox_r0(c0, sweep, hi1, lo1, c3, K);
+        const uint4 ub = philox_r0(c0 + 1u, sweep, hi1, lo1, c3, K);
+        bulk_update(own_b, oth, w, up, p, ua, ub);
+    }
+
+    // The same update with the word's two Philox blocks (ua, ub) supplied.
+    __device__ __forceinline__ void bulk_update(uint32_t* own_b, const uint32_t* oth, int w, int up,
+                                                int p, const uint4& ua, const uint4& ub) const
+    {
         const uint32_t* o = oth + w;
         const uint32_t own = own_b[w];
         const uint32_t ntm = o[-rowW()];
@@ -164,11 +173,34 @@ struct Traj {
         const uint32_t nx1 = xshift(o, p, nx0);
         uint32_t dsum = (own ^ ntm) + (own ^ ntp) + (own ^ nx0) + (own ^ nx1);
         if (D == 3) dsum += (own ^ o[d_ym]) + (own ^ o[d_yp]);
-        const uint4 ua = philox_r0(c0, sweep, hi1, lo1, c3, K);
-        const uint4 ub = philox_r0(c0 + 1u, sweep, hi1, lo1, c3, K);
         uint32_t flip = accept8<D>(dsum, ua, ub, tab);
         if (!FAST) flip &= vmask;
         own_b[w] = own ^ flip;
+    }
+
+    // Site jl of a cut-row word that switches during the protocol: couplings
+    // beta (1 - lambda) to its own replica (self_w), beta lambda to the next
+    // one (glue_w), tested against step k's table; replaces its flip bit.
+    // record: add its share of the work increment dE_k.
+    __device__ __forceinline__ void switched_site(uint32_t& flip, int jl, uint32_t own,
+                                                  uint32_t self_w, uint32_t glue_w, uint32_t dsum,
+                                                  const uint4& ua, const uint4& ub, int k,
+                                                  const TeamJob& J, int w_self, int w_glue,
+                                                  bool record, int& dE) const
+    {
+        const int sh = 4 * jl;
+        const uint32_t ob = (own >> sh) & 1u;
+        const int as = (int)(ob ^ ((self_w >> sh) & 1u));
+        const int ag = (int)(ob ^ ((glue_w >> sh) & 1u));
+        const int a_cnt = (int)((dsum >> sh) & 0xFu) - as;   // fixed links
+        const int a = (2 * D - 1) - 2 * a_cnt;
+        const int b = 1 - 2 * as;
+        const int cg = 1 - 2 * ag;
+        const int mm = a * J.den + b * w_self + cg * w_glue;
+        const int ti = (((a + 2 * D - 1) >> 1) * 2 + (b > 0)) * 2 + (cg > 0);
+        const bool acc = (mm <= 0) || (word8(ua, ub, jl) < __ldg(J.tcut + k * (8 * D) + ti));
+        flip = (flip & ~(0xFu << sh)) | ((uint32_t)acc << sh);
+        if (record) dE += b - cg;
     }
 
     // Rows t = 0, 1 next to the cut.  lg = columns glued across the cut; k >= 0
@@ -177,6 +209,17 @@ struct Traj {
                                              int r, int p, uint32_t c0, uint32_t sweep,
                                              uint32_t c3, int k, int lg, const TeamJob& J,
                                              int w_self, int w_glue, bool record, int& dE) const
+    {
+        const uint4 ua = philox_r0(c0, sweep, hi1, lo1, c3, K);
+        const uint4 ub = philox_r0(c0 + 1u, sweep, hi1, lo1, c3, K);
+        cut_update(own_b, oth, w, t, r, p, ua, ub, k, lg, J, w_self, w_glue, record, dE);
+    }
+
+    // The same update with the word's two Philox blocks (ua, ub) supplied.
+    __device__ __forceinline__ void cut_update(uint32_t* own_b, const uint32_t* oth, int w, int t,
+                                               int r, int p, const uint4& ua, const uint4& ub,
+                                               int k, int lg, const TeamJob& J, int w_self,
+                                               int w_glue, bool record, int& dE) const
     {
         const int rw = rowW();
         const int repW = g.Lt * rw;
@@ -196,8 +239,6 @@ struct Traj {
         const uint32_t nx1 = xshift(o, p, nx0);
         uint32_t dsum = (own ^ normal) + (own ^ cross) + (own ^ nx0) + (own ^ nx1);
         if (D == 3) dsum += (own ^ o[d_ym]) + (own ^ o[d_yp]);
-        const uint4 ua = philox_r0(c0, sweep, hi1, lo1, c3, K);
-        const uint4 ub = philox_r0(c0 + 1u, sweep, hi1, lo1, c3, K);
         uint32_t flip = accept8<D>(dsum, ua, ub, tab);
         // Switching sites g0 <= x < g1 during the protocol: couplings
         // beta (1 - lambda) to their own replica, beta lambda to the next one.
@@ -205,21 +246,9 @@ struct Traj {
         const int jlo = k >= 0 ? max(((J.g0 - p + 1) >> 1) - 8 * q, 0) : 8;
         const int jhi = min(((J.g1 - p + 1) >> 1) - 8 * q, 8);
 #pragma unroll 1
-        for (int jl = jlo; jl < jhi; ++jl) {
-            const int sh = 4 * jl;
-            const uint32_t ob = (own >> sh) & 1u;
-            const int as = (int)(ob ^ ((self_w >> sh) & 1u));
-            const int ag = (int)(ob ^ ((glue_w >> sh) & 1u));
-            const int a_cnt = (int)((dsum >> sh) & 0xFu) - as;   // fixed links
-            const int a = (2 * D - 1) - 2 * a_cnt;
-            const int b = 1 - 2 * as;
-            const int cg = 1 - 2 * ag;
-            const int mm = a * J.den + b * w_self + cg * w_glue;
-            const int ti = (((a + 2 * D - 1) >> 1) * 2 + (b > 0)) * 2 + (cg > 0);
-            const bool acc = (mm <= 0) || (word8(ua, ub, jl) < __ldg(J.tcut + k * (8 * D) + ti));
-            flip = (flip & ~(0xFu << sh)) | ((uint32_t)acc << sh);
-            if (record) dE += b - cg;
-        }
+        for (int jl = jlo; jl < jhi; ++jl)
+            switched_site(flip, jl, own, self_w, glue_w, dsum, ua, ub, k, J, w_self, w_glue,
+                          record, dE);
         if (!FAST) flip &= vmask;
         own_b[w] = own ^ flip;
     }
@@ -258,6 +287,65 @@ struct Traj {
                 if (t < Lt) bulk_item(own_b, oth, w, t == Lt - 1 ? wrap_up : rw, p, c0, sweep, c3);
             }
         }
+    }
+
+    // Threads that own one row of each colour (a team with a thread per word
+    // of the lattice): the Philox blocks of half-sweep (sweep, c) of that row.
+    // They depend on the sweep index and the colour only, never on spins, so
+    // they can be drawn a half-sweep ahead.
+    __device__ __forceinline__ void row_draw(uint32_t sweep, int c, uint4& ua, uint4& ub) const
+    {
+        const uint32_t c0 = (uint32_t)(((r0 * g.Lt + t0) * Ly() + y) * g.G + 2 * q);
+        const uint32_t c3 = (uint32_t)c | c3base;
+        ua = philox_r0(c0, sweep, hi1, lo1, c3, K);
+        ub = philox_r0(c0 + 1u, sweep, hi1, lo1, c3, K);
+    }
+
+    // The half-sweep of colour c over this thread's one row, blocks supplied.
+    // A warp holds bulk and cut rows side by side, so both kinds share one
+    // instruction stream: a bulk row's neighbour "across the cut" is its t+1
+    // row with an empty glue mask, and only the switched sites of a cut row
+    // (x = l during the protocol) take the per-site loop.
+    __device__ __forceinline__ void row_half_sweep(int c, const uint4& ua, const uint4& ub, int k,
+                                                   int lg, const TeamJob& J, int w_self,
+                                                   int w_glue, bool record, int& dE) const
+    {
+        const int Lt = g.Lt;
+        if (t0 >= Lt) return;   // a thread without sites
+        const int rw = rowW();
+        const int repW = Lt * rw;
+        const int n = g.nrep;
+        uint32_t* own_b = S + c * n * repW;
+        const int w = (r0 * Lt + t0) * rw + y * W() + q;
+        const uint32_t* o = S + (1 - c) * n * repW + w;
+        const int p = (c + y + t0) & 1;
+        const bool cut = t0 < 2;
+        // the ordinary time neighbour (t - 1; t = 2 for the cut row t = 1)
+        const int off_n = t0 == 0 ? (Lt - 1) * rw : (t0 == 1 ? (Lt == 2 ? -rw : rw) : -rw);
+        // the row across the cut (t = 0, 1), else t + 1
+        const int off_x = t0 == 0 ? rw : t0 == 1 ? -rw : (t0 == Lt - 1 ? -(Lt - 1) * rw : rw);
+        // the glued partner across the cut: replica r+1 above it, r-1 below (mod n)
+        const int off_g = !cut ? 0 : t0 == 0 ? (r0 == n - 1 ? -(n - 1) * repW : repW)
+                                            : (r0 == 0 ? (n - 1) * repW : -repW);
+        const uint32_t m = cut ? glue_mask(lg, p) : 0u;
+        const uint32_t own = own_b[w];
+        const uint32_t nrm = o[off_n];
+        const uint32_t self_w = o[off_x];
+        const uint32_t glue_w = o[off_x + off_g];
+        const uint32_t cross = (self_w & ~m) | (glue_w & m);
+        const uint32_t nx0 = o[0];
+        const uint32_t nx1 = xshift(o, p, nx0);
+        uint32_t dsum = (own ^ nrm) + (own ^ cross) + (own ^ nx0) + (own ^ nx1);
+        if (D == 3) dsum += (own ^ o[d_ym]) + (own ^ o[d_yp]);
+        uint32_t flip = accept8<D>(dsum, ua, ub, tab);
+        const int jlo = (cut && k >= 0) ? max(((J.g0 - p + 1) >> 1) - 8 * q, 0) : 8;
+        const int jhi = min(((J.g1 - p + 1) >> 1) - 8 * q, 8);
+#pragma unroll 1
+        for (int jl = jlo; jl < jhi; ++jl)
+            switched_site(flip, jl, own, self_w, glue_w, dsum, ua, ub, k, J, w_self, w_glue,
+                          record, dE);
+        if (!FAST) flip &= vmask;
+        own_b[w] = own ^ flip;
     }
 
     // Loads a stored configuration (int8 +-1, natural order [r][t][y][x]) into
@@ -322,7 +410,12 @@ struct WarpBarrier {
 // (the caller applies the direction's sign and, in protocol 2, the factor L_y
 // that makes W = (beta/N) W_int).
 // sin: the stored state to resume from when J.k_begin > 0 (else unused).
-template <int D, bool FAST, int CW, int CLY, class Bar>
+// ROW: every thread owns one row of each colour (the team has a thread per
+// word); each half-sweep then draws the next one's Philox blocks beside its
+// own update, so the independent chains cover the latency of the
+// shared-memory loads and the barrier that a team this small (one warp per
+// trajectory, few warps per SM) has no other warps to hide.
+template <int D, bool FAST, int CW, int CLY, bool ROW = false, class Bar>
 __device__ __forceinline__ int run_trajectory(const Geom& g, const PhiloxKeys& K, const TeamJob& J,
                                               long long traj, uint32_t* S_team,
                                               const uint32_t* tab, int tid, int nthr, Bar bar,
@@ -331,6 +424,24 @@ __device__ __forceinline__ int run_trajectory(const Geom& g, const PhiloxKeys& K
     const Traj<D, FAST, CW, CLY> tr(g, S_team, tab, K, (uint32_t)traj,
                                     ((uint32_t)(J.dir < 0) << 1) | ((uint32_t)J.l << 2), tid, nthr);
     int dE = 0;
+    // the global sweep index: thermalisation sweeps 0 .. n_therm - 1, then
+    // protocol sweep i of step k is n_therm + k n_sweep + i
+    uint32_t s = J.k_begin > 0 ? (uint32_t)J.n_therm + (uint32_t)J.k_begin * (uint32_t)J.n_sweep
+                               : 0u;
+    uint4 ua, ub;   // ROW: the blocks of the coming half-sweep
+    if constexpr (ROW) tr.row_draw(s, 0, ua, ub);
+    auto half = [&](int c, int kk, int lg, int ws, int wg, bool rec) {
+        if constexpr (ROW) {
+            uint4 na, nb;
+            tr.row_draw(c ? s + 1u : s, c ^ 1, na, nb);
+            tr.row_half_sweep(c, ua, ub, kk, lg, J, ws, wg, rec, dE);
+            ua = na;
+            ub = nb;
+        } else {
+            tr.half_sweep(c, s, kk, lg, J, ws, wg, rec, dE);
+        }
+        bar();
+    };
     if (J.k_begin > 0) {
         if (tid >= 0) tr.import_spins(sin);
         bar();
@@ -340,15 +451,11 @@ __device__ __forceinline__ int run_trajectory(const Geom& g, const PhiloxKeys& K
         // thermalisation at the start geometry: forward lambda = 0 (x < g0
         // glued), reverse lambda = 1 (x < g1 glued)
         const int lg_therm = J.dir > 0 ? J.g0 : J.g1;
-        for (int s = 0; s < J.n_therm; ++s) {
-            tr.half_sweep(0, (uint32_t)s, -1, lg_therm, J, 0, 0, false, dE);
-            bar();
-            tr.half_sweep(1, (uint32_t)s, -1, lg_therm, J, 0, 0, false, dE);
-            bar();
+        for (int i = 0; i < J.n_therm; ++i, ++s) {
+            half(0, -1, lg_therm, 0, 0, false);
+            half(1, -1, lg_therm, 0, 0, false);
         }
     }
-    // the global sweep index: protocol sweep i of step k is n_therm + k n_sweep + i
-    uint32_t s = (uint32_t)J.n_therm + (uint32_t)J.k_begin * (uint32_t)J.n_sweep;
     for (int k = J.k_begin; k < J.k_end; ++k) {
         // protocol 2: only column y = k / den moves; the columns before it sit
         // at the end geometry, the ones after it at the start geometry
@@ -362,10 +469,8 @@ __device__ __forceinline__ int run_trajectory(const Geom& g, const PhiloxKeys& K
             lg = (tr.y < ya) == (J.dir > 0) ? J.g1 : J.g0;
         }
         for (int i = 0; i < J.n_sweep; ++i, ++s) {
-            tr.half_sweep(0, s, kk, lg, J, w_self, w_glue, i == 0, dE);
-            bar();
-            tr.half_sweep(1, s, kk, lg, J, w_self, w_glue, false, dE);
-            bar();
+            half(0, kk, lg, w_self, w_glue, i == 0);
+            half(1, kk, lg, w_self, w_glue, false);
         }
     }
     return dE;
