@@ -255,7 +255,14 @@ def cpu_oracle_rate(w, seconds: float):
     dt = time.perf_counter() - t0
     sample = (f"{n_per_job} trajectories at each of l = {[j.l for j in jobs]} of the same "
               f"workload ({updates:.3e} spin updates, {dt:.1f} s)")
-    return updates / dt, len(jobs) * n_per_job / dt, threads, sample
+    # one core: one trajectory of the first sampled job on one thread
+    j = jobs[0]
+    t1 = time.perf_counter()
+    oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, 1, j.seed,
+               n_therm=j.n_therm, traj0=j.traj0, n_threads=1, update=j.update,
+               protocol=j.protocol, n_replica=j.n_replica, whole=j.whole)
+    single = j.with_(n_traj=1).updates / (time.perf_counter() - t1)
+    return updates / dt, len(jobs) * n_per_job / dt, threads, sample, single
 
 
 # Sources of each timed kernel: a recorded DRAM traffic figure stands only
@@ -539,9 +546,9 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, trate, cores, sample = cpu_oracle_rate(w, args.cpu_seconds / (3 if sw else 1))
+        rate, trate, cores, sample, single = cpu_oracle_rate(w, args.cpu_seconds / (3 if sw else 1))
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-               "trajectories_per_s": trate}
+               "trajectories_per_s": trate, "single_core_value": single}
     if plan is not None:
         jz.jz_plan_free(plan)
     jz.ising_replica_free(ctx)
