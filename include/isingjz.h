@@ -150,6 +150,19 @@ void ising_replica_free(ising_ctx* ctx);
  * ISING_OK, or the first deferred error of queued work. */
 int ising_sync(ising_ctx* ctx);
 
+/* Device time, in milliseconds, of the trajectory kernel launches of the last
+ * run call on this context (jarzynski_run, _ex, _batch, _segment and the
+ * autotuner's trial runs; not the plain baseline, the estimator or plans):
+ * from CUDA events recorded on the context's stream just before the call's
+ * first kernel launch and just after its last one, so the call's table and
+ * result copies are excluded (and, for a batch of several lattice shapes,
+ * the copies between its launches are included).  Waits for that launch to
+ * finish.  *ms is written on success.  Errors: ISING_ERR_ARG when the last
+ * run call launched no kernel (there was none yet, or it returned an error
+ * before its first launch), ISING_ERR_CUDA.  This is measurement support for the section 3
+ * trajectory step; the paper defines no such call. */
+int ising_last_launch_ms(ising_ctx* ctx, float* ms);
+
 /* Runs n_traj trajectories of the forward transformation l -> l+1 with
  * n_therm = 1000 and trajectory indices 0..n_traj-1 (section 3 protocol,
  * Appendix A work).  work_int_out[i] (caller-owned, n_traj int64 entries,

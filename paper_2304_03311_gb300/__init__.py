@@ -88,6 +88,7 @@ def load():
         "ising_replica_init": (ctypes.c_int, [P(vp), ctypes.c_int, ctypes.c_size_t, vp]),
         "ising_replica_free": (None, [vp]),
         "ising_sync": (ctypes.c_int, [vp]),
+        "ising_last_launch_ms": (ctypes.c_int, [vp, P(ctypes.c_float)]),
         "jarzynski_run": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_int, ctypes.c_uint64, vp]),
@@ -170,6 +171,13 @@ def ising_replica_free(ctx) -> None:
 
 def ising_sync(ctx) -> None:
     _check(load().ising_sync(ctx), "ising_sync")
+
+
+def ising_last_launch_ms(ctx) -> float:
+    """Device time (ms) of the last run call's kernel launches, copies excluded."""
+    ms = ctypes.c_float()
+    _check(load().ising_last_launch_ms(ctx, ctypes.byref(ms)), "ising_last_launch_ms")
+    return ms.value
 
 
 def jarzynski_run(ctx, d, L, L_t, beta, l, n_step, n_sweep, n_traj, seed, work_int_out):

@@ -381,6 +381,10 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
                                        n_jobs * sizeof(jz::JobDesc), cudaMemcpyHostToDevice, st))))
         return rc;
     const jz::PhiloxKeys K = key_schedule(p0.seed);
+    if (ctx->k_open) {
+        if ((rc = cuda_err(cudaEventRecord(ctx->ev_k0, st)))) return rc;
+        ctx->k_open = false;
+    }
     if (sw) {
         uint32_t* gS = nullptr;
         if (in_hbm) {
@@ -401,6 +405,8 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
                                            n_jobs, n_cta, sh, st, gS))))
             return rc;
     }
+    if ((rc = cuda_err(cudaEventRecord(ctx->ev_k1, st)))) return rc;
+    ctx->k_timed = true;
     if (!outs_on_device || (n_spin_traj && !spins_on_device)) {
         long long c = 0, so = 0;
         for (int i = 0; i < n_jobs; ++i) {
@@ -429,6 +435,8 @@ int run_jobs(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const* 
              int8_t* const* spins)
 {
     if (!ctx || !jobs || !outs || n_jobs < 1) return ISING_ERR_ARG;
+    ctx->k_open = true;   // a new run call: its first launch opens the timed span
+    ctx->k_timed = false;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
     for (int j = 0; j < n_jobs; ++j) {
         int rc = check_params(&jobs[j]);
@@ -516,6 +524,12 @@ int ising_replica_init(ising_ctx** out, int device, size_t hbm_budget_bytes, voi
         }
         ctx->own_stream = true;
     }
+    if (cudaEventCreate(&ctx->ev_k0) != cudaSuccess || cudaEventCreate(&ctx->ev_k1) != cudaSuccess) {
+        if (ctx->ev_k0) cudaEventDestroy(ctx->ev_k0);
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return ISING_ERR_CUDA;
+    }
     *out = ctx;
     return ISING_OK;
 }
@@ -529,7 +543,18 @@ void ising_replica_free(ising_ctx* ctx)
                       &ctx->est_out, &ctx->lattice})
         if (b->ptr) cudaFree(b->ptr);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    cudaEventDestroy(ctx->ev_k0);
+    cudaEventDestroy(ctx->ev_k1);
     delete ctx;
+}
+
+int ising_last_launch_ms(ising_ctx* ctx, float* ms)
+{
+    if (!ctx || !ms || !ctx->k_timed) return ISING_ERR_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
+    int rc = cuda_err(cudaEventSynchronize(ctx->ev_k1));
+    if (rc) return rc;
+    return cuda_err(cudaEventElapsedTime(ms, ctx->ev_k0, ctx->ev_k1));
 }
 
 int ising_sync(ising_ctx* ctx)
@@ -650,6 +675,8 @@ int jarzynski_run_segment(ising_ctx* ctx, const jz_params* p, int k_begin, int k
                           int64_t* work_io, int8_t* spins_io)
 {
     if (!ctx || !p || !work_io || !spins_io) return ISING_ERR_ARG;
+    ctx->k_open = true;
+    ctx->k_timed = false;
     int rc = check_params(p);
     if (rc) return rc;
     if (k_begin < 0 || k_end <= k_begin || k_end > p->n_step) return ISING_ERR_ARG;

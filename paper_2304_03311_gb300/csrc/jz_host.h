@@ -56,6 +56,11 @@ struct ising_ctx {
     std::vector<uint32_t> h_tcut;
     std::vector<jz::JobDesc> h_jobs;
     std::map<std::tuple<int, int, int>, int> threads;   // per-shape CTA size (tuned)
+    // device time of the last run call's kernel launches (ising_last_launch_ms):
+    // ev_k0 before its first launch, ev_k1 after its last one
+    cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;
+    bool k_open = false;    // the next launch is the call's first
+    bool k_timed = false;   // a run call has recorded both events
 };
 
 namespace jzh {

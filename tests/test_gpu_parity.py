@@ -143,6 +143,32 @@ def test_cta_size_does_not_change_results(job):
         jz.ising_replica_free(c)
 
 
+def test_last_launch_time_covers_the_kernel_only():
+    """ising_last_launch_ms: an error before any run call and after a call
+    rejected by its argument checks; after a run, a positive device time no
+    longer than the call's wall time."""
+    import time
+    c = jz.ising_replica_init(0, 0, None)
+    try:
+        with pytest.raises(jz.IsingError):
+            jz.ising_last_launch_ms(c)
+        job = SMALL[0]
+        gpu_run(c, job, spins=False)   # warm-up: module load, first allocations
+        t0 = time.perf_counter()
+        gpu_run(c, job, spins=False)
+        wall_ms = (time.perf_counter() - t0) * 1e3
+        ms = jz.ising_last_launch_ms(c)
+        assert 0.0 < ms <= wall_ms
+        bad = jz.make_params(2, 15, 16, BC2, 4, 10, 1, 8, 0)   # odd L
+        w = torch.empty(8, dtype=torch.int64, device="cuda")
+        with pytest.raises(jz.IsingError):
+            jz.jarzynski_run_ex(c, bad, w)
+        with pytest.raises(jz.IsingError):
+            jz.ising_last_launch_ms(c)
+    finally:
+        jz.ising_replica_free(c)
+
+
 def test_host_and_device_outputs_agree(ctx):
     job = SMALL[1]
     Wd, Sd = gpu_run(ctx, job, on_device=True)
