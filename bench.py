@@ -477,9 +477,12 @@ def run_ours(args):
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
 
     d = w.jobs[0].d
-    updates_per_launch = w.updates   # one launch per rank per step
-    n_alg = (N_ALG_SW if sw else N_ALG)[d]
-    achieved = n_alg * updates_per_launch / (kernel_ms / 1e3) / 1e12
+    # one launch per rank per step; each job's updates at its own dimension's cost
+    table = N_ALG_SW if sw else N_ALG
+    ops_per_launch = sum(table[j.d] * j.updates for j in w.jobs)
+    n_alg = table[d] if all(j.d == d for j in w.jobs) else {
+        f"{dd}D": table[dd] for dd in sorted({j.d for j in w.jobs})}
+    achieved = ops_per_launch / (kernel_ms / 1e3) / 1e12
     peak = SM_COUNT * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     kbase = "sw_kernel" if sw else "persistent_kernel" if plan is not None else "traj_kernel"
     kname = (f"sw_kernel<{d}>" if sw else
