@@ -274,6 +274,17 @@ KERNEL_SOURCES = {
 }
 
 
+def algorithmic_ops(jobs, sw: bool):
+    """Integer operations one launch of these jobs is charged for: each job's
+    spin updates at its own dimension's per-update cost.  Returns the total and
+    the per-update figure (one number, or one per dimension for mixed jobs)."""
+    table = N_ALG_SW if sw else N_ALG
+    total = sum(table[j.d] * j.updates for j in jobs)
+    dims = sorted({j.d for j in jobs})
+    per = table[dims[0]] if len(dims) == 1 else {f"{dd}D": table[dd] for dd in dims}
+    return total, per
+
+
 def kernel_source_hash(kernel: str) -> str:
     """sha256 over the sources of one kernel, in the order listed."""
     csrc = os.path.join(ROOT, "paper_2304_03311_gb300", "csrc")
@@ -477,11 +488,7 @@ def run_ours(args):
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
 
     d = w.jobs[0].d
-    # one launch per rank per step; each job's updates at its own dimension's cost
-    table = N_ALG_SW if sw else N_ALG
-    ops_per_launch = sum(table[j.d] * j.updates for j in w.jobs)
-    n_alg = table[d] if all(j.d == d for j in w.jobs) else {
-        f"{dd}D": table[dd] for dd in sorted({j.d for j in w.jobs})}
+    ops_per_launch, n_alg = algorithmic_ops(w.jobs, sw)   # one launch per rank per step
     achieved = ops_per_launch / (kernel_ms / 1e3) / 1e12
     peak = SM_COUNT * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     kbase = "sw_kernel" if sw else "persistent_kernel" if plan is not None else "traj_kernel"

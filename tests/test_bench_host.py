@@ -1,0 +1,62 @@
+"""Host logic of bench.py (no GPU): the workload sizes of the benchmark
+configurations, the roofline's operation count, and the rule that a recorded
+DRAM traffic figure stands only while its kernel's sources are unchanged."""
+import json
+import os
+
+import pytest
+
+import bench
+from paper_2304_03311_gb300 import workloads as wl
+
+
+@pytest.mark.parametrize("config,jobs,updates", [
+    (1, 1, 1000 * 2 * 16 * 16 * (1000 + 200 * 1)),
+    (2, 31, 31 * 16384 * 2 * 64 * 64 * (1000 + 1000 * 2)),
+    (3, 8, 8 * 4096 * 2 * 16 * 16 * 16 * (1000 + 2000 * 1)),
+])
+def test_workload_sizes(config, jobs, updates):
+    """Spin updates per launch: n_traj x V x (n_therm + N n_sweep) summed over
+    the transformations (V counts both replicas)."""
+    w = wl.CONFIGS[config]()
+    assert len(w.jobs) == jobs
+    assert w.updates == updates
+
+
+def test_uneven_batch_is_charged_per_dimension():
+    w = wl.CONFIGS[4]()
+    total, per = bench.algorithmic_ops(w.jobs, sw=False)
+    two = sum(j.updates for j in w.jobs if j.d == 2)
+    three = sum(j.updates for j in w.jobs if j.d == 3)
+    assert two > 0 and three > 0 and two + three == w.updates
+    assert total == bench.N_ALG[2] * two + bench.N_ALG[3] * three
+    assert per == {"2D": bench.N_ALG[2], "3D": bench.N_ALG[3]}
+
+
+def test_single_dimension_reports_one_figure():
+    w = wl.CONFIGS[3]()
+    total, per = bench.algorithmic_ops(w.jobs, sw=False)
+    assert per == bench.N_ALG[3] and total == bench.N_ALG[3] * w.updates
+    total, per = bench.algorithmic_ops(w.jobs, sw=True)
+    assert per == bench.N_ALG_SW[3] and total == bench.N_ALG_SW[3] * w.updates
+
+
+def test_recorded_traffic_stands_only_for_unchanged_sources(tmp_path, monkeypatch):
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "dram_traffic.json")))
+    for workload, r in rec["launches"].items():
+        kernel = next(k for k, srcs in bench.KERNEL_SOURCES.items()
+                      if list(srcs) == r["sources"] and r["kernel"].startswith(k))
+        if r["source_sha256"] == bench.kernel_source_hash(kernel):
+            assert bench.traffic_from_profile(kernel, workload) == r["dram_bytes_per_launch"]
+    # a record whose hash does not match the sources is not reported
+    fake_root = tmp_path
+    (fake_root / "profiles").mkdir()
+    bad = {"launches": {"w": {"kernel": "traj_kernel", "dram_bytes_per_launch": 1,
+                              "sources": list(bench.KERNEL_SOURCES["traj_kernel"]),
+                              "source_sha256": "0" * 64}}}
+    (fake_root / "profiles" / "dram_traffic.json").write_text(json.dumps(bad))
+    real_hash = bench.kernel_source_hash("traj_kernel")
+    monkeypatch.setattr(bench, "ROOT", str(fake_root))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda k: real_hash)
+    assert bench.traffic_from_profile("traj_kernel", "w") is None
+    assert bench.traffic_from_profile("traj_kernel", "other") is None
