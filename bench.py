@@ -562,7 +562,9 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, trate, cores, sample, single = cpu_oracle_rate(w, args.cpu_seconds / (3 if sw else 1))
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-               "trajectories_per_s": trate, "single_core_value": single}
+               "trajectories_per_s": trate, "single_core_value": single,
+               # the whole workload on these cores, extrapolated at the sampled rate
+               "full_workload_s_estimate": w.updates / rate if rate > 0 else None}
     if plan is not None:
         jz.jz_plan_free(plan)
     jz.ising_replica_free(ctx)
