@@ -84,9 +84,11 @@ typedef struct ising_ctx ising_ctx;
  *                 (3D) bytes for the V = n L_t L^(d-1) sites, in shared memory
  *                 up to 227 KiB (V up to about 50,000), beyond that in an HBM
  *                 slice per CTA.
- *                 Served by jarzynski_run_ex, jarzynski_run_batch and the
- *                 server (jz_submit); the other entry points return
- *                 ISING_ERR_UNSUPPORTED for it.
+ *                 Served by jarzynski_run_ex, jarzynski_run_batch,
+ *                 jarzynski_run_segment, jarzynski_run_noalloc, the
+ *                 persistent plans and the server (jz_submit);
+ *                 jarzynski_run_plain and ising_autotune's timing do not
+ *                 serve it (ISING_ERR_UNSUPPORTED, resp. the fixed CTA size).
  *              Other values: ISING_ERR_ARG.
  *   beta       coupling, 0 <= beta <= 4
  *   l          width of region A before the move, 0 <= l <= L-1
@@ -310,27 +312,31 @@ int jarzynski_run_plain(ising_ctx* ctx, const jz_params* p, int64_t* work_int_ou
  * not stall in cudaMalloc / cudaFree (both can synchronise the device).
  * This call makes no cudaMalloc, cudaFree or other allocating call.  Its
  * scratch (one job descriptor and the N x 8d switched-site thresholds, or
- * N x 2 bond thresholds for Swendsen-Wang) lives in a single file-scope device
- * array of 1 MiB, which every GPU that loads the library keeps until the
- * process exits.  Both updates are served; lattices beyond one CTA's shared
- * memory (which jarzynski_run_ex runs from an HBM slice) are not.
+ * N x 2 bond thresholds for Swendsen-Wang) lives in a single file-scope
+ * device array of 1 MiB, which every GPU that loads the library keeps until
+ * the process exits.  The descriptor and thresholds reach that array as the
+ * arguments of small staging kernels enqueued on cuda_stream (about 31 KB per
+ * launch), so the call reads no host memory after it returns.  Both updates
+ * are served; lattices beyond one CTA's shared memory (which
+ * jarzynski_run_ex runs from an HBM slice) are not.
  *   p             the transformation; final spins are not returned
  *   work_int_out  caller-owned DEVICE memory, p->n_traj int64 entries
  *   cuda_stream   cudaStream_t to enqueue on (NULL = the legacy default stream)
  * Returns once the work is enqueued: synchronise the stream before reading
  * work_int_out.  Results are bit-identical to jarzynski_run_ex.
  * Limit: 262080 threshold words, p->n_step * 8 * p->d for Metropolis (N <=
- * 16380 in 2D, N <= 10920 in 3D) and p->n_step * 2 for Swendsen-Wang;
- * larger protocols return ISING_ERR_SCRATCH_LIMIT, lattices beyond shared
- * memory ISING_ERR_UNSUPPORTED, host output memory ISING_ERR_ARG, other
- * errors as jarzynski_run_ex.
- * The first call on a device (the calling thread's current device) looks up
- * the array's device address once; make that first call before any stream
- * capture.  All calls share the one array and leave their contents in it;
- * nothing there needs to start at zero because each call rewrites everything
- * it reads.  Calls whose GPU work can overlap (different streams with no
- * ordering between them) race on the array: issue them on one stream or
- * synchronise in between. */
+ * 16380 in 2D, N <= 10920 in 3D) and p->n_step * 2 for Swendsen-Wang (N <=
+ * 131040); larger protocols return ISING_ERR_SCRATCH_LIMIT, lattices beyond
+ * shared memory ISING_ERR_UNSUPPORTED, host output memory ISING_ERR_ARG,
+ * other errors as jarzynski_run_ex.
+ * Every call looks up the array's device address on the calling thread's
+ * current device (cudaGetSymbolAddress, which loads the library's device code
+ * on that device the first time); make the first call on a device before any
+ * stream capture.  All calls share the one array and leave their contents in
+ * it; nothing there needs to start at zero because each call rewrites
+ * everything it reads before its kernels read it.  Calls whose GPU work can
+ * overlap (different streams with no ordering between them) race on the
+ * array: issue them on one stream or synchronise in between. */
 int jarzynski_run_noalloc(const jz_params* p, int64_t* work_int_out, void* cuda_stream);
 
 /* FP64 estimator on the device (Appendix A, eq. Jarzynski_theorem; section 2):
@@ -375,6 +381,13 @@ int ising_autotune(ising_ctx* ctx, const jz_params* p, int* threads);
  * the legacy default stream and synchronises the device.
  * Errors: ISING_ERR_ARG (kind or rate), ISING_ERR_CUDA. */
 int ising_probe(int device, int kind, double* rate);
+
+/* Build check; the paper has no counterpart.  Writes the compute capability
+ * the library's device code was compiled for, as major * 10 + minor
+ * (cudaFuncGetAttributes' binaryVersion of one of its kernels: 103 for the
+ * sm_103a build), on `device`.  Errors: ISING_ERR_ARG, ISING_ERR_CUDA (no such
+ * device, or no code in the library loads on it). */
+int ising_binary_version(int device, int* version);
 
 /* Human-readable text for an error code (static storage). */
 const char* ising_strerror(int code);

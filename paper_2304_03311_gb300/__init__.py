@@ -22,7 +22,7 @@ __all__ = [
     "IsingError", "JzParams", "lib_path", "load", "ising_replica_init", "ising_replica_free",
     "ising_sync", "jarzynski_run", "jarzynski_run_ex", "jarzynski_run_batch", "jarzynski_run_plain",
     "estimator_reduce", "ising_strerror", "jz_params_default", "ising_probe",
-    "jarzynski_run_noalloc",
+    "jarzynski_run_noalloc", "ising_binary_version",
 ]
 
 ISING_OK = 0
@@ -103,6 +103,7 @@ def load():
                                             P(ctypes.c_double), P(ctypes.c_double)]),
         "ising_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "ising_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]),
+        "ising_binary_version": (ctypes.c_int, [ctypes.c_int, P(ctypes.c_int)]),
         "ising_set_threads": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_int]),
         "ising_autotune": (ctypes.c_int, [vp, P(JzParams), P(ctypes.c_int)]),
@@ -250,6 +251,13 @@ def ising_probe(device: int, kind: int) -> float:
     r = ctypes.c_double()
     _check(load().ising_probe(int(device), int(kind), ctypes.byref(r)), "ising_probe")
     return r.value
+
+
+def ising_binary_version(device: int = 0) -> int:
+    """Compute capability the device code was built for (103 = sm_103a)."""
+    v = ctypes.c_int()
+    _check(load().ising_binary_version(int(device), ctypes.byref(v)), "ising_binary_version")
+    return v.value
 
 
 def ising_set_threads(ctx, d: int, L: int, L_t: int, threads: int) -> None:

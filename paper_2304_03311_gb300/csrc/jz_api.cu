@@ -142,7 +142,7 @@ jz::PhiloxKeys key_schedule(uint64_t seed)
 // fixed-link sum a' (odd, |a'| <= 2D-1) and the self / glue bond products b, c
 // (m = a' den + b w_self + c w_glue, x = (2 beta m) / den, den = N in protocol 1
 // and N / L_y in protocol 2).
-void build_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcut, size_t off)
+void build_tables_into(const jz_params& p, uint32_t tb[4], uint32_t* tcut)
 {
     const int D = p.d;
     for (int a = 0; a < 4; ++a) {
@@ -160,10 +160,15 @@ void build_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcu
                     const long long m = a * N + (ib ? ws : -ws) + (ic ? wg : -wg);
                     uint32_t T = 0xFFFFFFFFu;
                     if (m > 0) T = threshold((2.0 * p.beta * (double)m) / (double)N);
-                    tcut[off + (size_t)k * per + (ia * 2 + ib) * 2 + ic] = T;
+                    tcut[(size_t)k * per + (ia * 2 + ib) * 2 + ic] = T;
                 }
         }
     }
+}
+
+void build_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcut, size_t off)
+{
+    build_tables_into(p, tb, tcut.data() + off);
 }
 
 // Couplings of the switching column at protocol step k, in units of 1/den:
@@ -192,17 +197,22 @@ uint32_t bond_threshold(double x)
 // Swendsen-Wang tables of one job: tb[0] the full link (x = 2 beta); per step
 // k the switching column's self and glued links at lambda_{k+1}:
 // x = (2 beta w) / den with w = w_self, w_glue.
-void build_bond_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcut,
-                       size_t off)
+void build_bond_tables_into(const jz_params& p, uint32_t tb[4], uint32_t* tcut)
 {
     tb[0] = bond_threshold(2.0 * p.beta);
     tb[1] = tb[2] = tb[3] = 0;
     for (long long k = 0; k < p.n_step; ++k) {
         long long den, ws, wg;
         step_weights(p, k, &den, &ws, &wg);
-        tcut[off + 2 * k] = bond_threshold((2.0 * p.beta * (double)ws) / (double)den);
-        tcut[off + 2 * k + 1] = bond_threshold((2.0 * p.beta * (double)wg) / (double)den);
+        tcut[2 * k] = bond_threshold((2.0 * p.beta * (double)ws) / (double)den);
+        tcut[2 * k + 1] = bond_threshold((2.0 * p.beta * (double)wg) / (double)den);
     }
+}
+
+void build_bond_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcut,
+                       size_t off)
+{
+    build_bond_tables_into(p, tb, tcut.data() + off);
 }
 
 // Whether a Swendsen-Wang trajectory of lattice g fits one CTA's shared memory.
@@ -823,8 +833,16 @@ constexpr size_t kNoAllocScratchBytes = (size_t)1 << 20;   // 1 MiB per device
 constexpr size_t kNoAllocJobBytes = 256;                   // descriptor slot
 constexpr size_t kNoAllocMaxThresholds =
     (kNoAllocScratchBytes - kNoAllocJobBytes) / sizeof(uint32_t);   // 262080 words
-constexpr int kNoAllocMaxDevices = 64;
+constexpr size_t kNoAllocWords = kNoAllocScratchBytes / sizeof(uint32_t);
 static_assert(sizeof(jz::JobDesc) <= kNoAllocJobBytes, "descriptor slot too small");
+
+// The scratch contents travel to the device as kernel arguments, in chunks of
+// kStageWords words (31.7 KB of parameters per launch), so the call reads no
+// host memory after it returns and needs no pinned staging buffer.
+constexpr int kStageWords = 7936;
+struct StageChunk {
+    uint32_t w[kStageWords];
+};
 }  // namespace
 
 // Held by every GPU that loads the library, until exit.  Host code sees only a
@@ -832,30 +850,52 @@ static_assert(sizeof(jz::JobDesc) <= kNoAllocJobBytes, "descriptor slot too smal
 // cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-namespace {
-std::mutex g_noalloc_mutex;                         // guards the two below
-void* g_noalloc_dev_addr[kNoAllocMaxDevices] = {};  // per-device address of the array
-// host staging of the thresholds, sized once at load so calls never allocate
-std::vector<uint32_t> g_noalloc_host_tcut(kNoAllocMaxThresholds);
-
-// Device address of the scratch array on `device` (current), looked up on the
-// first call for that device.
-int noalloc_scratch_address(int device, void** out)
+// Copies n words of the argument chunk to dst (one launch per chunk).
+__global__ void __launch_bounds__(256) noalloc_stage_kernel(uint32_t* __restrict__ dst, int n,
+                                                            const StageChunk c)
 {
-    if (device < 0 || device >= kNoAllocMaxDevices) return ISING_ERR_UNSUPPORTED;
-    if (!g_noalloc_dev_addr[device]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return ISING_ERR_CUDA;
-        }
-        g_noalloc_dev_addr[device] = p;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        dst[i] = c.w[i];
+}
+
+namespace {
+std::mutex g_noalloc_mutex;   // guards the host image below
+// host image of the scratch (descriptor slot, then the thresholds), static so
+// that calls never allocate
+uint32_t g_noalloc_host[kNoAllocWords];
+StageChunk g_noalloc_chunk;
+
+// Device address of the scratch array on the current device.  Looked up on
+// every call: after a device reset the module reloads at a new address.
+int noalloc_scratch_address(void** out)
+{
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return ISING_ERR_CUDA;
     }
-    *out = g_noalloc_dev_addr[device];
+    *out = p;
     return ISING_OK;
 }
 }  // namespace
+
+extern "C" int ising_binary_version(int device, int* version)
+{
+    if (!version) return ISING_ERR_ARG;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess) {
+        cudaGetLastError();
+        return ISING_ERR_CUDA;
+    }
+    if (device < 0 || device >= n) return ISING_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return ISING_ERR_CUDA;
+    cudaFuncAttributes a;
+    const int rc = cuda_err(cudaFuncGetAttributes(&a, noalloc_stage_kernel));
+    if (rc) return rc;
+    *version = a.binaryVersion;
+    return ISING_OK;
+}
 
 extern "C" int jarzynski_run_noalloc(const jz_params* p, int64_t* work_int_out, void* cuda_stream)
 {
@@ -868,16 +908,12 @@ extern "C" int jarzynski_run_noalloc(const jz_params* p, int64_t* work_int_out, 
     const jz::Geom g = make_geom(p->d, p->L, p->L_t, nrep_of(*p));
     if (sw ? !sw_fits(g) : !shape_fits(g)) return ISING_ERR_UNSUPPORTED;
     if (!is_device_ptr(work_int_out)) return ISING_ERR_ARG;
-    int device = 0;
-    if (cudaGetDevice(&device) != cudaSuccess) {
-        cudaGetLastError();
-        return ISING_ERR_CUDA;
-    }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
     void* base = nullptr;
-    if ((rc = noalloc_scratch_address(device, &base))) return rc;
-    uint32_t* d_tcut = (uint32_t*)((unsigned char*)base + kNoAllocJobBytes);
+    if ((rc = noalloc_scratch_address(&base))) return rc;
+    uint32_t* d_words = (uint32_t*)base;
+    uint32_t* d_tcut = d_words + kNoAllocJobBytes / sizeof(uint32_t);
 
     jz::JobDesc J{};
     J.l = p->l;
@@ -892,18 +928,24 @@ extern "C" int jarzynski_run_noalloc(const jz_params* p, int64_t* work_int_out, 
     J.n_traj = p->n_traj;
     J.traj0 = p->traj0;
     J.cta0 = 0;
-    if (sw) build_bond_tables(*p, J.tb, g_noalloc_host_tcut, 0);
-    else build_tables(*p, J.tb, g_noalloc_host_tcut, 0);
+    // the thresholds go to the host image behind the descriptor slot
+    uint32_t* h_tcut = g_noalloc_host + kNoAllocJobBytes / sizeof(uint32_t);
+    if (sw) build_bond_tables_into(*p, J.tb, h_tcut);
+    else build_tables_into(*p, J.tb, h_tcut);
     J.tcut = d_tcut;
     J.w_out = (long long*)work_int_out;
     J.spins_out = nullptr;
-    // pageable sources: each copy returns once its bytes are staged, so the
-    // host buffers may be reused as soon as the call returns
-    if ((rc = cuda_err(cudaMemcpyAsync(d_tcut, g_noalloc_host_tcut.data(),
-                                       n_tcut * sizeof(uint32_t), cudaMemcpyHostToDevice, st))))
-        return rc;
-    if ((rc = cuda_err(cudaMemcpyAsync(base, &J, sizeof J, cudaMemcpyHostToDevice, st))))
-        return rc;
+    std::memset(g_noalloc_host, 0, kNoAllocJobBytes);
+    std::memcpy(g_noalloc_host, &J, sizeof J);
+    // stage descriptor + thresholds, one launch per chunk of kernel arguments
+    const size_t total = kNoAllocJobBytes / sizeof(uint32_t) + n_tcut;
+    for (size_t off = 0; off < total; off += kStageWords) {
+        const int cnt = (int)std::min<size_t>(kStageWords, total - off);
+        std::memcpy(g_noalloc_chunk.w, g_noalloc_host + off, (size_t)cnt * sizeof(uint32_t));
+        noalloc_stage_kernel<<<(cnt + 255) / 256, 256, 0, st>>>(d_words + off, cnt,
+                                                               g_noalloc_chunk);
+        if ((rc = cuda_err(cudaGetLastError()))) return rc;
+    }
     const jz::PhiloxKeys K = key_schedule(p->seed);
     if (sw) return cuda_err(jz::launch_sw(p->d, g, K, (const jz::JobDesc*)base, 1, p->n_traj, st));
     const jz::LaunchShape sh = shape_for(g, 0);

@@ -73,6 +73,9 @@ jz::Geom make_geom(int d, int L, int Lt, int nrep);
 uint32_t threshold(double x);
 jz::PhiloxKeys key_schedule(uint64_t seed);
 void build_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcut, size_t off);
+// The same tables written to tcut[0 .. n_step * 8d) (bond tables: n_step * 2).
+void build_tables_into(const jz_params& p, uint32_t tb[4], uint32_t* tcut);
+void build_bond_tables_into(const jz_params& p, uint32_t tb[4], uint32_t* tcut);
 uint32_t bond_threshold(double x);
 void step_weights(const jz_params& p, long long k, long long* den, long long* w_self,
                   long long* w_glue);

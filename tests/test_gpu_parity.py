@@ -332,3 +332,8 @@ def test_large_narrow_lattice_runs_as_cta_team(ctx):
             np.testing.assert_array_equal(Sg, So)
     finally:
         jz.ising_replica_free(c)
+
+
+def test_device_code_was_built_for_sm103a():
+    jzbuild.build()
+    assert jz.ising_binary_version(0) == 103
