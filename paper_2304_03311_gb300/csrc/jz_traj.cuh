@@ -203,47 +203,44 @@ struct Traj {
         if (record) dE += b - cg;
     }
 
-    // Rows t = 0, 1 next to the cut.  lg = columns glued across the cut; k >= 0
-    // is the protocol step (the switched column then uses the step's table).
-    __device__ __forceinline__ void cut_item(uint32_t* own_b, const uint32_t* oth, int w, int t,
-                                             int r, int p, uint32_t c0, uint32_t sweep,
-                                             uint32_t c3, int k, int lg, const TeamJob& J,
-                                             int w_self, int w_glue, bool record, int& dE) const
-    {
-        const uint4 ua = philox_r0(c0, sweep, hi1, lo1, c3, K);
-        const uint4 ub = philox_r0(c0 + 1u, sweep, hi1, lo1, c3, K);
-        cut_update(own_b, oth, w, t, r, p, ua, ub, k, lg, J, w_self, w_glue, record, dE);
-    }
-
-    // The same update with the word's two Philox blocks (ua, ub) supplied.
-    __device__ __forceinline__ void cut_update(uint32_t* own_b, const uint32_t* oth, int w, int t,
+    // Row t of replica r (word w, row parity p), a row next to the cut (t = 0,
+    // 1) or a bulk row, in one instruction stream: a bulk row's neighbour
+    // "across" is its t+1 row with an empty glue mask, and only the switched
+    // sites of a cut row (k >= 0: the protocol step, whose table they use)
+    // take the per-site loop.  lg = columns glued across the cut.
+    __device__ __forceinline__ void row_update(uint32_t* own_b, const uint32_t* oth, int w, int t,
                                                int r, int p, const uint4& ua, const uint4& ub,
                                                int k, int lg, const TeamJob& J, int w_self,
                                                int w_glue, bool record, int& dE) const
     {
+        const int Lt = g.Lt;
         const int rw = rowW();
-        const int repW = g.Lt * rw;
+        const int repW = Lt * rw;
+        const int n = g.nrep;
+        const bool cut = t < 2;
+        // the ordinary time neighbour (t - 1; t = 2 for the cut row t = 1)
+        const int off_n = t == 0 ? (Lt - 1) * rw : (t == 1 ? (Lt == 2 ? -rw : rw) : -rw);
+        // the row across the cut (t = 0, 1), else t + 1
+        const int off_x = t == 0 ? rw : t == 1 ? -rw : (t == Lt - 1 ? -(Lt - 1) * rw : rw);
+        // the glued partner across the cut: replica r+1 above it, r-1 below (mod n)
+        const int off_g = !cut ? 0 : t == 0 ? (r == n - 1 ? -(n - 1) * repW : repW)
+                                           : (r == 0 ? (n - 1) * repW : -repW);
+        const uint32_t m = cut ? glue_mask(lg, p) : 0u;
         const uint32_t* o = oth + w;
         const uint32_t own = own_b[w];
-        const int cross_off = t == 0 ? rw : -rw;                   // self row across the cut
-        const uint32_t self_w = o[cross_off];
-        // the glued partner: replica r+1 above the cut, r-1 below it (mod n)
-        const int n = g.nrep;
-        const int glue_off = t == 0 ? (r == n - 1 ? -(n - 1) * repW : repW)
-                                    : (r == 0 ? (n - 1) * repW : -repW);
-        const uint32_t glue_w = o[cross_off + glue_off];
-        const uint32_t normal = o[t == 0 ? (g.Lt - 1) * rw : (g.Lt == 2 ? -rw : rw)];
-        const uint32_t m = glue_mask(lg, p);
+        const uint32_t nrm = o[off_n];
+        const uint32_t self_w = o[off_x];
+        const uint32_t glue_w = o[off_x + off_g];
         const uint32_t cross = (self_w & ~m) | (glue_w & m);
         const uint32_t nx0 = o[0];
         const uint32_t nx1 = xshift(o, p, nx0);
-        uint32_t dsum = (own ^ normal) + (own ^ cross) + (own ^ nx0) + (own ^ nx1);
+        uint32_t dsum = (own ^ nrm) + (own ^ cross) + (own ^ nx0) + (own ^ nx1);
         if (D == 3) dsum += (own ^ o[d_ym]) + (own ^ o[d_yp]);
         uint32_t flip = accept8<D>(dsum, ua, ub, tab);
         // Switching sites g0 <= x < g1 during the protocol: couplings
         // beta (1 - lambda) to their own replica, beta lambda to the next one.
         // Site j of the word has x = 2 (8q + j) + p.
-        const int jlo = k >= 0 ? max(((J.g0 - p + 1) >> 1) - 8 * q, 0) : 8;
+        const int jlo = (cut && k >= 0) ? max(((J.g0 - p + 1) >> 1) - 8 * q, 0) : 8;
         const int jhi = min(((J.g1 - p + 1) >> 1) - 8 * q, 8);
 #pragma unroll 1
         for (int jl = jlo; jl < jhi; ++jl)
@@ -267,14 +264,24 @@ struct Traj {
         const uint32_t cstride = (uint32_t)(TS * Ly() * g.G);   // Philox blocks per TS slices
         const int pc = (c + y) & 1;
         const int wrap_up = -(Lt - 1) * rw;
+        if (t0 >= Lt) return;   // a thread without sites
 #pragma unroll 1
         for (int r = r0; r < g.nrep; r += RS) {
             int t = t0;
             int w = (r * Lt + t0) * rw + y * W() + q;
             uint32_t c0 = (uint32_t)(((r * Lt + t0) * Ly() + y) * g.G + 2 * q);
-            for (; t < 2 && t < Lt; t += TS, w += stride, c0 += cstride)
-                cut_item(own_b, oth, w, t, r, (pc ^ t) & 1, c0, sweep, c3, k, lg, J, w_self,
-                         w_glue, record, dE);
+            // The thread's first row, cut (t0 < 2) or bulk, in one stream for
+            // the whole team; with TS = 1 the team's second row (t = 1) is a
+            // cut row too.  The rest are bulk rows.
+            do {
+                const uint4 ua = philox_r0(c0, sweep, hi1, lo1, c3, K);
+                const uint4 ub = philox_r0(c0 + 1u, sweep, hi1, lo1, c3, K);
+                row_update(own_b, oth, w, t, r, (pc ^ t) & 1, ua, ub, k, lg, J, w_self, w_glue,
+                           record, dE);
+                t += TS;
+                w += stride;
+                c0 += cstride;
+            } while (t < 2 && t < Lt);
             if (TS & 1) {
                 for (; t < Lt; t += TS, w += stride, c0 += cstride)
                     bulk_item(own_b, oth, w, t == Lt - 1 ? wrap_up : rw, (pc ^ t) & 1, c0, sweep,
@@ -302,10 +309,6 @@ struct Traj {
     }
 
     // The half-sweep of colour c over this thread's one row, blocks supplied.
-    // A warp holds bulk and cut rows side by side, so both kinds share one
-    // instruction stream: a bulk row's neighbour "across the cut" is its t+1
-    // row with an empty glue mask, and only the switched sites of a cut row
-    // (x = l during the protocol) take the per-site loop.
     __device__ __forceinline__ void row_half_sweep(int c, const uint4& ua, const uint4& ub, int k,
                                                    int lg, const TeamJob& J, int w_self,
                                                    int w_glue, bool record, int& dE) const
@@ -315,37 +318,9 @@ struct Traj {
         const int rw = rowW();
         const int repW = Lt * rw;
         const int n = g.nrep;
-        uint32_t* own_b = S + c * n * repW;
         const int w = (r0 * Lt + t0) * rw + y * W() + q;
-        const uint32_t* o = S + (1 - c) * n * repW + w;
-        const int p = (c + y + t0) & 1;
-        const bool cut = t0 < 2;
-        // the ordinary time neighbour (t - 1; t = 2 for the cut row t = 1)
-        const int off_n = t0 == 0 ? (Lt - 1) * rw : (t0 == 1 ? (Lt == 2 ? -rw : rw) : -rw);
-        // the row across the cut (t = 0, 1), else t + 1
-        const int off_x = t0 == 0 ? rw : t0 == 1 ? -rw : (t0 == Lt - 1 ? -(Lt - 1) * rw : rw);
-        // the glued partner across the cut: replica r+1 above it, r-1 below (mod n)
-        const int off_g = !cut ? 0 : t0 == 0 ? (r0 == n - 1 ? -(n - 1) * repW : repW)
-                                            : (r0 == 0 ? (n - 1) * repW : -repW);
-        const uint32_t m = cut ? glue_mask(lg, p) : 0u;
-        const uint32_t own = own_b[w];
-        const uint32_t nrm = o[off_n];
-        const uint32_t self_w = o[off_x];
-        const uint32_t glue_w = o[off_x + off_g];
-        const uint32_t cross = (self_w & ~m) | (glue_w & m);
-        const uint32_t nx0 = o[0];
-        const uint32_t nx1 = xshift(o, p, nx0);
-        uint32_t dsum = (own ^ nrm) + (own ^ cross) + (own ^ nx0) + (own ^ nx1);
-        if (D == 3) dsum += (own ^ o[d_ym]) + (own ^ o[d_yp]);
-        uint32_t flip = accept8<D>(dsum, ua, ub, tab);
-        const int jlo = (cut && k >= 0) ? max(((J.g0 - p + 1) >> 1) - 8 * q, 0) : 8;
-        const int jhi = min(((J.g1 - p + 1) >> 1) - 8 * q, 8);
-#pragma unroll 1
-        for (int jl = jlo; jl < jhi; ++jl)
-            switched_site(flip, jl, own, self_w, glue_w, dsum, ua, ub, k, J, w_self, w_glue,
-                          record, dE);
-        if (!FAST) flip &= vmask;
-        own_b[w] = own ^ flip;
+        row_update(S + c * n * repW, S + (1 - c) * n * repW, w, t0, r0, (c + y + t0) & 1, ua, ub,
+                   k, lg, J, w_self, w_glue, record, dE);
     }
 
     // Loads a stored configuration (int8 +-1, natural order [r][t][y][x]) into
