@@ -44,7 +44,10 @@ N_ALG = {2: 32, 3: 36}
 # compares); the data-dependent union-find and root flip draws are not counted,
 # so this fraction is a lower bound.
 N_ALG_SW = {2: 104, 3: 104}
-SM_COUNT, INT_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+# Integer lanes per SM per clock (64 ALU + 64 FMA-pipe integer lanes); the SM
+# count and clock are read from the live device.
+INT_LANES_PER_SM = 128
+SM_MAX_MHZ_FALLBACK = 2070.0
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -98,9 +101,15 @@ def parse_args():
                          "L with L_t = 4L (l = 1..4 for L = 24, 2..5 for L = 48)")
     ap.add_argument("--no-compare", action="store_true",
                     help="sw: skip the equal-error comparison with Metropolis")
-    ap.add_argument("--plain", type=int, default=0,
+    ap.add_argument("--plain", type=int, default=8,
                     help="also time the plain one-lattice-per-launch baseline on this many "
-                         "trajectories of the middle l")
+                         "trajectories of the middle l (0: skip)")
+    ap.add_argument("--bias-traj", type=int, default=512,
+                    help="trajectories per l of the Swendsen-Wang reference scan of the "
+                         "thermalisation-bias check (0: skip)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline workload only (no configs 1 and 3, plain baseline or bias "
+                         "check beside the default config-2 run)")
     return ap.parse_args()
 
 
@@ -325,14 +334,304 @@ def c_function_errors(w, results):
 
 
 # ------------------------------------------------------------ our arm -------
+def device_facts(torch, local_rank):
+    """SM count from the device properties and the maximum SM clock from
+    nvidia-smi (the derived integer-issue ceiling uses both)."""
+    props = torch.cuda.get_device_properties(local_rank)
+    mhz = None
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits",
+                              "-i", str(local_rank)], capture_output=True, text=True, timeout=20).stdout
+        mhz = float(out.strip().splitlines()[0])
+    except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+        mhz = None
+    return {"name": props.name, "sm_count": props.multi_processor_count,
+            "sm_max_mhz": mhz if mhz else SM_MAX_MHZ_FALLBACK,
+            "sm_max_mhz_source": "nvidia-smi clocks.max.sm" if mhz else "fallback 2070 MHz"}
+
+
+def ceilings(jz, dev_index, facts):
+    """The three ceilings of the trajectory kernel's roofline, from the live
+    device: derived issue ceiling (SMs x 128 integer lanes x max clock, int-op/s),
+    the measured mixed IMAD/LOP3/IADD3 issue rate (thread-instr/s) and the
+    measured Philox4x32-10-only update rate (4 updates per block)."""
+    derived = facts["sm_count"] * INT_LANES_PER_SM * facts["sm_max_mhz"] * 1e6
+    mix = jz.ising_probe(dev_index, 2)
+    philox = jz.ising_probe(dev_index, 3)
+    return {"derived_int_ops_per_s": derived, "probe_mix_int_ops_per_s": mix,
+            "philox_update_ceiling_per_s": 4.0 * philox,
+            "derived_basis": f"{facts['sm_count']} SMs x {INT_LANES_PER_SM} int lanes/clk x "
+                             f"{facts['sm_max_mhz']:.0f} MHz ({facts['sm_max_mhz_source']})"}
+
+
+def fractions(ops_per_s, updates_per_s, ceil):
+    return {"frac_derived": ops_per_s / ceil["derived_int_ops_per_s"],
+            "frac_probe": ops_per_s / ceil["probe_mix_int_ops_per_s"],
+            "frac_philox_ceiling": updates_per_s / ceil["philox_update_ceiling_per_s"]}
+
+
+def job_params(jz, j, **over):
+    kw = dict(n_therm=j.n_therm, direction=j.direction, traj0=j.traj0, update=j.update,
+              protocol=j.protocol, n_replica=j.n_replica, whole=j.whole)
+    kw.update(over)
+    return jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj, j.seed,
+                          **kw)
+
+
+def exchange_work(arrays, jobs, world, group):
+    """The one exchange step of the method: every job's W_int shards gathered
+    in global trajectory order on every rank (shard.gather_work, which reports a
+    missing or mis-sized shard instead of waiting on it)."""
+    from paper_2304_03311_gb300 import shard
+    return [shard.gather_work(a.cpu().numpy() if hasattr(a, "cpu") else a,
+                              j.n_traj * world, group=group)
+            for a, j in zip(arrays, jobs)]
+
+
+class Scan:
+    """One workload on the device: its parameters, output buffers, tuned CTA
+    sizes, and a step = the trajectory launch(es) + the FP64 estimator per job
+    (+ the c-function on the host)."""
+
+    def __init__(self, jz, torch, ctx, stream, dev, w, world=1, host_group=None, threads=0,
+                 autotune=True, use_plan=False):
+        self.jz, self.torch, self.ctx, self.stream, self.w = jz, torch, ctx, stream, w
+        self.world, self.group = world, host_group
+        self.sw = all(j.update == 1 for j in w.jobs)
+        self.outs = [torch.empty(j.n_traj, dtype=torch.int64, device=dev) for j in w.jobs]
+        self.params = [job_params(jz, j) for j in w.jobs]
+        self.n_groups = len({(j.d, j.L, j.L_t, j.seed, j.update, j.n_replica) for j in w.jobs})
+        self.tuned = {}
+        self.plan = None
+        self.est = None
+        if use_plan:
+            self.est = torch.zeros(3 * len(w.jobs), dtype=torch.float64, device=dev)
+            self.plan = jz.jz_plan_create(ctx, self.params, self.outs, self.est, threads)
+            cta, grid, n_items = jz.jz_plan_info(self.plan)
+            self.tuned = {"persistent_cta": cta, "grid": grid, "work_items": n_items}
+            self.n_groups = 1
+        else:
+            for shape, j in {(j.d, j.L, j.L_t): j for j in w.jobs}.items():
+                if threads:
+                    jz.ising_set_threads(ctx, *shape, threads)
+                    self.tuned[str(shape)] = threads
+                elif autotune and j.update == 0:
+                    try:
+                        self.tuned[str(shape)] = jz.ising_autotune(ctx, self.params[w.jobs.index(j)])
+                    except jz.IsingError:   # lattices beyond shared memory are not tuned
+                        self.tuned[str(shape)] = "default (lattice in HBM)"
+
+    def launches_per_step(self):
+        return 2 if self.plan is not None else self.n_groups + len(self.w.jobs)
+
+    def estimate(self, buffers):
+        res = []
+        for j, b in zip(self.w.jobs, buffers):
+            _, ds, err = self.jz.estimator_reduce(self.ctx, b, j.n_traj * self.world, j.beta,
+                                                  j.n_step, j.direction, 32)
+            res.append((ds, err))
+        return res
+
+    def step(self):
+        """One step; returns ((start event, end event, library launch ms), c-function)."""
+        torch, jz = self.torch, self.jz
+        k0 = torch.cuda.Event(enable_timing=True)
+        k1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(self.stream):
+            k0.record(self.stream)
+            if self.plan is not None:
+                jz.jz_plan_launch(self.plan)
+            else:
+                jz.jarzynski_run_batch(self.ctx, self.params, self.outs)
+            k1.record(self.stream)
+            if self.plan is not None and self.world == 1:
+                e = self.est.cpu().numpy().reshape(-1, 3)
+                return (k0, k1, None), c_function_errors(self.w, [(r[1], r[2]) for r in e])
+            bufs = self.outs
+            if self.world > 1:
+                bufs = exchange_work(self.outs, self.w.jobs, self.world, self.group)
+            res = self.estimate(bufs)
+        # the trajectory launches alone (library events on the same stream, the
+        # call's table and result copies excluded); the plan's graph has none
+        launch_ms = jz.ising_last_launch_ms(self.ctx) if self.plan is None else None
+        return (k0, k1, launch_ms), c_function_errors(self.w, res)
+
+    def free(self):
+        if self.plan is not None:
+            self.jz.jz_plan_free(self.plan)
+
+
+def timed(torch, dist, scan, steps, warmup, flush, world, local_rank):
+    """W untimed steps, then K steps bracketed by barrier + synchronize, L2
+    flushed between steps; device time from CUDA events on the launching
+    stream, max over ranks."""
+    stream = scan.stream
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+
+    for _ in range(warmup):
+        scan.step()
+        flush_l2()
+    stream.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    pairs = []
+    t_start.record(stream)
+    cfun = None
+    for i in range(steps):
+        pair, cfun = scan.step()
+        pairs.append(pair)
+        if i + 1 < steps:
+            flush_l2()
+    t_end.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    kernel_ms = statistics.mean(ms if ms is not None else a.elapsed_time(b) for a, b, ms in pairs)
+    if world > 1:
+        t = torch.tensor([elapsed_ms, kernel_ms], dtype=torch.float64,
+                         device=torch.device("cuda", local_rank))
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms, kernel_ms = float(t[0]), float(t[1])
+    ms_per_step = elapsed_ms / steps
+    return {"ms_per_step": ms_per_step, "kernel_ms": kernel_ms, "cfun": cfun, "clocks": clocks,
+            "steps": steps, "warmup": warmup}
+
+
+def workload_record(w, t, ceil, world=1, sw=False):
+    """Rates and roofline fractions of one timed workload."""
+    updates = w.updates * world
+    ops, n_alg = algorithmic_ops(w.jobs, sw)
+    k_s = t["kernel_ms"] / 1e3
+    rec = {"workload": w.name, "ms_per_step": t["ms_per_step"], "kernel_ms": t["kernel_ms"],
+           "spin_updates_per_s": updates / (t["ms_per_step"] / 1e3),
+           "trajectories_per_s": w.trajectories * world / (t["ms_per_step"] / 1e3),
+           "kernel_spin_updates_per_s": w.updates / k_s, "ops_per_update": n_alg,
+           "steps": t["steps"], "warmup": t["warmup"], "clocks": t["clocks"],
+           "c_function_err_max": max(e for _, e in t["cfun"]) if t["cfun"] else None}
+    if ceil and not sw:
+        rec.update(fractions(ops / k_s, w.updates / k_s, ceil))
+    return rec
+
+
+def pulls(test, ref):
+    """Per-l pulls of two c-function scans (value, error) and their summary."""
+    p = [(a - b) / math.hypot(ea, eb) for (a, ea), (b, eb) in zip(test, ref)]
+    chi2 = sum(x * x for x in p) / len(p)
+    return {"max_abs_pull": max(abs(x) for x in p), "mean_pull": sum(p) / len(p),
+            "chi2_per_l": chi2,
+            # 31 independent unit normals: chi2/l below 1.8 and no pull beyond 3.6
+            # fail by chance in well under 1 % of scans
+            "passes": chi2 < 1.8 and max(abs(x) for x in p) < 3.6}
+
+
+def bias_and_cost(jz, torch, ctx, stream, dev, headline_w, headline_cfun, headline_ms, args):
+    """Thermalisation bias of the 2D L = 64 scan and the cost of a c-function
+    at fixed error for both updates.  A Jarzynski estimate is unbiased only from
+    an equilibrium start (Appendix A), so each scan's per-l c-function is pulled
+    against a Swendsen-Wang reference with 1000 cluster sweeps of
+    thermalisation (the paper's set-up, section 4) on independent
+    trajectories; each update's cost is the time to reach the headline's rms
+    c-function error at the smallest tested n_therm whose pulls pass."""
+    nref = args.bias_traj
+    base = headline_w.jobs
+
+    def run(tag, update, n_therm, n_traj, traj0):
+        jobs = [j.with_(update=update, n_therm=n_therm, n_traj=n_traj, traj0=traj0) for j in base]
+        w = wl.Workload(f"{headline_w.name}_{tag}", jobs)
+        outs = [torch.empty(n_traj, dtype=torch.int64, device=dev) for _ in jobs]
+        ps = [job_params(jz, j) for j in jobs]
+        with torch.cuda.stream(stream):
+            jz.jarzynski_run_batch(ctx, ps, outs)
+        ms = jz.ising_last_launch_ms(ctx)
+        res = []
+        for j, o in zip(jobs, outs):
+            _, ds, err = jz.estimator_reduce(ctx, o, n_traj, j.beta, j.n_step, j.direction, 32)
+            res.append((ds, err))
+        return {"cfun": c_function_errors(w, res), "kernel_ms": ms, "n_traj_per_l": n_traj,
+                "n_therm": n_therm}
+
+    rms = lambda v: math.sqrt(sum(e * e for _, e in v) / len(v))
+    # independent trajectory ranges: the headline uses 0 .. n_traj-1
+    ref = run("sw_ref", 1, 1000, nref, 1 << 28)
+    head = {"cfun": headline_cfun, "kernel_ms": headline_ms, "n_traj_per_l": base[0].n_traj,
+            "n_therm": base[0].n_therm}
+    cands = {"metropolis": [head, run("m4000", 0, 4000, 2 * nref, 2 << 28)],
+             "sw": [run("sw100", 1, 100, nref, 3 << 28)]}
+    target = rms(headline_cfun)
+    out = {"reference": f"Swendsen-Wang, n_therm = 1000, {nref} trajectories per l "
+                        f"(independent of the headline's)",
+           "headline": dict(pulls(headline_cfun, ref["cfun"]), n_therm=base[0].n_therm),
+           "target_c_err_rms": target}
+    cost = {}
+    for upd, runs in cands.items():
+        tested = []
+        chosen = None
+        for r in runs:
+            pl = pulls(r["cfun"], ref["cfun"])
+            tested.append({"n_therm": r["n_therm"], **pl})
+            if chosen is None and pl["passes"]:
+                chosen = r
+        entry = {"tested": tested}
+        if chosen is not None:
+            e = rms(chosen["cfun"])
+            t_s = chosen["kernel_ms"] / 1e3
+            n_per_l = chosen["n_traj_per_l"]
+            need = n_per_l * (e / target) ** 2          # trajectories per l at the target error
+            seconds = t_s * (e / target) ** 2
+            entry.update({"n_therm": chosen["n_therm"], "run_kernel_s": t_s,
+                          "n_traj_per_l": n_per_l, "c_err_rms": e,
+                          "trajectories_per_s": n_per_l * len(base) / t_s,
+                          "trajectories_per_l_at_target": need,
+                          "seconds_at_target": seconds})
+        cost[upd] = entry
+    if all("seconds_at_target" in c for c in cost.values()):
+        cost["sw_over_metropolis_time_at_target"] = (cost["sw"]["seconds_at_target"] /
+                                                     cost["metropolis"]["seconds_at_target"])
+    out["cost_at_fixed_error"] = cost
+    return out
+
+
+def plain_baseline(jz, torch, ctx, dev, w, value, n):
+    """K0: the plain one-lattice-per-launch form on n trajectories of the
+    middle transformation, and the fused kernel on the same trajectories
+    (identical bits, hence equal statistical error)."""
+    j = w.jobs[len(w.jobs) // 2].with_(n_traj=n)
+    pw = torch.empty(j.n_traj, dtype=torch.int64, device=dev)
+    pp = job_params(jz, j)
+    jz.ising_sync(ctx)
+    t0 = time.perf_counter()
+    jz.jarzynski_run_plain(ctx, pp, pw)
+    jz.ising_sync(ctx)
+    dt = time.perf_counter() - t0
+    fw = torch.empty_like(pw)
+    jz.jarzynski_run_ex(ctx, pp, fw)
+    jz.ising_sync(ctx)
+    return {"value": j.updates / dt, "unit": UNIT, "sample": f"{j.n_traj} trajectories of l = {j.l}",
+            "seconds": dt, "bit_identical_to_fused": bool(torch.equal(pw, fw)),
+            "speedup_of_fused": value / (j.updates / dt)}
+
+
 def run_ours(args):
-    import numpy as np
     import torch
     import torch.distributed as dist
 
     rank, world, local_rank = dist_env()
+    host_group = None
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
+        # the W_int exchange is a host-side gather (8 bytes per trajectory)
+        host_group = dist.new_group(backend="gloo")
     torch.cuda.set_device(local_rank)
     from paper_2304_03311_gb300 import build as jzbuild
     if rank == 0 or world == 1:
@@ -347,109 +646,15 @@ def run_ours(args):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
     ctx = jz.ising_replica_init(local_rank, 0, stream.cuda_stream)
-    outs = [torch.empty(j.n_traj, dtype=torch.int64, device=dev) for j in w.jobs]
-    params = [jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj,
-                             j.seed, n_therm=j.n_therm, direction=j.direction, traj0=j.traj0,
-                             update=j.update, protocol=j.protocol, n_replica=j.n_replica,
-                             whole=j.whole)
-              for j in w.jobs]
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    n_groups = len({(j.d, j.L, j.L_t, j.seed) for j in w.jobs})
-    tuned = {}
-    plan = None
-    est = None
     if sw and args.config == 4:
         raise SystemExit("--update sw runs configs 1-3 (the persistent plan is Metropolis only)")
-    if args.config == 4:
-        # uneven batch: one persistent launch + batched estimator, one CUDA graph
-        est = torch.zeros(3 * len(w.jobs), dtype=torch.float64, device=dev)
-        plan = jz.jz_plan_create(ctx, params, outs, est, args.threads)
-        cta, grid, n_items = jz.jz_plan_info(plan)
-        tuned = {"persistent_cta": cta, "grid": grid, "work_items": n_items}
-        n_groups = 1
-    else:
-        for shape, j in {(j.d, j.L, j.L_t): j for j in w.jobs}.items():
-            if args.threads:
-                jz.ising_set_threads(ctx, *shape, args.threads)
-                tuned[str(shape)] = args.threads
-            elif not args.no_autotune and not sw:
-                p = params[w.jobs.index(j)]
-                try:
-                    tuned[str(shape)] = jz.ising_autotune(ctx, p)
-                except jz.IsingError:      # lattices beyond shared memory are not tuned
-                    tuned[str(shape)] = "default (lattice in HBM)"
-
-    def estimate(buffers, gathered_world):
-        res = []
-        for j, b in zip(w.jobs, buffers):
-            _, ds, err = jz.estimator_reduce(ctx, b, j.n_traj * gathered_world, j.beta,
-                                             j.n_step, j.direction, 32)
-            res.append((ds, err))
-        return res
-
-    def step():
-        k0 = torch.cuda.Event(enable_timing=True)
-        k1 = torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
-            k0.record(stream)
-            if plan is not None:
-                jz.jz_plan_launch(plan)
-            else:
-                jz.jarzynski_run_batch(ctx, params, outs)
-            k1.record(stream)
-            if plan is not None and world == 1:
-                e = est.cpu().numpy().reshape(-1, 3)
-                return (k0, k1, None), c_function_errors(w, [(r[1], r[2]) for r in e])
-            bufs = outs
-            if world > 1:
-                bufs = []
-                for o in outs:
-                    parts = [torch.empty_like(o) for _ in range(world)]
-                    dist.all_gather(parts, o)
-                    bufs.append(torch.cat(parts))
-            res = estimate(bufs, world)
-        # the trajectory launches alone (library events on the same stream, the
-        # call's table and result copies excluded); the plan's graph has none
-        launch_ms = jz.ising_last_launch_ms(ctx) if plan is None else None
-        return (k0, k1, launch_ms), c_function_errors(w, res)
-
-    def flush_l2():
-        with torch.cuda.stream(stream):
-            flush.fill_(1)
-
-    for _ in range(args.warmup):
-        step()
-        flush_l2()
-    stream.synchronize()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local_rank)
-    sampler.start()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    kernel_pairs = []
-    t_start.record(stream)
-    cfun = None
-    for i in range(args.steps):
-        pair, cfun = step()
-        kernel_pairs.append(pair)
-        if i + 1 < args.steps:
-            flush_l2()
-    t_end.record(stream)
-    stream.synchronize()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clocks = sampler.stop()
-    elapsed_ms = t_start.elapsed_time(t_end)
-    kernel_ms = statistics.mean(ms if ms is not None else a.elapsed_time(b)
-                                for a, b, ms in kernel_pairs)
-    if world > 1:
-        t = torch.tensor([elapsed_ms, kernel_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms, kernel_ms = float(t[0]), float(t[1])
-    ms_per_step = elapsed_ms / args.steps
+    facts = device_facts(torch, local_rank)
+    ceil = ceilings(jz, local_rank, facts)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    scan = Scan(jz, torch, ctx, stream, dev, w, world, host_group, args.threads,
+                not args.no_autotune, use_plan=args.config == 4)
+    t = timed(torch, dist, scan, args.steps, args.warmup, flush, world, local_rank)
+    cfun, kernel_ms, ms_per_step, clocks = t["cfun"], t["kernel_ms"], t["ms_per_step"], t["clocks"]
     updates_step = w.updates * world
     value = updates_step / (ms_per_step / 1e3)
     traj_rate = w.trajectories * world / (ms_per_step / 1e3)
@@ -464,23 +669,16 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         with torch.cuda.stream(stream):
-            jz.jarzynski_run_batch(ctx, params, host_outs)
-            if world > 1:
-                gathered = []
-                for h in host_outs:
-                    parts = [torch.empty(len(h), dtype=torch.int64, device=dev)
-                             for _ in range(world)]
-                    dist.all_gather(parts, h.to(dev))
-                    gathered.append(torch.cat([p.cpu() for p in parts]).numpy())
-            else:
-                gathered = host_outs
-            estimate(gathered, world)
+            jz.jarzynski_run_batch(ctx, scan.params, host_outs)
+            gathered = (exchange_work(host_outs, w.jobs, world, host_group) if world > 1
+                        else host_outs)
+            scan.estimate(gathered)
     stream.synchronize()
     e2e_s = time.perf_counter() - t0
     if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t[0])
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt[0])
     table_bytes = sum(j.n_step * (2 if sw else 8 * j.d) * 4 + 96 for j in w.jobs)
     h2d = table_bytes + sum(8 * j.n_traj * world for j in w.jobs)
     d2h = sum(8 * j.n_traj for j in w.jobs) + 24 * len(w.jobs)
@@ -490,73 +688,66 @@ def run_ours(args):
     d = w.jobs[0].d
     ops_per_launch, n_alg = algorithmic_ops(w.jobs, sw)   # one launch per rank per step
     achieved = ops_per_launch / (kernel_ms / 1e3) / 1e12
-    peak = SM_COUNT * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-    kbase = "sw_kernel" if sw else "persistent_kernel" if plan is not None else "traj_kernel"
+    peak = ceil["derived_int_ops_per_s"] / 1e12
+    kbase = "sw_kernel" if sw else "persistent_kernel" if scan.plan is not None else "traj_kernel"
     kname = (f"sw_kernel<{d}>" if sw else
-             "persistent_kernel" if plan is not None else f"traj_kernel<{d},...>")
+             "persistent_kernel" if scan.plan is not None else f"traj_kernel<{d},...>")
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved,
                 "peak": peak, "unit": "Tintop/s", "frac": achieved / peak,
                 "traffic": traffic_from_profile(kbase, w.name),
                 "ops_per_update": n_alg, "kernel_ms": kernel_ms,
-                "peak_basis": "152 SMs x 128 int lanes/clk x 2070 MHz (derived)"}
+                "peak_basis": ceil["derived_basis"] + " (derived)"}
+    if not sw:
+        fr = fractions(ops_per_launch / (kernel_ms / 1e3), w.updates / (kernel_ms / 1e3), ceil)
+        roofline.update({"frac_probe": fr["frac_probe"],
+                         "frac_philox_ceiling": fr["frac_philox_ceiling"],
+                         "probe_peak": ceil["probe_mix_int_ops_per_s"] / 1e12,
+                         "philox_update_ceiling": ceil["philox_update_ceiling_per_s"]})
 
     equal_error = None
     if sw and not args.no_compare:
         # the same workload with Metropolis sweeps: time per step and the
         # c-function error it reaches; at equal error the cost scales as err^2 t
-        mparams = [jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj,
-                                  j.seed, n_therm=j.n_therm, direction=j.direction,
-                                  traj0=j.traj0, update=0, protocol=j.protocol,
-                                  n_replica=j.n_replica, whole=j.whole)
-                   for j in w.jobs]
-        if not args.no_autotune and not args.threads:
-            for shape, j in {(j.d, j.L, j.L_t): j for j in w.jobs}.items():
-                try:
-                    jz.ising_autotune(ctx, mparams[w.jobs.index(j)])
-                except jz.IsingError:
-                    pass
-        with torch.cuda.stream(stream):
-            jz.jarzynski_run_batch(ctx, mparams, outs)
-            m0 = torch.cuda.Event(enable_timing=True)
-            m1 = torch.cuda.Event(enable_timing=True)
-            flush.fill_(1)
-            m0.record(stream)
-            jz.jarzynski_run_batch(ctx, mparams, outs)
-            m1.record(stream)
-        stream.synchronize()
-        m_ms = m0.elapsed_time(m1)
-        mfun = c_function_errors(w, estimate(outs, 1))
+        mw = wl.Workload(w.name + "_metropolis", [j.with_(update=0) for j in w.jobs])
+        mscan = Scan(jz, torch, ctx, stream, dev, mw, world, host_group, args.threads,
+                     not args.no_autotune)
+        mt = timed(torch, dist, mscan, 1, 1, flush, world, local_rank)
+        m_ms, mfun = mt["kernel_ms"], mt["cfun"]
+        rms = lambda v: math.sqrt(sum(x * x for x in v) / len(v))
         m_err = [e for _, e in mfun]
         s_err = [e for _, e in cfun]
-        rms = lambda v: math.sqrt(sum(x * x for x in v) / len(v))
-        # both updates sample the same Z ratios: their c-functions must agree
-        pulls = [(a - b) / math.hypot(ea, eb) for (a, ea), (b, eb) in zip(cfun, mfun)]
+        pl = pulls(cfun, mfun)
         equal_error = {
             "metropolis": {"kernel_ms": m_ms, "c_err_rms": rms(m_err)},
             "sw": {"kernel_ms": kernel_ms, "c_err_rms": rms(s_err)},
             "sw_speedup_at_equal_error": (rms(m_err) ** 2 * m_ms) / (rms(s_err) ** 2 * kernel_ms),
-            "c_function_pull_max": max(abs(p) for p in pulls),
-            "c_function_chi2_per_l": sum(p * p for p in pulls) / len(pulls),
+            "c_function_pull_max": pl["max_abs_pull"], "c_function_chi2_per_l": pl["chi2_per_l"],
             "basis": "same trajectories, N, sweeps and n_therm; cost at equal error ~ err^2 x time"}
 
+    # the other spec workloads and the plain baseline, beside the
+    # headline (one GPU only; the headline alone under torchrun)
+    default_run = (args.config == 2 and not sw and args.protocol == 1 and args.n_replica == 2
+                   and not args.whole and not args.lattice and not args.traj_per_l
+                   and not args.n_step and args.n_therm is None)
+    extras = world == 1 and not args.no_extras and default_run
+    configs = None
     plain = None
-    if args.plain > 0 and not sw:
-        j = w.jobs[len(w.jobs) // 2].with_(n_traj=args.plain)
-        pw = torch.empty(j.n_traj, dtype=torch.int64, device=dev)
-        pp = jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj, j.seed,
-                            n_therm=j.n_therm, direction=j.direction, traj0=j.traj0)
-        stream.synchronize()
-        t0 = time.perf_counter()
-        jz.jarzynski_run_plain(ctx, pp, pw)
-        jz.ising_sync(ctx)
-        dt = time.perf_counter() - t0
-        # same trajectories from the fused kernel: identical bits, so equal error
-        fw = torch.empty_like(pw)
-        jz.jarzynski_run_ex(ctx, pp, fw)
-        jz.ising_sync(ctx)
-        plain = {"value": j.updates / dt, "unit": UNIT, "sample": f"{j.n_traj} trajectories "
-                 f"of l = {j.l}", "bit_identical_to_fused": bool(torch.equal(pw, fw)),
-                 "speedup_of_fused": value / (j.updates / dt)}
+    bias = None
+    if extras:
+        configs = {"2": workload_record(w, t, ceil)}
+        for c, (steps, warm) in ((1, (20, 5)), (3, (3, 1))):
+            cw = wl.CONFIGS[c]()
+            cs = Scan(jz, torch, ctx, stream, dev, cw, 1, None, 0, not args.no_autotune)
+            ct = timed(torch, dist, cs, steps, warm, flush, 1, local_rank)
+            configs[str(c)] = workload_record(cw, ct, ceil)
+            configs[str(c)]["cta_threads"] = cs.tuned
+            cs.free()
+        if args.plain > 0:
+            plain = plain_baseline(jz, torch, ctx, dev, w, value, args.plain)
+        if args.bias_traj > 0:
+            bias = bias_and_cost(jz, torch, ctx, stream, dev, w, cfun, kernel_ms, args)
+    elif args.plain > 0 and not sw:
+        plain = plain_baseline(jz, torch, ctx, dev, w, value, args.plain)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -565,8 +756,7 @@ def run_ours(args):
                "trajectories_per_s": trate, "single_core_value": single,
                # the whole workload on these cores, extrapolated at the sampled rate
                "full_workload_s_estimate": w.updates / rate if rate > 0 else None}
-    if plan is not None:
-        jz.jz_plan_free(plan)
+    scan.free()
     jz.ising_replica_free(ctx)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -577,11 +767,13 @@ def run_ours(args):
                 "trajectories_per_s": traj_rate,
                 "c_function_err_max": max(e for _, e in cfun) if cfun else None,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "plain_gpu_baseline": plain, "cta_threads": tuned or "default",
+                "configs": configs, "plain_gpu_baseline": plain, "bias_check": bias,
+                "ceilings": ceil, "device": facts,
+                "cta_threads": scan.tuned or "default",
                 "update": args.update, "protocol": args.protocol,
                 "n_replica": args.n_replica, "whole_cut": args.whole,
                 "equal_error_vs_metropolis": equal_error,
-                "gpu_launches": args.steps * ((2 if plan is not None else n_groups + len(w.jobs))),
+                "gpu_launches": args.steps * scan.launches_per_step(),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:

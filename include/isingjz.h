@@ -67,6 +67,7 @@ extern "C" {
 #define ISING_ERR_NOT_FOUND   -8  /* unknown job id                              */
 #define ISING_ERR_PENDING     -9  /* job not finished yet (jz_poll)              */
 #define ISING_ERR_SCRATCH_LIMIT -10 /* too large for jarzynski_run_noalloc     */
+#define ISING_ERR_CANCELLED   -11 /* stopped by ising_cancel / jz_cancel          */
 
 /* Opaque per-device context: stream, device buffers, autotune choices. */
 typedef struct ising_ctx ising_ctx;
@@ -203,6 +204,37 @@ int jarzynski_run_ex(ising_ctx* ctx, const jz_params* p, int64_t* work_int_out,
 int jarzynski_run_segment(ising_ctx* ctx, const jz_params* p, int k_begin, int k_end,
                           int64_t* work_io, int8_t* spins_io);
 
+/* Cancellation and resumable runs; the paper has no counterpart.
+ * ising_cancel sets the context's cancel flag (an atomic host flag; safe to
+ * call from any host thread while another thread is inside a run call).
+ * While it is set, every run call on the context (jarzynski_run, _ex, _batch,
+ * _segment, _plain, _resumable, ising_autotune) returns ISING_ERR_CANCELLED
+ * instead of enqueuing more work; work already on the device runs to its end
+ * (no kernel is interrupted).  _batch and _plain test the flag between their
+ * launches.  ising_cancel_reset clears it.  Errors: ISING_ERR_ARG (NULL). */
+int ising_cancel(ising_ctx* ctx);
+int ising_cancel_reset(ising_ctx* ctx);
+
+/* A long transformation run as a sequence of protocol segments of
+ * steps_per_segment steps (jarzynski_run_segment semantics: the random counter
+ * is a function of the global sweep index, so the bits equal those of one
+ * jarzynski_run_ex call), with the cancel flag tested between segments.
+ *   *k_done    in: protocol steps already done (0 = start from the hot start;
+ *              otherwise work_io / spins_io hold the state after step
+ *              *k_done - 1); out: steps done when the call returns
+ *   max_segments  0 = run to the end; > 0 = stop after that many segments
+ *   work_io, spins_io  device buffers as for jarzynski_run_segment
+ * At most two segments are in flight, so a cancel takes effect within about
+ * two segments' time.  Returns ISING_OK when *k_done = n_step (the call has
+ * synchronised the context's stream), ISING_ERR_PENDING when max_segments
+ * stopped it, ISING_ERR_CANCELLED when the flag stopped it; in both of the
+ * latter cases the buffers hold the consistent state after step *k_done - 1
+ * and a later call (after ising_cancel_reset) resumes from there.  Errors: as
+ * jarzynski_run_segment, ISING_ERR_ARG for steps_per_segment < 1 or *k_done
+ * outside [0, n_step]. */
+int jarzynski_run_resumable(ising_ctx* ctx, const jz_params* p, int steps_per_segment,
+                            int max_segments, int* k_done, int64_t* work_io, int8_t* spins_io);
+
 /* Runs n_jobs transformations in one device launch per lattice shape (jobs of
  * equal (d, L, L_t) share a launch; the c-function scan of section 3 is one
  * call with one job per l).  work_outs[j] is job j's caller-owned output of
@@ -290,6 +322,26 @@ int jz_poll(jz_server* s, uint64_t job_id, jz_result* out);
  * job is still unfinished then (the job keeps running). */
 int jz_wait(jz_server* s, uint64_t job_id, double timeout_s, jz_result* out);
 
+/* Cancels a job: a queued job is dropped at once, a job already on the device
+ * runs to its end with its results discarded; either way it finishes with
+ * status ISING_ERR_CANCELLED.  A finished job keeps its result.  Returns
+ * ISING_OK, or ISING_ERR_NOT_FOUND for an unknown id.  The paper has no
+ * counterpart. */
+int jz_cancel(jz_server* s, uint64_t job_id);
+
+/* Per-job metrics as JSON lines: with path non-NULL the server appends one
+ * line per finished job to that file (opened in append mode; NULL closes it):
+ * its id, parameters, status, ln<e^-W>, Delta S_2 and its error, the server
+ * clock at submission, launch and completion, latency, spin updates and
+ * spin updates/s over its time on the device.  Errors: ISING_ERR_ARG,
+ * ISING_ERR_NOT_FOUND (the file cannot be opened). */
+int jz_server_set_log(jz_server* s, const char* path);
+
+/* The JSON line jz_server_set_log writes for one job, into buf (n bytes,
+ * NUL-terminated).  Host only (no device needed).  Returns the line's length,
+ * or ISING_ERR_ARG (NULL arguments, or n too small for the line). */
+int jz_result_json(uint64_t job_id, const jz_params* p, const jz_result* r, char* buf, size_t n);
+
 /* Copies a finished job's W_int (n_traj entries) to host memory work_out. */
 int jz_server_work(jz_server* s, uint64_t job_id, int64_t* work_out);
 
@@ -370,6 +422,37 @@ int ising_set_threads(ising_ctx* ctx, int d, int L, int L_t, int threads);
  * timed or stored and *threads receives that size (256 in 2D, 512 in 3D).
  * Errors: as jarzynski_run_ex. */
 int ising_autotune(ising_ctx* ctx, const jz_params* p, int* threads);
+
+/* Persisted autotune cache; the paper has no counterpart.  Keys are (GPU
+ * name, d, L, L_t, n, n_traj bucket) with bucket = floor(log2 n_traj): the
+ * best CTA size depends on the lattice and on how many trajectories fill the
+ * GPU.  The file is JSON, {"version": 1, "entries": [...]}, one entry per
+ * line with the keys gpu, d, L, L_t, n_replica, traj_bucket, cta_threads.
+ * The cache functions are host only (no device needed); the cache is not
+ * thread-safe.
+ *   create / free   an empty cache
+ *   load            merges a file's entries (later ones win); ISING_ERR_NOT_FOUND
+ *                   if the file cannot be opened, ISING_ERR_ARG if it is malformed
+ *   save            writes every entry; ISING_ERR_NOT_FOUND if it cannot write
+ *   put / get       one entry; get returns ISING_ERR_NOT_FOUND on a miss
+ *   size            number of entries
+ * ising_autotune_cached: on a hit for the context's GPU, fixes that CTA size
+ * for p's shape in the context (as ising_set_threads) without timing
+ * anything; on a miss runs ising_autotune and stores its choice.  *threads
+ * (nullable) receives the size, *hit (nullable) 1 for a hit and 0 otherwise.
+ * Swendsen-Wang jobs are not cached (their CTA size is fixed). */
+typedef struct jz_tune_cache jz_tune_cache;
+int jz_tune_cache_create(jz_tune_cache** out);
+void jz_tune_cache_free(jz_tune_cache* c);
+int jz_tune_cache_load(jz_tune_cache* c, const char* path);
+int jz_tune_cache_save(const jz_tune_cache* c, const char* path);
+int jz_tune_cache_put(jz_tune_cache* c, const char* gpu, int d, int L, int L_t, int n_replica,
+                      int n_traj, int cta_threads);
+int jz_tune_cache_get(const jz_tune_cache* c, const char* gpu, int d, int L, int L_t,
+                      int n_replica, int n_traj, int* cta_threads);
+int jz_tune_cache_size(const jz_tune_cache* c, int* n);
+int ising_autotune_cached(ising_ctx* ctx, jz_tune_cache* c, const jz_params* p, int* threads,
+                          int* hit);
 
 /* Measurement utility; the paper has no counterpart.  Runs an integer-issue
  * probe on `device` over all SMs at full occupancy and writes its rate:

@@ -22,7 +22,9 @@ __all__ = [
     "IsingError", "JzParams", "lib_path", "load", "ising_replica_init", "ising_replica_free",
     "ising_sync", "jarzynski_run", "jarzynski_run_ex", "jarzynski_run_batch", "jarzynski_run_plain",
     "estimator_reduce", "ising_strerror", "jz_params_default", "ising_probe",
-    "jarzynski_run_noalloc", "ising_binary_version",
+    "jarzynski_run_noalloc", "ising_binary_version", "ising_cancel", "ising_cancel_reset",
+    "jarzynski_run_resumable", "jz_cancel", "jz_server_set_log", "jz_result_json", "TuneCache",
+    "ising_autotune_cached",
 ]
 
 ISING_OK = 0
@@ -36,6 +38,7 @@ ISING_ERR_UNSUPPORTED = -7
 ISING_ERR_NOT_FOUND = -8
 ISING_ERR_PENDING = -9
 ISING_ERR_SCRATCH_LIMIT = -10
+ISING_ERR_CANCELLED = -11
 
 
 class JzParams(ctypes.Structure):
@@ -104,6 +107,27 @@ def load():
         "ising_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "ising_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]),
         "ising_binary_version": (ctypes.c_int, [ctypes.c_int, P(ctypes.c_int)]),
+        "ising_cancel": (ctypes.c_int, [vp]),
+        "ising_cancel_reset": (ctypes.c_int, [vp]),
+        "jarzynski_run_resumable": (ctypes.c_int, [vp, P(JzParams), ctypes.c_int, ctypes.c_int,
+                                                   P(ctypes.c_int), vp, vp]),
+        "jz_cancel": (ctypes.c_int, [vp, ctypes.c_uint64]),
+        "jz_server_set_log": (ctypes.c_int, [vp, ctypes.c_char_p]),
+        "jz_result_json": (ctypes.c_int, [ctypes.c_uint64, P(JzParams), P(JzResult),
+                                          ctypes.c_char_p, ctypes.c_size_t]),
+        "jz_tune_cache_create": (ctypes.c_int, [P(vp)]),
+        "jz_tune_cache_free": (None, [vp]),
+        "jz_tune_cache_load": (ctypes.c_int, [vp, ctypes.c_char_p]),
+        "jz_tune_cache_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
+        "jz_tune_cache_put": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int]),
+        "jz_tune_cache_get": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             P(ctypes.c_int)]),
+        "jz_tune_cache_size": (ctypes.c_int, [vp, P(ctypes.c_int)]),
+        "ising_autotune_cached": (ctypes.c_int, [vp, vp, P(JzParams), P(ctypes.c_int),
+                                                 P(ctypes.c_int)]),
         "ising_set_threads": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_int]),
         "ising_autotune": (ctypes.c_int, [vp, P(JzParams), P(ctypes.c_int)]),
@@ -337,3 +361,100 @@ def jz_server_work(server, job_id: int, work_out) -> None:
 
 def jz_server_free(server) -> None:
     load().jz_server_free(server)
+
+
+def ising_cancel(ctx) -> None:
+    """Set the context's cancel flag: run calls refuse new work until reset."""
+    _check(load().ising_cancel(ctx), "ising_cancel")
+
+
+def ising_cancel_reset(ctx) -> None:
+    _check(load().ising_cancel_reset(ctx), "ising_cancel_reset")
+
+
+def jarzynski_run_resumable(ctx, params: JzParams, steps_per_segment: int, work_io, spins_io,
+                            k_done: int = 0, max_segments: int = 0):
+    """Run the protocol from step k_done in segments, testing the cancel flag
+    between them.  Returns (status, k_done): status ISING_OK (finished),
+    ISING_ERR_PENDING (max_segments reached) or ISING_ERR_CANCELLED; other
+    errors raise IsingError."""
+    k = ctypes.c_int(int(k_done))
+    rc = load().jarzynski_run_resumable(ctx, ctypes.byref(params), int(steps_per_segment),
+                                        int(max_segments), ctypes.byref(k), _ptr(work_io),
+                                        _ptr(spins_io))
+    if rc not in (ISING_OK, ISING_ERR_PENDING, ISING_ERR_CANCELLED):
+        _check(rc, "jarzynski_run_resumable")
+    return rc, k.value
+
+
+def jz_cancel(server, job_id: int) -> None:
+    _check(load().jz_cancel(server, int(job_id)), "jz_cancel")
+
+
+def jz_server_set_log(server, path) -> None:
+    """Append one JSON line per finished job to `path` (None: stop logging)."""
+    _check(load().jz_server_set_log(server, None if path is None else str(path).encode()),
+           "jz_server_set_log")
+
+
+def jz_result_json(job_id: int, params: JzParams, result: JzResult) -> str:
+    buf = ctypes.create_string_buffer(1024)
+    n = load().jz_result_json(int(job_id), ctypes.byref(params), ctypes.byref(result), buf, 1024)
+    if n < 0:
+        _check(n, "jz_result_json")
+    return buf.value.decode()
+
+
+class TuneCache:
+    """The persisted autotune cache (see include/isingjz.h); host only."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check(load().jz_tune_cache_create(ctypes.byref(h)), "jz_tune_cache_create")
+        self.handle = h.value
+
+    def close(self):
+        if self.handle:
+            load().jz_tune_cache_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, path):
+        _check(load().jz_tune_cache_load(self.handle, str(path).encode()), "jz_tune_cache_load")
+
+    def save(self, path):
+        _check(load().jz_tune_cache_save(self.handle, str(path).encode()), "jz_tune_cache_save")
+
+    def put(self, gpu, d, L, L_t, n_replica, n_traj, cta_threads):
+        _check(load().jz_tune_cache_put(self.handle, gpu.encode(), int(d), int(L), int(L_t),
+                                        int(n_replica), int(n_traj), int(cta_threads)),
+               "jz_tune_cache_put")
+
+    def get(self, gpu, d, L, L_t, n_replica, n_traj):
+        """The cached CTA size, or None on a miss."""
+        t = ctypes.c_int()
+        rc = load().jz_tune_cache_get(self.handle, gpu.encode(), int(d), int(L), int(L_t),
+                                      int(n_replica), int(n_traj), ctypes.byref(t))
+        if rc == ISING_ERR_NOT_FOUND:
+            return None
+        _check(rc, "jz_tune_cache_get")
+        return t.value
+
+    def __len__(self):
+        n = ctypes.c_int()
+        _check(load().jz_tune_cache_size(self.handle, ctypes.byref(n)), "jz_tune_cache_size")
+        return n.value
+
+
+def ising_autotune_cached(ctx, cache: TuneCache, params: JzParams):
+    """(CTA size, hit): the cached choice for the context's GPU, else a fresh
+    ising_autotune whose choice is stored in the cache."""
+    t, hit = ctypes.c_int(), ctypes.c_int()
+    _check(load().ising_autotune_cached(ctx, cache.handle, ctypes.byref(params), ctypes.byref(t),
+                                        ctypes.byref(hit)), "ising_autotune_cached")
+    return t.value, bool(hit.value)

@@ -347,6 +347,8 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
         (rc = ensure(ctx, ctx->spins, (size_t)n_spin_traj * V)))
         return rc;
 
+    const Range nv_group("jz run group");
+    nvtxRangePushA("jz tables");   // host FP64 threshold tables (popped after the loop)
     ctx->h_tcut.assign(n_tcut, 0);
     ctx->h_jobs.assign(n_jobs, jz::JobDesc{});
     size_t off = 0;
@@ -383,6 +385,7 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
         cta += (p.n_traj + sh.teams - 1) / sh.teams;
         traj_off += p.n_traj;
     }
+    nvtxRangePop();
     cudaStream_t st = ctx->stream;
     if ((rc = cuda_err(cudaMemcpyAsync(ctx->tcut.ptr, ctx->h_tcut.data(),
                                        n_tcut * sizeof(uint32_t), cudaMemcpyHostToDevice, st))))
@@ -445,6 +448,7 @@ int run_jobs(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const* 
              int8_t* const* spins)
 {
     if (!ctx || !jobs || !outs || n_jobs < 1) return ISING_ERR_ARG;
+    if (ctx->cancel.load()) return ISING_ERR_CANCELLED;
     ctx->k_open = true;   // a new run call: its first launch opens the timed span
     ctx->k_timed = false;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
@@ -483,6 +487,7 @@ int run_jobs(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const* 
         auto& idx = groups[key];
         // keep the per-launch job table within bounds
         for (size_t s = 0; s < idx.size(); s += jz::kMaxJobsPerLaunch) {
+            if (ctx->cancel.load()) return ISING_ERR_CANCELLED;
             std::vector<int> part(idx.begin() + s,
                                   idx.begin() + std::min(idx.size(), s + jz::kMaxJobsPerLaunch));
             int rc = run_group(ctx, jobs, part, outs, spins, outs_dev, spins_dev, nullptr);
@@ -525,6 +530,9 @@ int ising_replica_init(ising_ctx** out, int device, size_t hbm_budget_bytes, voi
     if (!ctx) return ISING_ERR_NOMEM;
     ctx->device = device;
     ctx->budget = hbm_budget_bytes;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) ctx->gpu_name = prop.name;
+    else cudaGetLastError();
     if (cuda_stream) {
         ctx->stream = (cudaStream_t)cuda_stream;
     } else {
@@ -617,6 +625,8 @@ int ising_set_threads(ising_ctx* ctx, int d, int L, int L_t, int threads)
 int ising_autotune(ising_ctx* ctx, const jz_params* p, int* threads)
 {
     if (!ctx || !p) return ISING_ERR_ARG;
+    if (ctx->cancel.load()) return ISING_ERR_CANCELLED;
+    const Range nv("jz autotune");
     int rc = check_params(p);
     if (rc) return rc;
     if (p->update == 1) {   // Swendsen-Wang: a fixed CTA per trajectory, nothing to tune
@@ -685,6 +695,7 @@ int jarzynski_run_segment(ising_ctx* ctx, const jz_params* p, int k_begin, int k
                           int64_t* work_io, int8_t* spins_io)
 {
     if (!ctx || !p || !work_io || !spins_io) return ISING_ERR_ARG;
+    if (ctx->cancel.load()) return ISING_ERR_CANCELLED;
     ctx->k_open = true;
     ctx->k_timed = false;
     int rc = check_params(p);
@@ -702,6 +713,7 @@ int jarzynski_run_plain(ising_ctx* ctx, const jz_params* p, int64_t* work_int_ou
                         int8_t* spins_out)
 {
     if (!ctx || !p || !work_int_out) return ISING_ERR_ARG;
+    if (ctx->cancel.load()) return ISING_ERR_CANCELLED;
     int rc = check_params(p);
     if (rc) return rc;
     if (p->update != 0 || (p->protocol == 2 && p->d == 3) || nrep_of(*p) != 2 || p->whole)
@@ -726,6 +738,7 @@ int jarzynski_run_plain(ising_ctx* ctx, const jz_params* p, int64_t* work_int_ou
     const jz::PhiloxKeys K = key_schedule(p->seed);
     long long* w = w_dev ? (long long*)work_int_out : (long long*)ctx->work.ptr;
     for (int i = 0; i < p->n_traj; ++i) {
+        if (ctx->cancel.load()) return ISING_ERR_CANCELLED;
         int8_t* s = s_dev ? spins_out + (size_t)i * V
                           : (int8_t*)ctx->spins.ptr + (spins_out ? (size_t)i * V : 0);
         if ((rc = cuda_err(jz::plain_trajectory(p->d, g, K, p->l, p->direction, p->n_step,
@@ -757,6 +770,7 @@ int estimator_reduce(ising_ctx* ctx, const int64_t* work_int, int n_traj, double
     if (n_jack_bins < 1 || n_jack_bins > jz::kMaxJackBlocksHost) return ISING_ERR_ARG;
     if (!(beta >= 0.0 && std::isfinite(beta))) return ISING_ERR_ARG;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
+    const Range nv("jz estimator");
     int rc;
     const long long* src = (const long long*)work_int;
     cudaStream_t st = ctx->stream;
@@ -818,6 +832,7 @@ const char* ising_strerror(int code)
     case ISING_ERR_PENDING: return "job not finished";
     case ISING_ERR_SCRATCH_LIMIT:
         return "protocol too long for the fixed scratch of jarzynski_run_noalloc";
+    case ISING_ERR_CANCELLED: return "cancelled";
     default: return "unknown error";
     }
 }

@@ -4,9 +4,13 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <map>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -61,9 +65,19 @@ struct ising_ctx {
     cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;
     bool k_open = false;    // the next launch is the call's first
     bool k_timed = false;   // a run call has recorded both events
+    std::atomic<int> cancel{0};   // ising_cancel: run calls refuse new work while set
+    std::string gpu_name;         // device name (autotune cache key)
 };
 
 namespace jzh {
+// NVTX range around a host phase (visible in Nsight timelines; a no-op
+// unless a tool is attached).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 int ensure(ising_ctx* ctx, DevBuf& b, size_t bytes);
 int is_device_ptr(const void* p);
 int check_params(const jz_params* p);

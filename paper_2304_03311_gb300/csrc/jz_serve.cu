@@ -13,6 +13,7 @@
 
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -33,6 +34,7 @@ struct Job {
     jz_params p{};
     size_t need = 0;          // device bytes while running
     bool done = false;
+    bool cancel = false;      // jz_cancel on a running job: discard its results
     jz_result res{};
     std::vector<int64_t> work;
 };
@@ -92,11 +94,28 @@ struct jz_server {
     bool stop = false;
     std::thread worker;
     Clock::time_point t0;
+    FILE* log = nullptr;      // jz_server_set_log: one JSON line per finished job
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
     void run();
     int launch(Slot& s, Job& j);
+    void finish(uint64_t id, Job& j);
 };
+
+// Marks a job finished (lock held): wakes its waiters and logs its line.
+void jz_server::finish(uint64_t id, Job& j)
+{
+    j.done = true;
+    if (log) {
+        char line[1024];
+        if (jz_result_json(id, &j.p, &j.res, line, sizeof line) > 0) {
+            std::fputs(line, log);
+            std::fputc('\n', log);
+            std::fflush(log);
+        }
+    }
+    cv_done.notify_all();
+}
 
 // Enqueues one job on its slot's stream.  Called without the lock; the job
 // record is stable (held by unique_ptr) and not touched by other threads
@@ -178,7 +197,10 @@ void jz_server::run()
                 continue;
             }
             Job& j = *jobs[s.job];
-            if (e == cudaSuccess) {
+            const Range nv("jz retire");
+            if (e == cudaSuccess && j.cancel) {
+                j.res.status = ISING_ERR_CANCELLED;
+            } else if (e == cudaSuccess) {
                 j.res.status = ISING_OK;
                 j.res.log_ratio = s.h_est[0];
                 j.res.delta_S2 = s.h_est[1];
@@ -189,20 +211,19 @@ void jz_server::run()
                 j.res.status = ISING_ERR_CUDA;
             }
             j.res.done_s = now();
-            j.done = true;
             used -= j.need;
             s.busy = false;
-            cv_done.notify_all();
+            finish(s.job, j);
         }
         // admit in arrival order while a slot and the budget allow
         while (!queue.empty() && !stop) {
-            Job& j = *jobs[queue.front()];
+            const uint64_t head = queue.front();
+            Job& j = *jobs[head];
             if (j.need > budget) {
                 j.res.status = ISING_ERR_NOMEM;
                 j.res.start_s = j.res.done_s = now();
-                j.done = true;
                 queue.pop_front();
-                cv_done.notify_all();
+                finish(head, j);
                 continue;
             }
             Slot* free_slot = nullptr;
@@ -219,17 +240,20 @@ void jz_server::run()
             free_slot->job = id;
             j.res.start_s = now();
             lk.unlock();
-            const int rc = launch(*free_slot, j);
+            int rc;
+            {
+                const Range nv("jz admit");
+                rc = launch(*free_slot, j);
+            }
             lk.lock();
             if (rc) {
                 cudaStreamSynchronize(free_slot->stream);
                 cudaGetLastError();
                 j.res.status = rc;
                 j.res.done_s = now();
-                j.done = true;
                 used -= j.need;
                 free_slot->busy = false;
-                cv_done.notify_all();
+                finish(id, j);
             } else {
                 any_busy = true;
             }
@@ -342,12 +366,50 @@ int jz_server_work(jz_server* s, uint64_t job_id, int64_t* work_out)
     return ISING_OK;
 }
 
+int jz_cancel(jz_server* s, uint64_t job_id)
+{
+    if (!s) return ISING_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return ISING_ERR_NOT_FOUND;
+    Job& j = *it->second;
+    if (j.done) return ISING_OK;   // a finished job keeps its result
+    for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+        if (*q == job_id) {       // still queued: dropped before admission
+            s->queue.erase(q);
+            j.res.status = ISING_ERR_CANCELLED;
+            j.res.start_s = j.res.done_s = s->now();
+            s->finish(job_id, j);
+            return ISING_OK;
+        }
+    j.cancel = true;               // on the device: runs to its end, results discarded
+    return ISING_OK;
+}
+
+int jz_server_set_log(jz_server* s, const char* path)
+{
+    if (!s) return ISING_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->log) std::fclose(s->log);
+    s->log = nullptr;
+    if (!path) return ISING_OK;
+    s->log = std::fopen(path, "a");
+    return s->log ? ISING_OK : ISING_ERR_NOT_FOUND;
+}
+
 void jz_server_free(jz_server* s)
 {
     if (!s) return;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
+        // queued jobs are dropped: their waiters see ISING_ERR_CANCELLED
+        for (uint64_t id : s->queue) {
+            Job& j = *s->jobs[id];
+            j.res.status = ISING_ERR_CANCELLED;
+            j.res.start_s = j.res.done_s = s->now();
+            s->finish(id, j);
+        }
         s->queue.clear();
     }
     s->cv_work.notify_all();
@@ -362,6 +424,7 @@ void jz_server_free(jz_server* s)
         if (t.h_tcut) cudaFreeHost(t.h_tcut);
         if (t.h_work) cudaFreeHost(t.h_work);
     }
+    if (s->log) std::fclose(s->log);
     delete s;
 }
 

@@ -60,3 +60,20 @@ def test_recorded_traffic_stands_only_for_unchanged_sources(tmp_path, monkeypatc
     monkeypatch.setattr(bench, "kernel_source_hash", lambda k: real_hash)
     assert bench.traffic_from_profile("traj_kernel", "w") is None
     assert bench.traffic_from_profile("traj_kernel", "other") is None
+
+
+def test_pulls_of_identical_and_shifted_scans():
+    ref = [(0.1 * l, 0.01) for l in range(31)]
+    same = bench.pulls(ref, ref)
+    assert same["max_abs_pull"] == 0 and same["chi2_per_l"] == 0 and same["passes"]
+    # every l high by 4 combined standard deviations: the check must fail
+    shifted = [(v + 4 * 0.01 * 2 ** 0.5, e) for v, e in ref]
+    bad = bench.pulls(shifted, ref)
+    assert abs(bad["mean_pull"] - 4) < 1e-9 and not bad["passes"]
+
+
+def test_fractions_against_the_three_ceilings():
+    ceil = {"derived_int_ops_per_s": 40e12, "probe_mix_int_ops_per_s": 36e12,
+            "philox_update_ceiling_per_s": 2e12}
+    f = bench.fractions(20e12, 1e12, ceil)
+    assert f == {"frac_derived": 0.5, "frac_probe": 20 / 36, "frac_philox_ceiling": 0.5}

@@ -106,3 +106,61 @@ def test_dead_rank_is_reported_missing(tmp_path):
     out = _run(2, 1, tmp_path)
     assert 1 not in out
     assert "missing" in out[0]
+
+
+def _bench_worker(rank, world, port, out_dir, die_rank):
+    """The benchmark's own exchange (bench.exchange_work) on its weak-scaling
+    layout: rank r runs trajectories [r n, (r+1) n) of every l; stand-in work
+    values encode (global trajectory, l) so the gathered order is checkable."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=10))
+    w = bench.workload_for(2, rank, traj_per_l=5)
+    arrays = [np.arange(j.traj0, j.traj0 + j.n_traj, dtype=np.int64) * 1000 + j.l for j in w.jobs]
+    if rank == die_rank:
+        os._exit(0)
+    result = {}
+    try:
+        merged = bench.exchange_work(arrays, w.jobs, world, None)
+        result["merged"] = [m.tolist() for m in merged]
+    except shard.MissingShardError as exc:
+        result["missing"] = str(exc)
+    with open(os.path.join(out_dir, f"rank{rank}.json"), "w") as f:
+        json.dump(result, f)
+    if "missing" not in result:
+        dist.destroy_process_group()
+
+
+def _run_bench(world, die_rank, tmp_path):
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    procs = [ctx.Process(target=_bench_worker, args=(r, world, port, str(tmp_path), die_rank))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        if p.is_alive():
+            p.kill()
+            pytest.fail("a rank hung")
+    return {r: json.loads((tmp_path / f"rank{r}.json").read_text())
+            for r in range(world) if (tmp_path / f"rank{r}.json").exists()}
+
+
+def test_bench_exchange_gathers_every_l_in_global_order(tmp_path):
+    out = _run_bench(2, -1, tmp_path)
+    for r in (0, 1):
+        merged = out[r]["merged"]
+        assert len(merged) == 31
+        for l, m in enumerate(merged):
+            assert m == [t * 1000 + l for t in range(10)]
+
+
+def test_bench_exchange_reports_a_dead_rank(tmp_path):
+    out = _run_bench(2, 1, tmp_path)
+    assert 1 not in out
+    assert "missing" in out[0]
