@@ -108,13 +108,14 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
     return make_uint4(c0, c1, c2, c3);
 }
 
-// The same block with round 0's product M1 * c2 supplied (hi1, lo1): counter
-// word 2 is the trajectory index, fixed for a whole trajectory.
-__device__ __forceinline__ uint4 philox_r0(uint32_t c0, uint32_t c1, uint32_t hi1, uint32_t lo1,
+// One block with round 0's two products supplied: p0 = M0 * c0 and
+// (hi1, lo1) = M1 * c2.  Counter word 2 is the trajectory index, fixed for a
+// whole trajectory, and successive blocks of a thread step c0 by a constant,
+// so callers form p0 by 64-bit additions instead of a wide multiply.
+__device__ __forceinline__ uint4 philox_p0(uint64_t p0, uint32_t c1, uint32_t hi1, uint32_t lo1,
                                            uint32_t c3, const PhiloxKeys& K)
 {
-    const uint64_t p0 = (uint64_t)kPhiloxM0 * c0;
-    c0 = hi1 ^ c1 ^ K.k0[0];
+    uint32_t c0 = hi1 ^ c1 ^ K.k0[0];
     uint32_t c2 = (uint32_t)(p0 >> 32) ^ c3 ^ K.k1[0];
     c1 = lo1;
     c3 = (uint32_t)p0;
@@ -130,6 +131,13 @@ __device__ __forceinline__ uint4 philox_r0(uint32_t c0, uint32_t c1, uint32_t hi
         c2 = n2;
     }
     return make_uint4(c0, c1, c2, c3);
+}
+
+// The same block with only round 0's product M1 * c2 supplied (hi1, lo1).
+__device__ __forceinline__ uint4 philox_r0(uint32_t c0, uint32_t c1, uint32_t hi1, uint32_t lo1,
+                                           uint32_t c3, const PhiloxKeys& K)
+{
+    return philox_p0((uint64_t)kPhiloxM0 * c0, c1, hi1, lo1, c3, K);
 }
 
 // The last stage of the FP64 estimator of one job (Appendix A, eq.

@@ -287,11 +287,27 @@ struct Traj {
                     bulk_item(own_b, oth, w, t == Lt - 1 ? wrap_up : rw, (pc ^ t) & 1, c0, sweep,
                               c3);
             } else {
-                // t keeps its parity: the x-shift direction is fixed for the row set
+                // t keeps its parity: the x-shift direction is fixed for the row set.
+                // Each row's update runs beside the Philox blocks of the next row
+                // (they do not depend on spins), so one warp's instruction stream
+                // mixes the wide multiplies with the update's logic; the blocks'
+                // round-0 products M0 c0 advance by additions.
                 const int p = (pc ^ t0) & 1;
-                for (; t < Lt - TS; t += TS, w += stride, c0 += cstride)
-                    bulk_item(own_b, oth, w, rw, p, c0, sweep, c3);
-                if (t < Lt) bulk_item(own_b, oth, w, t == Lt - 1 ? wrap_up : rw, p, c0, sweep, c3);
+                if (t < Lt) {
+                    uint64_t p0 = (uint64_t)kPhiloxM0 * c0;
+                    const uint64_t dp = (uint64_t)kPhiloxM0 * cstride;
+                    uint4 ua = philox_p0(p0, sweep, hi1, lo1, c3, K);
+                    uint4 ub = philox_p0(p0 + kPhiloxM0, sweep, hi1, lo1, c3, K);
+                    for (; t < Lt - TS; t += TS, w += stride, c0 += cstride) {
+                        p0 += dp;
+                        const uint4 na = philox_p0(p0, sweep, hi1, lo1, c3, K);
+                        const uint4 nb = philox_p0(p0 + kPhiloxM0, sweep, hi1, lo1, c3, K);
+                        bulk_update(own_b, oth, w, rw, p, ua, ub);
+                        ua = na;
+                        ub = nb;
+                    }
+                    bulk_update(own_b, oth, w, t == Lt - 1 ? wrap_up : rw, p, ua, ub);
+                }
             }
         }
     }
