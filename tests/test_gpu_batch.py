@@ -129,3 +129,37 @@ def test_reduced_config4_in_one_launch(ctx):
         jz.jz_plan_free(plan)
     for j, o in list(zip(jobs, outs))[::7]:
         np.testing.assert_array_equal(o.cpu().numpy(), _single(ctx, j))
+
+
+def test_full_config4_plan_one_trajectory_per_shape(ctx):
+    """The uneven benchmark batch at full size (214 jobs, 9 lattice shapes, one
+    persistent CUDA-graph launch with the autotuned CTA size, as the benchmark
+    runs it): for every shape, one trajectory of its shortest job against the
+    oracle, and the batched estimator of every job against the oracle's."""
+    w = wl.config4()
+    outs = [torch.empty(j.n_traj, dtype=torch.int64, device="cuda") for j in w.jobs]
+    est = torch.zeros(3 * len(w.jobs), dtype=torch.float64, device="cuda")
+    plan = jz.jz_plan_create(ctx, [_params(j) for j in w.jobs], outs, est, 0)
+    try:
+        jz.jz_plan_launch(plan)
+        jz.ising_sync(ctx)
+    finally:
+        jz.jz_plan_free(plan)
+    res = [o.cpu().numpy() for o in outs]
+    shapes = {}
+    for i, j in enumerate(w.jobs):
+        key = (j.d, j.L)
+        if key not in shapes or j.n_step < w.jobs[shapes[key]].n_step:
+            shapes[key] = i
+    assert len(shapes) == 9
+    for (d, L), i in sorted(shapes.items()):
+        j = w.jobs[i]
+        ti = j.n_traj // 2
+        Wo, _ = oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, 1, j.seed,
+                           n_therm=j.n_therm, direction=j.direction, traj0=j.traj0 + ti)
+        assert res[i][ti] == Wo[0], (d, L, j.l)
+    e = est.cpu().numpy().reshape(-1, 3)
+    for j, W, (lr, ds, err) in zip(w.jobs, res, e):
+        ref_ds, ref_err = oest.delta_s2_with_error(W, j.beta, j.n_step, j.direction, 32)
+        assert abs(ds - ref_ds) <= 1e-12 * max(abs(ds), abs(ref_ds)) + 1e-14
+        assert abs(err - ref_err) <= 1e-10 * max(err, ref_err) + 1e-14

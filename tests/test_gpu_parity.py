@@ -284,11 +284,15 @@ def test_full_config1_sampled(ctx):
 
 
 def test_full_config2_sampled(ctx):
-    """The 31-transformation scan at full size, one launch as the benchmark runs it."""
+    """The 31-transformation scan at full size, one launch as the benchmark
+    runs it: one trajectory of every l (the first and last trajectory at the
+    two ends of the scan) against the oracle, and the estimator of every l."""
     w = wl.config2()
     res = _run_workload(ctx, w)
     _check_properties(w, res)
-    _check_sampled(w, res, [(0, 0), (15, 8191), (30, 16383)])
+    picks = [(l, (l * 523) % 16384) for l in range(31)]
+    picks[-1] = (30, 16383)
+    _check_sampled(w, res, picks)
     for job, W in zip(w.jobs, res):
         _, ds, err = jz.estimator_reduce(ctx, torch.from_numpy(W).cuda(), job.n_traj,
                                          job.beta, job.n_step, 1, 32)
@@ -298,16 +302,31 @@ def test_full_config2_sampled(ctx):
 
 
 def test_full_config3_sampled(ctx):
+    """The 3D slab scan at full size: one trajectory of every l against the oracle."""
     w = wl.config3()
     res = _run_workload(ctx, w)
     _check_properties(w, res)
-    _check_sampled(w, res, [(0, 0), (7, 4095)])
+    _check_sampled(w, res, [(i, (i * 1013) % 4096) for i in range(7)] + [(7, 4095)])
+
+
+@pytest.mark.parametrize("l", [0, 30])
+def test_full_shape_spins_match_oracle(ctx, l):
+    """Final spins at the benchmark's full 2D shape and protocol (L = L_t = 64,
+    N = 1000 x 2 sweeps, 1000 thermalisation sweeps) for two trajectories."""
+    job = wl.config2().jobs[l].with_(n_traj=2, traj0=9000)
+    Wg, Sg = gpu_run(ctx, job)
+    Wo, So = oracle_run(job)
+    np.testing.assert_array_equal(Wg, Wo)
+    np.testing.assert_array_equal(Sg, So)
 
 
 @pytest.mark.parametrize("job", [
     wl.Job(2, 64, 4096, BC2, 5, 2, 1, 6, seed=21, n_therm=3),           # 262 KB per lattice
     wl.Job(3, 12, 1280, BC3, 4, 2, 1, 4, seed=22, n_therm=2, direction=-1),
-], ids=["2d_L64_T4096", "3d_L12_T1280"])
+    # the paper's-style 2D L = 256, L_t = 8L (512 KB per lattice): 152 resident
+    # lattices exceed the part of L2 they keep, so their spins stream from DRAM
+    wl.Job(2, 256, 2048, BC2, 100, 2, 1, 3, seed=24, n_therm=2),
+], ids=["2d_L64_T4096", "3d_L12_T1280", "2d_L256_T2048"])
 def test_lattice_beyond_shared_memory_runs_from_hbm(ctx, job):
     """Replica lattices too large for one CTA's shared memory keep their spins
     in an HBM slice per CTA; the bits stay those of the oracle."""

@@ -138,3 +138,14 @@ def test_timeout_unknown_and_invalid(ctx):
         assert e.value.code == jz.ISING_ERR_ODD_EXTENT
     finally:
         jz.jz_server_free(server)     # waits for the long job, drops nothing queued
+
+
+def test_alone_reference_matches_oracle(alone):
+    """The mix's "alone" results (each job run by itself through
+    jarzynski_run_ex) are the oracle's bits, so the mix-invariance tests
+    compare the server against the oracle too."""
+    import oracle
+    for j in _mix():
+        Wo, _ = oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj, j.seed,
+                           n_therm=j.n_therm, direction=j.direction, traj0=j.traj0)
+        np.testing.assert_array_equal(alone[j][0], Wo)
