@@ -746,7 +746,9 @@ def run_ours(args):
             plain = plain_baseline(jz, torch, ctx, dev, w, value, args.plain)
         if args.bias_traj > 0:
             bias = bias_and_cost(jz, torch, ctx, stream, dev, w, cfun, kernel_ms, args)
-    elif args.plain > 0 and not sw:
+    elif args.plain > 0 and all(j.update == 0 and j.n_replica == 2 and not j.whole and
+                                (j.protocol == 1 or j.d == 2) for j in w.jobs):
+        # the plain form serves Metropolis, two replicas and moving ends only
         plain = plain_baseline(jz, torch, ctx, dev, w, value, args.plain)
 
     cpu = None

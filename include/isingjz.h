@@ -472,6 +472,17 @@ int ising_probe(int device, int kind, double* rate);
  * device, or no code in the library loads on it). */
 int ising_binary_version(int device, int* version);
 
+/* Debug build (libisingjz_debug.so, compiled with bounds checks; the paper
+ * has no counterpart).  Every lattice access of the trajectory kernels and
+ * every cluster-label and spin-bit access of the Swendsen-Wang kernel checks
+ * its index; an index outside its array is recorded in a device status word
+ * and the access is skipped, so the kernel neither faults nor reads another
+ * lattice.  *sites receives the OR of the check sites that failed since the
+ * last clear (0 = none), *index one failing index; clear != 0 resets the
+ * words (on the current device).  The release library returns
+ * ISING_ERR_UNSUPPORTED.  Errors: ISING_ERR_ARG, ISING_ERR_CUDA. */
+int ising_bounds_status(unsigned int* sites, unsigned int* index, int clear);
+
 /* Human-readable text for an error code (static storage). */
 const char* ising_strerror(int code);
 

@@ -17,6 +17,7 @@ import ctypes
 import os
 
 from .build import LIB as _LIB_PATH
+from .build import LIB_DEBUG as _LIB_DEBUG_PATH
 
 __all__ = [
     "IsingError", "JzParams", "lib_path", "load", "ising_replica_init", "ising_replica_free",
@@ -24,7 +25,7 @@ __all__ = [
     "estimator_reduce", "ising_strerror", "jz_params_default", "ising_probe",
     "jarzynski_run_noalloc", "ising_binary_version", "ising_cancel", "ising_cancel_reset",
     "jarzynski_run_resumable", "jz_cancel", "jz_server_set_log", "jz_result_json", "TuneCache",
-    "ising_autotune_cached",
+    "ising_autotune_cached", "ising_bounds_status", "use_debug_library",
 ]
 
 ISING_OK = 0
@@ -75,6 +76,16 @@ def lib_path() -> str:
     return _LIB_PATH
 
 
+def use_debug_library() -> None:
+    """Bind to the bounds-checked build libisingjz_debug.so (build it with
+    ``build.build(debug=True)``) instead of the release library.  Must be
+    called before the first call into the library in this process."""
+    global _LIB_PATH
+    if _lib is not None:
+        raise RuntimeError("the release library is already loaded in this process")
+    _LIB_PATH = _LIB_DEBUG_PATH
+
+
 def load():
     """Load libisingjz.so (build it with ``paper_2304_03311_gb300.build.build()``)."""
     global _lib
@@ -107,6 +118,7 @@ def load():
         "ising_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "ising_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P(ctypes.c_double)]),
         "ising_binary_version": (ctypes.c_int, [ctypes.c_int, P(ctypes.c_int)]),
+        "ising_bounds_status": (ctypes.c_int, [P(ctypes.c_uint), P(ctypes.c_uint), ctypes.c_int]),
         "ising_cancel": (ctypes.c_int, [vp]),
         "ising_cancel_reset": (ctypes.c_int, [vp]),
         "jarzynski_run_resumable": (ctypes.c_int, [vp, P(JzParams), ctypes.c_int, ctypes.c_int,
@@ -458,3 +470,11 @@ def ising_autotune_cached(ctx, cache: TuneCache, params: JzParams):
     _check(load().ising_autotune_cached(ctx, cache.handle, ctypes.byref(params), ctypes.byref(t),
                                         ctypes.byref(hit)), "ising_autotune_cached")
     return t.value, bool(hit.value)
+
+
+def ising_bounds_status(clear: bool = False):
+    """(failed check sites, one failing index) of the bounds-checked build."""
+    a, b = ctypes.c_uint(), ctypes.c_uint()
+    _check(load().ising_bounds_status(ctypes.byref(a), ctypes.byref(b), int(bool(clear))),
+           "ising_bounds_status")
+    return a.value, b.value

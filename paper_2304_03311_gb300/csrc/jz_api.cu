@@ -895,6 +895,27 @@ int noalloc_scratch_address(void** out)
 }
 }  // namespace
 
+extern "C" int ising_bounds_status(unsigned int* sites, unsigned int* index, int clear)
+{
+#ifdef JZ_BOUNDS_CHECK
+    if (!sites || !index) return ISING_ERR_ARG;
+    unsigned int a[2], b[2], c[2];
+    int rc;
+    if ((rc = cuda_err(jz::bounds_status_traj(a, clear != 0))) ||
+        (rc = cuda_err(jz::bounds_status_batch(b, clear != 0))) ||
+        (rc = cuda_err(jz::bounds_status_sw(c, clear != 0))))
+        return rc;
+    *sites = a[0] | b[0] | c[0];
+    *index = a[0] ? a[1] : b[0] ? b[1] : c[1];
+    return ISING_OK;
+#else
+    (void)sites;
+    (void)index;
+    (void)clear;
+    return ISING_ERR_UNSUPPORTED;
+#endif
+}
+
 extern "C" int ising_binary_version(int device, int* version)
 {
     if (!version) return ISING_ERR_ARG;

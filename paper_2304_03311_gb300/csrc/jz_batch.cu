@@ -154,4 +154,20 @@ cudaError_t launch_estimator_batch(const EstJob* jobs, int n_jobs, double* out, 
     return cudaGetLastError();
 }
 
+cudaError_t bounds_status_batch(unsigned int out[2], bool clear)
+{
+#ifdef JZ_BOUNDS_CHECK
+    cudaError_t e = cudaMemcpyFromSymbol(out, jz_bounds_status, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess && clear) {
+        const unsigned int z[2] = {0u, 0u};
+        e = cudaMemcpyToSymbol(jz_bounds_status, z, sizeof z);
+    }
+    return e;
+#else
+    out[0] = out[1] = 0u;
+    (void)clear;
+    return cudaSuccess;
+#endif
+}
+
 }  // namespace jz

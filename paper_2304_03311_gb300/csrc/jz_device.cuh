@@ -17,6 +17,25 @@ namespace jz {
 
 constexpr int kMaxJobsPerLaunch = 4096;
 
+// Bounds-checked builds (compiled with -DJZ_BOUNDS_CHECK: the debug library).
+// Every lattice access of the trajectory kernels and every label / spin-bit
+// access of the Swendsen-Wang kernel checks its index against its array; an
+// index outside it sets bit `site` of this translation unit's status word
+// (entry 0; entry 1 keeps one offending index) and the access is skipped.
+// Release builds compile each check to nothing.
+#ifdef JZ_BOUNDS_CHECK
+static __device__ unsigned int jz_bounds_status[2];
+__device__ __forceinline__ bool in_bounds(long long i, long long n, int site)
+{
+    if (i >= 0 && i < n) return true;
+    atomicOr(&jz_bounds_status[0], 1u << site);
+    jz_bounds_status[1] = (unsigned int)i;
+    return false;
+}
+#else
+__device__ __forceinline__ bool in_bounds(long long, long long, int) { return true; }
+#endif
+
 // Philox4x32-10 round constants and Weyl key increments (Salmon, Moraes, Dror
 // and Shaw, SC'11).
 constexpr uint32_t kPhiloxM0 = 0xD2511F53u;

@@ -34,6 +34,12 @@ int sw_cta_threads(int D);
 cudaError_t launch_sw(int D, const Geom& g, const PhiloxKeys& K, const JobDesc* jobs,
                       int n_jobs, long long n_cta, cudaStream_t st, uint32_t* gS = nullptr);
 double run_probe(int kind, int device);
+// Status words of the bounds-checked build, one per translation unit with
+// kernels (zeros in release builds): [0] = check sites that saw an index
+// outside their array, [1] = one such index; clear resets them.
+cudaError_t bounds_status_traj(unsigned int out[2], bool clear);
+cudaError_t bounds_status_batch(unsigned int out[2], bool clear);
+cudaError_t bounds_status_sw(unsigned int out[2], bool clear);
 cudaError_t plain_trajectory(int D, const Geom& g, const PhiloxKeys& K, int l, int dir,
                              int n_step, int n_sweep, int n_therm, uint32_t traj,
                              const uint32_t tb[4], const uint32_t* tcut, int8_t* s,

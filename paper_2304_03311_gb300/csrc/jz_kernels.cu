@@ -156,6 +156,22 @@ cudaError_t launch_traj(int D, const Geom& g, const PhiloxKeys& K, const JobDesc
                 : launch_traj_t<3, false, 0, 0>(g, K, jobs, n_jobs, n_cta, sh, st, gS);
 }
 
+cudaError_t bounds_status_traj(unsigned int out[2], bool clear)
+{
+#ifdef JZ_BOUNDS_CHECK
+    cudaError_t e = cudaMemcpyFromSymbol(out, jz_bounds_status, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess && clear) {
+        const unsigned int z[2] = {0u, 0u};
+        e = cudaMemcpyToSymbol(jz_bounds_status, z, sizeof z);
+    }
+    return e;
+#else
+    out[0] = out[1] = 0u;
+    (void)clear;
+    return cudaSuccess;
+#endif
+}
+
 cudaError_t launch_estimator(const long long* w_int, int n, double scale, int direction,
                              int n_blocks, double* out, cudaStream_t st)
 {

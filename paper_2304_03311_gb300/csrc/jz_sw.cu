@@ -114,20 +114,23 @@ __device__ __forceinline__ int glue_offset(const SwGeom& g, int r)
     return r == g.nrep - 1 ? -(g.nrep - 1) * g.VR : g.VR;
 }
 
-__device__ __forceinline__ int spin_bit(const uint32_t* sp, int i)
+// Spin bit of site i < V (checked in bounds-checked builds).
+__device__ __forceinline__ int spin_bit(const uint32_t* sp, int i, int V)
 {
-    return (sp[i >> 5] >> (i & 31)) & 1;
+    return in_bounds(i, V, 20) ? (int)((sp[i >> 5] >> (i & 31)) & 1u) : 0;
 }
 
 // Root of a with path halving: every visited node is re-pointed to its
 // grandparent.  A plain store is enough: the new parent is an ancestor of the
 // node, and a hook that a concurrent union made on that node is only ever
 // overwritten after the union has moved on to join the node's old tree.
-__device__ __forceinline__ int find_root(volatile int* lab, int a)
+__device__ __forceinline__ int find_root(volatile int* lab, int a, int V)
 {
     for (;;) {
+        if (!in_bounds(a, V, 21)) return 0;
         const int p = lab[a];
         if (p == a) return a;
+        if (!in_bounds(p, V, 22)) return 0;
         const int gp = lab[p];
         if (gp == p) return p;
         lab[a] = gp;
@@ -135,12 +138,12 @@ __device__ __forceinline__ int find_root(volatile int* lab, int a)
     }
 }
 
-__device__ __forceinline__ void merge(int* lab, int a, int b)
+__device__ __forceinline__ void merge(int* lab, int a, int b, int V)
 {
     volatile int* vl = lab;
     for (;;) {
-        a = find_root(vl, a);
-        b = find_root(vl, b);
+        a = find_root(vl, a, V);
+        b = find_root(vl, b, V);
         if (a == b) return;
         if (a < b) {
             const int t = a;
@@ -241,8 +244,9 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
                 const int lo_i = (r * g.Lt * g.Ly + y) * g.L + x;
                 const int up_s = lo_i + g.SL;
                 const int up_g = up_s + glue_offset(g, r);
-                const int s0 = 1 - 2 * spin_bit(sp, lo_i);
-                e += s0 * ((1 - 2 * spin_bit(sp, up_s)) - (1 - 2 * spin_bit(sp, up_g)));
+                const int s0 = 1 - 2 * spin_bit(sp, lo_i, g.V);
+                e += s0 * ((1 - 2 * spin_bit(sp, up_s, g.V)) -
+                           (1 - 2 * spin_bit(sp, up_g, g.V)));
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
@@ -274,7 +278,7 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
             bool ax = false, at = false, ay = false, ag = false, last = true;
             if (i < g.V) {
                 const Site s = decode<D>(i, g);
-                const int si = spin_bit(sp, i);
+                const int si = spin_bit(sp, i, g.V);
                 last = s.x == g.L - 1;
                 const int jx = last ? i + 1 - g.L : i + 1;
                 int jt = -1, jg = -1, jy = -1;
@@ -305,10 +309,10 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
                 }
                 if (D == 3) jy = s.y == g.Ly - 1 ? i + g.L - g.SL : i + g.L;
                 const uint4 u = philox_r0((uint32_t)i, (uint32_t)sw, hi1, lo1, cb, K);
-                ax = u.x < t_full && spin_bit(sp, jx) == si;
-                at = jt >= 0 && u.y < Tt && spin_bit(sp, jt) == si;
-                if (D == 3) ay = u.z < t_full && spin_bit(sp, jy) == si;
-                ag = jg >= 0 && u.w < Tg && spin_bit(sp, jg) == si;
+                ax = u.x < t_full && spin_bit(sp, jx, g.V) == si;
+                at = jt >= 0 && u.y < Tt && spin_bit(sp, jt, g.V) == si;
+                if (D == 3) ay = u.z < t_full && spin_bit(sp, jy, g.V) == si;
+                ag = jg >= 0 && u.w < Tg && spin_bit(sp, jg, g.V) == si;
             }
             const bool inw = ax && lane != 31 && !last;   // bond to the next lane's site
             const uint32_t m = __ballot_sync(0xFFFFFFFFu, inw);
@@ -343,7 +347,7 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
                 else if (dirn == 1) j = s.t == g.Lt - 1 ? i + g.SL - g.VR : i + g.SL;
                 else if (dirn == 2) j = i + g.SL + glue_offset(g, s.r);
                 else j = s.y == g.Ly - 1 ? i + g.L - g.SL : i + g.L;
-                merge(lab, i, j);
+                if (in_bounds(i, g.V, 23) && in_bounds(j, g.V, 24)) merge(lab, i, j, g.V);
             };
             auto push = [&](uint32_t m, int e) {   // m: the warp's mask of bonds
                 const int c = __popc(m);
@@ -386,7 +390,7 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
             const int i = base + lane;
             int f = 0;
             if (i < g.V) {
-                const int root = find_root((volatile int*)lab, i);
+                const int root = find_root((volatile int*)lab, i, g.V);
                 f = (int)((fz[root >> 5] >> (root & 31)) & 1u);
             }
             const uint32_t m = __ballot_sync(0xFFFFFFFFu, f);
@@ -401,7 +405,7 @@ sw_kernel(const SwGeom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
     if (so != nullptr) {
         so += local * (long long)g.V;
         for (int i = threadIdx.x; i < g.V; i += blockDim.x)
-            so[i] = spin_bit(sp, i) ? (int8_t)-1 : (int8_t)1;
+            so[i] = spin_bit(sp, i, g.V) ? (int8_t)-1 : (int8_t)1;
     }
 }
 
@@ -427,6 +431,22 @@ SwGeom make_swgeom(int D, const Geom& geo)
 }  // namespace
 
 int sw_cta_threads(int D) { return sw_threads(D); }
+
+cudaError_t bounds_status_sw(unsigned int out[2], bool clear)
+{
+#ifdef JZ_BOUNDS_CHECK
+    cudaError_t e = cudaMemcpyFromSymbol(out, jz_bounds_status, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess && clear) {
+        const unsigned int z[2] = {0u, 0u};
+        e = cudaMemcpyToSymbol(jz_bounds_status, z, sizeof z);
+    }
+    return e;
+#else
+    out[0] = out[1] = 0u;
+    (void)clear;
+    return cudaSuccess;
+#endif
+}
 
 size_t sw_smem_bytes(const Geom& geo)
 {

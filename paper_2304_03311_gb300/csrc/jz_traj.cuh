@@ -93,6 +93,17 @@ struct Traj {
     uint32_t m_next;
 
     __device__ __forceinline__ int W() const { return CW > 0 ? CW : g.GW; }
+
+    // Word i of one colour's NR * GW lattice words (checked in bounds-checked
+    // builds: an index outside the colour is recorded and the access skipped).
+    __device__ __forceinline__ uint32_t ld(const uint32_t* colour, int i, int site) const
+    {
+        return in_bounds(i, (long long)g.NR * g.GW, site) ? colour[i] : 0u;
+    }
+    __device__ __forceinline__ void st(uint32_t* colour, int i, uint32_t v, int site) const
+    {
+        if (in_bounds(i, (long long)g.NR * g.GW, site)) colour[i] = v;
+    }
     __device__ __forceinline__ int Ly() const { return D == 2 ? 1 : (CLY > 0 ? CLY : g.Ly); }
     __device__ __forceinline__ int rowW() const { return Ly() * W(); }
 
@@ -139,11 +150,13 @@ struct Traj {
         return nj == 8 ? 0xFFFFFFFFu : ((1u << (4 * nj)) - 1u);
     }
 
-    // The x neighbour not at the same h: h-1 for p = 0, h+1 for p = 1.  o points
-    // at word q of the other colour; the row's other words are o[d_qm] / o[d_qp].
-    __device__ __forceinline__ uint32_t xshift(const uint32_t* o, int p, uint32_t nx0) const
+    // The x neighbour not at the same h: h-1 for p = 0, h+1 for p = 1.  Word w
+    // of the other colour oth is word q of the row; the row's other words are
+    // w + d_qm / w + d_qp.
+    __device__ __forceinline__ uint32_t xshift(const uint32_t* oth, int w, int p,
+                                               uint32_t nx0) const
     {
-        const uint32_t nb = o[p ? d_qp : d_qm];
+        const uint32_t nb = ld(oth, w + (p ? d_qp : d_qm), 6);
         if (FAST) return p ? __funnelshift_r(nx0, nb, 4) : __funnelshift_l(nb, nx0, 4);
         // ragged rows: the row's last word holds fewer than eight sites
         return p ? (((nx0 >> 4) & m_next) | ((nb & 0xFu) << sh_next))
@@ -165,17 +178,16 @@ struct Traj {
     __device__ __forceinline__ void bulk_update(uint32_t* own_b, const uint32_t* oth, int w, int up,
                                                 int p, const uint4& ua, const uint4& ub) const
     {
-        const uint32_t* o = oth + w;
-        const uint32_t own = own_b[w];
-        const uint32_t ntm = o[-rowW()];
-        const uint32_t ntp = o[up];
-        const uint32_t nx0 = o[0];
-        const uint32_t nx1 = xshift(o, p, nx0);
+        const uint32_t own = ld(own_b, w, 1);
+        const uint32_t ntm = ld(oth, w - rowW(), 10);
+        const uint32_t ntp = ld(oth, w + up, 11);
+        const uint32_t nx0 = ld(oth, w, 5);
+        const uint32_t nx1 = xshift(oth, w, p, nx0);
         uint32_t dsum = (own ^ ntm) + (own ^ ntp) + (own ^ nx0) + (own ^ nx1);
-        if (D == 3) dsum += (own ^ o[d_ym]) + (own ^ o[d_yp]);
+        if (D == 3) dsum += (own ^ ld(oth, w + d_ym, 7)) + (own ^ ld(oth, w + d_yp, 8));
         uint32_t flip = accept8<D>(dsum, ua, ub, tab);
         if (!FAST) flip &= vmask;
-        own_b[w] = own ^ flip;
+        st(own_b, w, own ^ flip, 9);
     }
 
     // Site jl of a cut-row word that switches during the protocol: couplings
@@ -226,16 +238,15 @@ struct Traj {
         const int off_g = !cut ? 0 : t == 0 ? (r == n - 1 ? -(n - 1) * repW : repW)
                                            : (r == 0 ? (n - 1) * repW : -repW);
         const uint32_t m = cut ? glue_mask(lg, p) : 0u;
-        const uint32_t* o = oth + w;
-        const uint32_t own = own_b[w];
-        const uint32_t nrm = o[off_n];
-        const uint32_t self_w = o[off_x];
-        const uint32_t glue_w = o[off_x + off_g];
+        const uint32_t own = ld(own_b, w, 1);
+        const uint32_t nrm = ld(oth, w + off_n, 2);
+        const uint32_t self_w = ld(oth, w + off_x, 3);
+        const uint32_t glue_w = ld(oth, w + off_x + off_g, 4);
         const uint32_t cross = (self_w & ~m) | (glue_w & m);
-        const uint32_t nx0 = o[0];
-        const uint32_t nx1 = xshift(o, p, nx0);
+        const uint32_t nx0 = ld(oth, w, 5);
+        const uint32_t nx1 = xshift(oth, w, p, nx0);
         uint32_t dsum = (own ^ nrm) + (own ^ cross) + (own ^ nx0) + (own ^ nx1);
-        if (D == 3) dsum += (own ^ o[d_ym]) + (own ^ o[d_yp]);
+        if (D == 3) dsum += (own ^ ld(oth, w + d_ym, 7)) + (own ^ ld(oth, w + d_yp, 8));
         uint32_t flip = accept8<D>(dsum, ua, ub, tab);
         // Switching sites g0 <= x < g1 during the protocol: couplings
         // beta (1 - lambda) to their own replica, beta lambda to the next one.
@@ -247,7 +258,7 @@ struct Traj {
             switched_site(flip, jl, own, self_w, glue_w, dsum, ua, ub, k, J, w_self, w_glue,
                           record, dE);
         if (!FAST) flip &= vmask;
-        own_b[w] = own ^ flip;
+        st(own_b, w, own ^ flip, 9);
     }
 
     __device__ __forceinline__ void half_sweep(int c, uint32_t sweep, int k, int lg,
@@ -357,7 +368,7 @@ struct Traj {
                         const int x = 2 * (8 * q + j) + p;
                         if (x < g.L && src[row0 + x] < 0) v |= 1u << (4 * j);
                     }
-                    base[w] = v;
+                    st(base, w, v, 12);
                 }
             }
         }
@@ -381,7 +392,7 @@ struct Traj {
                                        ((ua.w >> 31) << 12) | ((ub.x >> 31) << 16) |
                                        ((ub.y >> 31) << 20) | ((ub.z >> 31) << 24) |
                                        ((ub.w >> 31) << 28);
-                    base[w] = v & vmask;
+                    st(base, w, v & vmask, 12);
                 }
             }
         }
@@ -481,7 +492,8 @@ __device__ __forceinline__ void export_spins(const Geom& g, const uint32_t* S_te
         const int t = trow % g.Lt;
         const int c = (x + y + t) & 1;
         const int h = x >> 1;
-        const uint32_t word = S_team[(size_t)(c * g.NR + R) * g.GW + (h >> 3)];
+        const long long wi = (long long)(c * g.NR + R) * g.GW + (h >> 3);
+        const uint32_t word = in_bounds(wi, 2LL * g.NR * g.GW, 13) ? S_team[wi] : 0u;
         dst[i] = ((word >> (4 * (h & 7))) & 1u) ? (int8_t)-1 : (int8_t)1;
     }
 }

@@ -76,3 +76,9 @@ def test_strerror_and_host_only_entry_points(lib):
     assert lib.ising_replica_init(None, 0, 0, None) == jz.ISING_ERR_ARG
     lib.ising_replica_free(None)      # NULL is a no-op
     assert lib.ising_sync(None) == jz.ISING_ERR_ARG
+
+
+def test_release_build_has_no_bounds_status(lib):
+    import ctypes
+    a, b = ctypes.c_uint(), ctypes.c_uint()
+    assert lib.ising_bounds_status(ctypes.byref(a), ctypes.byref(b), 0) == jz.ISING_ERR_UNSUPPORTED
