@@ -29,7 +29,7 @@ constexpr int kMaxTeams = 64;
 // registers so that two 512-thread CTAs fit on an SM; the generic variant
 // keeps the full register file of one CTA, and so does the 2D GW = 1 variant,
 // whose one-row pipeline holds the next half-sweep's Philox blocks.
-template <int D, bool FAST, int CW, int CLY, bool WARP, bool HBM>
+template <int D, bool FAST, int CW, int CLY, bool WARP, bool HBM, int CLT = 0, int CTS = 0>
 __global__ void __launch_bounds__(512, (CW > 1 || (CW == 1 && D == 3)) ? 2 : 1)
 traj_kernel(const Geom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, int n_jobs,
             const LaunchShape sh, uint32_t* __restrict__ gS)
@@ -64,8 +64,8 @@ traj_kernel(const Geom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
         dE = run_trajectory<D, FAST, CW, CLY, kRow>(g, K, tj, traj, St, s_tab, tid,
                                                     sh.team_threads, WarpBarrier{}, sin);
     else if (WARP)
-        dE = run_trajectory<D, FAST, CW, CLY>(g, K, tj, traj, St, s_tab, tid, sh.team_threads,
-                                              WarpBarrier{}, sin);
+        dE = run_trajectory<D, FAST, CW, CLY, false, CLT, CTS>(g, K, tj, traj, St, s_tab, tid,
+                                                               sh.team_threads, WarpBarrier{}, sin);
     else
         dE = run_trajectory<D, FAST, CW, CLY>(g, K, tj, traj, St, s_tab, tid, sh.team_threads,
                                               CtaBarrier{}, sin);
@@ -118,7 +118,7 @@ estimator_kernel(const long long* __restrict__ w_int, int n, double scale, int d
 // ------------------------------------------------------------ host launchers --
 size_t traj_smem_bytes(const Geom& g) { return (size_t)2 * g.NR * g.GW * sizeof(uint32_t); }
 
-template <int D, bool FAST, int CW, int CLY>
+template <int D, bool FAST, int CW, int CLY, int CLT = 0, int CTS = 0>
 static cudaError_t launch_traj_t(const Geom& g, const PhiloxKeys& K, const JobDesc* jobs,
                                  int n_jobs, long long n_cta, const LaunchShape& sh,
                                  cudaStream_t st, uint32_t* gS)
@@ -126,7 +126,7 @@ static cudaError_t launch_traj_t(const Geom& g, const PhiloxKeys& K, const JobDe
     const size_t smem = gS ? 0 : traj_smem_bytes(g) * sh.teams;
     auto kern = gS ? (sh.warp ? traj_kernel<D, FAST, CW, CLY, true, true>
                               : traj_kernel<D, FAST, CW, CLY, false, true>)
-                   : (sh.warp ? traj_kernel<D, FAST, CW, CLY, true, false>
+                   : (sh.warp ? traj_kernel<D, FAST, CW, CLY, true, false, CLT, CTS>
                               : traj_kernel<D, FAST, CW, CLY, false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -136,13 +136,17 @@ static cudaError_t launch_traj_t(const Geom& g, const PhiloxKeys& K, const JobDe
 }
 
 // Shapes with compile-time row geometry: 2D L = 16 and 64 (GW = 1, 4) and 3D
-// L = 16 (GW = 1, L_y = 16); every other shape runs the generic instantiation.
+// L = 16 (GW = 1, L_y = 16); the 2D L = L_t = 64 warp teams (eight time slices
+// per thread) also fix L_t and the slice step.  Every other shape runs the
+// generic instantiation.
 cudaError_t launch_traj(int D, const Geom& g, const PhiloxKeys& K, const JobDesc* jobs,
                         int n_jobs, long long n_cta, const LaunchShape& sh, cudaStream_t st,
                         uint32_t* gS)
 {
     const bool fast = (g.Lh % 8) == 0;
     if (D == 2) {
+        if (fast && g.GW == 4 && g.Lt == 64 && sh.warp && sh.team_threads == 32 && !gS)
+            return launch_traj_t<2, true, 4, 1, 64, 8>(g, K, jobs, n_jobs, n_cta, sh, st, gS);
         if (fast && g.GW == 4)
             return launch_traj_t<2, true, 4, 1>(g, K, jobs, n_jobs, n_cta, sh, st, gS);
         if (fast && g.GW == 1)

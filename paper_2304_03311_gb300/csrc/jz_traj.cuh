@@ -76,7 +76,9 @@ struct TeamJob {
     const uint32_t* tcut;
 };
 
-template <int D, bool FAST, int CW = 0, int CLY = 0>
+// CLT, CTS > 0: L_t and the slice step TS fixed at compile time (the 2D L = 64,
+// L_t = 64 warp teams); 0 reads them from Geom and the team size.
+template <int D, bool FAST, int CW = 0, int CLY = 0, int CLT = 0, int CTS = 0>
 struct Traj {
     const Geom& g;
     uint32_t* S;              // this team's spin words [2][NR * GW]
@@ -118,7 +120,7 @@ struct Traj {
         lo1 = (uint32_t)p1;
         const int col = W() * Ly();
         const int slots = nthr / col;   // threads per word column
-        TS = slots < g.Lt ? slots : g.Lt;
+        TS = CTS > 0 ? CTS : (slots < g.Lt ? slots : g.Lt);
         RS = slots / TS;
         if (tid < 0 || tid / col >= TS * RS) {
             q = y = 0;
@@ -304,7 +306,28 @@ struct Traj {
                 // mixes the wide multiplies with the update's logic; the blocks'
                 // round-0 products M0 c0 advance by additions.
                 const int p = (pc ^ t0) & 1;
-                if (t < Lt) {
+                if constexpr (CLT > 0 && CTS > 0 && CLT % CTS == 0 && CLT / CTS >= 3) {
+                    // L_t and the slice step fixed at compile time: the rows
+                    // t0 + k CTS, k = 1 .. L_t/CTS - 1, unrolled with immediate
+                    // word offsets (no loop or address arithmetic per row)
+                    constexpr int NROW = CLT / CTS;
+                    constexpr int STR = CTS * (D == 2 ? 1 : CLY) * CW;
+                    const int up_last = t0 == CTS - 1 ? wrap_up : rw;
+                    uint64_t p0 = (uint64_t)kPhiloxM0 * c0;
+                    const uint64_t dp = (uint64_t)kPhiloxM0 * cstride;
+                    uint4 ua = philox_p0(p0, sweep, hi1, lo1, c3, K);
+                    uint4 ub = philox_p0(p0 + kPhiloxM0, sweep, hi1, lo1, c3, K);
+#pragma unroll
+                    for (int k = 1; k < NROW - 1; ++k) {
+                        p0 += dp;
+                        const uint4 na = philox_p0(p0, sweep, hi1, lo1, c3, K);
+                        const uint4 nb = philox_p0(p0 + kPhiloxM0, sweep, hi1, lo1, c3, K);
+                        bulk_update(own_b, oth, w + (k - 1) * STR, rw, p, ua, ub);
+                        ua = na;
+                        ub = nb;
+                    }
+                    bulk_update(own_b, oth, w + (NROW - 2) * STR, up_last, p, ua, ub);
+                } else if (t < Lt) {
                     uint64_t p0 = (uint64_t)kPhiloxM0 * c0;
                     const uint64_t dp = (uint64_t)kPhiloxM0 * cstride;
                     uint4 ua = philox_p0(p0, sweep, hi1, lo1, c3, K);
@@ -417,13 +440,13 @@ struct WarpBarrier {
 // own update, so the independent chains cover the latency of the
 // shared-memory loads and the barrier that a team this small (one warp per
 // trajectory, few warps per SM) has no other warps to hide.
-template <int D, bool FAST, int CW, int CLY, bool ROW = false, class Bar>
+template <int D, bool FAST, int CW, int CLY, bool ROW = false, int CLT = 0, int CTS = 0, class Bar>
 __device__ __forceinline__ int run_trajectory(const Geom& g, const PhiloxKeys& K, const TeamJob& J,
                                               long long traj, uint32_t* S_team,
                                               const uint32_t* tab, int tid, int nthr, Bar bar,
                                               const int8_t* sin = nullptr)
 {
-    const Traj<D, FAST, CW, CLY> tr(g, S_team, tab, K, (uint32_t)traj,
+    const Traj<D, FAST, CW, CLY, CLT, CTS> tr(g, S_team, tab, K, (uint32_t)traj,
                                     ((uint32_t)(J.dir < 0) << 1) | ((uint32_t)J.l << 2), tid, nthr);
     int dE = 0;
     // the global sweep index: thermalisation sweeps 0 .. n_therm - 1, then
