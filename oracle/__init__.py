@@ -28,21 +28,27 @@ _lock = threading.Lock()
 _lib = None
 
 
-def build(force: bool = False, out: str | None = None, mutant: int = 0) -> str:
+def build(force: bool = False, out: str | None = None, mutant: int = 0,
+          sanitize: bool = False) -> str:
     """Compile jz_oracle.c into oracle/liboracle.so with gcc (-O2, OpenMP).
 
     -ffp-contract=off keeps the threshold formula free of fused multiply-adds
     on every host, so the tables are the plain libm evaluation of the formula.
     ``mutant`` > 0 builds, at ``out``, a copy with one planted mistake (tests
-    only, to show that the pins catch it).
+    only, to show that the pins catch it).  ``sanitize`` builds, at ``out``, a
+    copy instrumented with AddressSanitizer and UndefinedBehaviorSanitizer
+    (errors abort; a process loading it must preload the ASan runtime).
     """
     path = out or _LIB_PATH
-    if (mutant == 0 and not force and os.path.exists(path)
+    if (mutant == 0 and not sanitize and not force and os.path.exists(path)
             and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
         return path
     tmp = path + f".tmp{os.getpid()}"
+    san = (["-fsanitize=address,undefined", "-fno-sanitize-recover=all",
+            "-fno-omit-frame-pointer", "-g"] if sanitize else [])
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-           "-ffp-contract=off", f"-DORACLE_MUTANT={int(mutant)}", "-o", tmp, _SRC, "-lm"]
+           "-ffp-contract=off", f"-DORACLE_MUTANT={int(mutant)}"] + san + [
+           "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, path)
     return path
