@@ -405,19 +405,38 @@ int estimator_reduce(ising_ctx* ctx, const int64_t* work_int, int n_traj, double
                      int n_step, int direction, int n_jack_bins, double* log_ratio,
                      double* delta_S2, double* delta_S2_err);
 
-/* Launch-shape control; the paper has no counterpart.  Fixes the CTA size the
- * context uses for lattices of shape (d, L, L_t): threads = ceil(L/8) * L_y * TS
- * with 1 <= TS <= L_t (each thread owns one spin-word column of every TS-th
- * time slice), at most 512; threads = 0 restores the default choice.
- * Results do not depend on it.  Errors: ISING_ERR_ARG. */
+/* Launch-shape control; the paper has no counterpart.  A time slice holds
+ * col = ceil(L/8) * L_y spin words; each thread owns one word column of every
+ * TS-th slice.  Fixes the CTA size the context uses for lattices of shape
+ * (d, L, L_t), at most 512 threads:
+ *   col <= 32  a multiple of 32: warp teams of col * TS <= 32 threads, as many
+ *              per CTA as fit (one team of threads / col slices per CTA when
+ *              fewer than four warp teams' lattices fit its shared memory)
+ *   col > 32   col * TS with 1 <= TS <= L_t: one team per CTA
+ * threads = 0 restores the default: the shape, among the warp-team layouts of
+ * every CTA size and one team per CTA of every TS, that keeps the most lanes
+ * of each SM busy for the launch's trajectory count (CUDA occupancy of the
+ * kernel that runs the lattice).  Results do not depend on the shape.
+ * Errors: ISING_ERR_ARG. */
 int ising_set_threads(ising_ctx* ctx, int d, int L, int L_t, int threads);
 
+/* The launch shape jarzynski_run_ex would use for p alone in this context:
+ * shape[0] threads per team (one trajectory), shape[1] teams per CTA,
+ * shape[2] threads per CTA, shape[3] 1 for warp teams (__syncwarp) and 0 for
+ * one team per CTA (__syncthreads), shape[4] 1 when the lattices live in
+ * HBM.  Swendsen-Wang: one trajectory per CTA of its fixed size.  shape is
+ * host memory of 5 ints.  Errors: ISING_ERR_ARG (as check of p),
+ * ISING_ERR_UNSUPPORTED (a time slice wider than 512 threads), ISING_ERR_CUDA. */
+int ising_launch_shape(ising_ctx* ctx, const jz_params* p, int* shape);
+
 /* Autotuner; the paper has no counterpart.  Times every admissible CTA size
- * (TS a power of two up to L_t, and the default) on a short sample of the
- * transformation p -- same shape, coupling and l, n_therm = 16, N = 16,
- * n_sweep = 1, min(p->n_traj, 4864) trajectories -- keeps the fastest for p's
- * shape in the context (as ising_set_threads would) and writes it to
- * *threads (nullable).  Synchronises the context's stream.  Swendsen-Wang
+ * (multiples of 32 that are powers of two, or TS a power of two up to L_t)
+ * and the default shape on a short sample of the transformation p -- same
+ * shape, coupling and l, n_therm = 16, N = 16, n_sweep = 1,
+ * min(p->n_traj, 4864) trajectories -- keeps the fastest for p's shape in
+ * the context (as ising_set_threads would) and writes it to *threads
+ * (nullable): a CTA size, or 0 when the default shape, where it is none of
+ * the sizes', was fastest.  Synchronises the context's stream.  Swendsen-Wang
  * (p->update = 1) runs one trajectory per CTA of a fixed size: nothing is
  * timed or stored and *threads receives that size (256 in 2D, 512 in 3D).
  * Errors: as jarzynski_run_ex. */
@@ -427,7 +446,8 @@ int ising_autotune(ising_ctx* ctx, const jz_params* p, int* threads);
  * name, d, L, L_t, n, n_traj bucket) with bucket = floor(log2 n_traj): the
  * best CTA size depends on the lattice and on how many trajectories fill the
  * GPU.  The file is JSON, {"version": 1, "entries": [...]}, one entry per
- * line with the keys gpu, d, L, L_t, n_replica, traj_bucket, cta_threads.
+ * line with the keys gpu, d, L, L_t, n_replica, traj_bucket, cta_threads
+ * (0 for the default shape, as ising_autotune reports it).
  * The cache functions are host only (no device needed); the cache is not
  * thread-safe.
  *   create / free   an empty cache

@@ -25,7 +25,7 @@ __all__ = [
     "estimator_reduce", "ising_strerror", "jz_params_default", "ising_probe",
     "jarzynski_run_noalloc", "ising_binary_version", "ising_cancel", "ising_cancel_reset",
     "jarzynski_run_resumable", "jz_cancel", "jz_server_set_log", "jz_result_json", "TuneCache",
-    "ising_autotune_cached", "ising_bounds_status", "use_debug_library",
+    "ising_autotune_cached", "ising_bounds_status", "use_debug_library", "ising_launch_shape",
 ]
 
 ISING_OK = 0
@@ -143,6 +143,7 @@ def load():
         "ising_set_threads": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_int]),
         "ising_autotune": (ctypes.c_int, [vp, P(JzParams), P(ctypes.c_int)]),
+        "ising_launch_shape": (ctypes.c_int, [vp, P(JzParams), P(ctypes.c_int)]),
         "jz_plan_create": (ctypes.c_int, [vp, P(JzParams), ctypes.c_int, P(vp), vp, ctypes.c_int,
                                           P(vp)]),
         "jz_plan_launch": (ctypes.c_int, [vp]),
@@ -302,9 +303,18 @@ def ising_set_threads(ctx, d: int, L: int, L_t: int, threads: int) -> None:
            "ising_set_threads")
 
 
+def ising_launch_shape(ctx, params: JzParams) -> dict:
+    """The launch shape jarzynski_run_ex would use for `params` in this context."""
+    v = (ctypes.c_int * 5)()
+    _check(load().ising_launch_shape(ctx, ctypes.byref(params), v), "ising_launch_shape")
+    return {"team_threads": v[0], "teams": v[1], "cta_threads": v[2], "warp": bool(v[3]),
+            "hbm": bool(v[4])}
+
+
 def ising_autotune(ctx, params: JzParams) -> int:
-    """Time the admissible CTA sizes on a short sample of `params`, keep the
-    fastest for its shape in the context, and return it."""
+    """Time the admissible CTA sizes and the default shape on a short sample of
+    `params`, keep the fastest for its shape in the context, and return its
+    CTA size (0 when the default shape won)."""
     t = ctypes.c_int()
     _check(load().ising_autotune(ctx, ctypes.byref(params), ctypes.byref(t)), "ising_autotune")
     return t.value

@@ -276,6 +276,101 @@ jz::LaunchShape shape_for(const jz::Geom& g, int cta_threads)
     return s;
 }
 
+// The relative rate of a launch of shape sh over n_traj trajectories of g
+// (n_traj <= 0: enough to fill every SM), fitted to rates measured on GB300
+// for every layout of 2D L = 34 .. 256 and 3D L = 8 .. 48 (L_t = L) at 256,
+// 2048 and 8192 trajectories:
+//   min(active warps per SM, kSatWarps) x (fraction of lanes owning a word)
+//   x R / (R + kBarrierRows) for one team per CTA,
+// where active warps are the resident ones (CUDA occupancy of the kernel
+// that runs g) or fewer when the trajectories do not fill the SMs, and R is
+// a thread's rows per half-sweep: a CTA team drains at its barrier, a warp
+// team's __syncwarp costs next to nothing.  Negative when sh cannot launch.
+constexpr double kSatWarps = 16.0;     // the integer pipes are saturated from here on
+constexpr double kBarrierRows = 1.5;   // a CTA barrier costs about 1.5 rows of work
+double shape_score(int d, const jz::Geom& g, const jz::LaunchShape& sh, long long n_traj,
+                   int n_sm)
+{
+    if (sh.cta_threads <= 0 || sh.cta_threads > 512 || sh.teams < 1) return -1.0;
+    if ((size_t)sh.teams * jz::traj_smem_bytes(g) > jz::kMaxSmemPerCta) return -1.0;
+    int ctas = 0;
+    if (jz::traj_occupancy(d, g, sh, &ctas) != cudaSuccess) {
+        cudaGetLastError();
+        return -1.0;
+    }
+    if (ctas < 1) return -1.0;
+    const int wc = (sh.cta_threads + 31) / 32;
+    double warps = (double)ctas * wc;
+    if (n_traj > 0) {
+        const long long n_cta = (n_traj + sh.teams - 1) / sh.teams;
+        warps = std::min(warps, (double)n_cta * wc / n_sm);
+    }
+    const double lanes = (double)sh.teams * sh.team_threads / (32.0 * wc);
+    double sc = std::min(warps, kSatWarps) * lanes;
+    if (!sh.warp) {
+        const int ts = std::max(1, std::min(sh.team_threads / (g.GW * g.Ly), g.Lt));
+        const double rows = (double)g.nrep * g.Lt / ts;
+        sc *= rows / (rows + kBarrierRows);
+    }
+    return sc;
+}
+
+// The shape a lattice in shared memory runs with when no CTA size is fixed.
+// Candidates: the warp-team layouts of shape_for for CTAs of 32 ... 512
+// threads, and one team per CTA for every slice step TS (col * TS <= 512).
+// shape_for(g, 0) is kept unless another candidate scores kKeepMargin more
+// (shape_score).  On the measured layouts this picks within about 2 % of the
+// fastest one on average and runs 1.39x the rate of shape_for(g, 0): narrow
+// slices of large lattices (2D L ~ 130 .. 240 with L_t = L), whose warp
+// teams each hold a whole lattice of shared memory and leave an SM four
+// warps, gain 1.4 - 1.9x as CTA teams; small jobs, whose trajectories fill
+// more SMs when each has more threads, 2 - 3x.  Lattices in HBM keep
+// shape_for(g, 0).
+constexpr double kKeepMargin = 1.05;
+jz::LaunchShape default_shape(int d, const jz::Geom& g, long long n_traj)
+{
+    const jz::LaunchShape base = shape_for(g, 0);
+    if (jz::traj_smem_bytes(g) > jz::kMaxSmemPerCta) return base;
+    int dev = 0, n_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        n_sm < 1) {
+        cudaGetLastError();
+        return base;
+    }
+    const double s0 = shape_score(d, g, base, n_traj, n_sm);
+    jz::LaunchShape best = base;
+    double best_s = s0 * kKeepMargin;
+    auto consider = [&](const jz::LaunchShape& sh) {
+        const double sc = shape_score(d, g, sh, n_traj, n_sm);
+        if (sc > best_s) {
+            best_s = sc;
+            best = sh;
+        }
+    };
+    const int col = g.GW * g.Ly;
+    if (col <= 32)
+        for (int t = 32; t <= 512; t *= 2) consider(shape_for(g, t));
+    // one team per CTA: for w = 1 .. 16 warps the largest slice step that
+    // fits them, and the even step below it; a CTA team has at least a warp
+    // of threads (its first eight fill the shared threshold table)
+    int last = 0;
+    for (int w = 1; w <= 16; ++w) {
+        const int top = std::min(32 * w / col, g.Lt);
+        for (int ts = top; ts >= 1 && ts >= top - 1; --ts) {
+            if (ts == last || col * ts < 32) continue;
+            jz::LaunchShape sh{};
+            sh.team_threads = col * ts;
+            sh.teams = 1;
+            sh.cta_threads = col * ts;
+            sh.warp = 0;
+            consider(sh);
+        }
+        last = top;
+    }
+    return best;
+}
+
 // Whether one time slice of words fits a CTA of 512 threads (any lattice
 // satisfying this runs, with its lattice in HBM if not in shared memory).
 bool threads_fit(const jz::Geom& g) { return g.GW * g.Ly <= 512; }
@@ -297,12 +392,13 @@ bool threads_ok(const jz::Geom& g, int threads)
     return threads % col == 0 && threads / col <= g.Lt;
 }
 
-// The context's launch shape for this lattice: the tuned / fixed CTA size, else the default.
-jz::LaunchShape ctx_shape(const ising_ctx* ctx, int d, const jz::Geom& g)
+// The context's launch shape for this lattice: the tuned / fixed CTA size,
+// else the default for a launch of n_traj trajectories.
+jz::LaunchShape ctx_shape(const ising_ctx* ctx, int d, const jz::Geom& g, long long n_traj)
 {
     auto it = ctx->threads.find(std::make_tuple(d, g.L, g.Lt));
     const int t = (it != ctx->threads.end() && threads_ok(g, it->second)) ? it->second : 0;
-    return shape_for(g, t);
+    return t ? shape_for(g, t) : default_shape(d, g, n_traj);
 }
 
 int cuda_err(cudaError_t e)
@@ -323,7 +419,9 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
     if (!sw && !threads_fit(g)) return ISING_ERR_UNSUPPORTED;
     // lattices beyond shared memory run from HBM, one slice per CTA
     const bool in_hbm = sw ? !sw_fits(g) : !shape_fits(g);
-    jz::LaunchShape sh = ctx_shape(ctx, p0.d, g);
+    long long n_traj_launch = 0;
+    for (int j : idx) n_traj_launch += jobs[j].n_traj;
+    jz::LaunchShape sh = sw ? shape_for(g, 0) : ctx_shape(ctx, p0.d, g, n_traj_launch);
     if (sw) sh.teams = 1;
     const int n_jobs = (int)idx.size();
     const int per = sw ? 2 : 8 * p0.d;
@@ -622,6 +720,26 @@ int ising_set_threads(ising_ctx* ctx, int d, int L, int L_t, int threads)
     return ISING_OK;
 }
 
+int ising_launch_shape(ising_ctx* ctx, const jz_params* p, int* shape)
+{
+    if (!ctx || !p || !shape) return ISING_ERR_ARG;
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
+    const jz::Geom g = make_geom(p->d, p->L, p->L_t, nrep_of(*p));
+    if (p->update == 1) {
+        const int t = jz::sw_cta_threads(p->d);
+        const int v[5] = {t, 1, t, 0, sw_fits(g) ? 0 : 1};
+        std::memcpy(shape, v, sizeof v);
+        return ISING_OK;
+    }
+    if (!threads_fit(g)) return ISING_ERR_UNSUPPORTED;
+    const jz::LaunchShape sh = ctx_shape(ctx, p->d, g, p->n_traj);
+    const int v[5] = {sh.team_threads, sh.teams, sh.cta_threads, sh.warp, shape_fits(g) ? 0 : 1};
+    std::memcpy(shape, v, sizeof v);
+    return ISING_OK;
+}
+
 int ising_autotune(ising_ctx* ctx, const jz_params* p, int* threads)
 {
     if (!ctx || !p) return ISING_ERR_ARG;
@@ -644,6 +762,8 @@ int ising_autotune(ising_ctx* ctx, const jz_params* p, int* threads)
     s.traj0 = 0;
     if ((rc = ensure(ctx, ctx->est_in, (size_t)s.n_traj * sizeof(long long)))) return rc;
     int64_t* out = (int64_t*)ctx->est_in.ptr;
+    // explicit CTA sizes, then 0: the default shape for the sample's
+    // trajectory count, when it is none of theirs
     std::vector<int> cands;
     const int col = g.GW * g.Ly;
     if (col <= 32) {
@@ -652,6 +772,16 @@ int ising_autotune(ising_ctx* ctx, const jz_params* p, int* threads)
         for (int ts = 1; ts <= g.Lt && col * ts <= 512; ts *= 2) cands.push_back(col * ts);
         const int def = shape_for(g, 0).cta_threads;
         if (std::find(cands.begin(), cands.end(), def) == cands.end()) cands.push_back(def);
+    }
+    {
+        const jz::LaunchShape d0 = default_shape(p->d, g, s.n_traj);
+        bool listed = false;
+        for (int t : cands) {
+            const jz::LaunchShape e = shape_for(g, t);
+            listed = listed || (e.team_threads == d0.team_threads && e.teams == d0.teams &&
+                                e.cta_threads == d0.cta_threads && e.warp == d0.warp);
+        }
+        if (!listed) cands.push_back(0);
     }
     const auto key = std::make_tuple(p->d, p->L, p->L_t);
     cudaEvent_t e0, e1;
@@ -664,7 +794,8 @@ int ising_autotune(ising_ctx* ctx, const jz_params* p, int* threads)
     float best_ms = 1e30f;
     int64_t* outs[1] = {out};
     for (int t : cands) {
-        ctx->threads[key] = t;
+        if (t) ctx->threads[key] = t;
+        else ctx->threads.erase(key);
         if ((rc = run_jobs(ctx, &s, 1, outs, nullptr))) break;           // warm-up
         cudaEventRecord(e0, ctx->stream);
         if ((rc = run_jobs(ctx, &s, 1, outs, nullptr))) break;
@@ -679,7 +810,8 @@ int ising_autotune(ising_ctx* ctx, const jz_params* p, int* threads)
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    ctx->threads[key] = best;
+    if (best) ctx->threads[key] = best;
+    else ctx->threads.erase(key);
     if (rc) return rc;
     if (threads) *threads = best;
     return ISING_OK;
@@ -984,7 +1116,7 @@ extern "C" int jarzynski_run_noalloc(const jz_params* p, int64_t* work_int_out, 
     }
     const jz::PhiloxKeys K = key_schedule(p->seed);
     if (sw) return cuda_err(jz::launch_sw(p->d, g, K, (const jz::JobDesc*)base, 1, p->n_traj, st));
-    const jz::LaunchShape sh = shape_for(g, 0);
+    const jz::LaunchShape sh = default_shape(p->d, g, p->n_traj);
     return cuda_err(jz::launch_traj(p->d, g, K, (const jz::JobDesc*)base, 1,
                                     (p->n_traj + sh.teams - 1) / sh.teams, sh, st));
 }

@@ -58,7 +58,7 @@ void jz_tune_cache_free(jz_tune_cache* c) { delete c; }
 int jz_tune_cache_put(jz_tune_cache* c, const char* gpu, int d, int L, int L_t, int n_replica,
                       int n_traj, int cta_threads)
 {
-    if (!c || !gpu || (d != 2 && d != 3) || L < 2 || L_t < 2 || n_traj < 1 || cta_threads < 1)
+    if (!c || !gpu || (d != 2 && d != 3) || L < 2 || L_t < 2 || n_traj < 1 || cta_threads < 0)
         return ISING_ERR_ARG;
     const int n = n_replica == 0 ? 2 : n_replica;
     c->entries[TuneKey(clean_name(gpu), d, L, L_t, n, traj_bucket(n_traj))] = cta_threads;
@@ -128,7 +128,7 @@ int jz_tune_cache_load(jz_tune_cache* c, const char* path)
                         "{\"gpu\": \"%255[^\"]\", \"d\": %d, \"L\": %d, \"L_t\": %d, "
                         "\"n_replica\": %d, \"traj_bucket\": %d, \"cta_threads\": %d}",
                         gpu, &d, &L, &Lt, &n, &b, &t) != 7 ||
-            (d != 2 && d != 3) || L < 2 || Lt < 2 || n < 2 || b < 0 || b > 40 || t < 1) {
+            (d != 2 && d != 3) || L < 2 || Lt < 2 || n < 2 || b < 0 || b > 40 || t < 0) {
             rc = ISING_ERR_ARG;
             break;
         }

@@ -24,6 +24,9 @@ size_t traj_smem_bytes(const Geom& g);
 cudaError_t launch_traj(int D, const Geom& g, const PhiloxKeys& K, const JobDesc* jobs,
                         int n_jobs, long long n_cta, const LaunchShape& sh, cudaStream_t st,
                         uint32_t* gS = nullptr);
+// CTAs of shape sh resident per SM for the trajectory kernel launch_traj
+// runs on g with its lattices in shared memory.
+cudaError_t traj_occupancy(int D, const Geom& g, const LaunchShape& sh, int* ctas_per_sm);
 cudaError_t launch_estimator(const long long* w_int, int n, double scale, int direction,
                              int n_blocks, double* out, cudaStream_t st);
 size_t sw_smem_bytes(const Geom& g);
@@ -106,7 +109,8 @@ jz::LaunchShape shape_for(const jz::Geom& g, int cta_threads);
 bool shape_fits(const jz::Geom& g);
 bool threads_fit(const jz::Geom& g);
 bool threads_ok(const jz::Geom& g, int threads);
-jz::LaunchShape ctx_shape(const ising_ctx* ctx, int d, const jz::Geom& g);
+jz::LaunchShape default_shape(int d, const jz::Geom& g, long long n_traj);
+jz::LaunchShape ctx_shape(const ising_ctx* ctx, int d, const jz::Geom& g, long long n_traj);
 int cuda_err(cudaError_t e);
 int run_jobs(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const* outs,
              int8_t* const* spins);

@@ -118,46 +118,73 @@ estimator_kernel(const long long* __restrict__ w_int, int n, double scale, int d
 // ------------------------------------------------------------ host launchers --
 size_t traj_smem_bytes(const Geom& g) { return (size_t)2 * g.NR * g.GW * sizeof(uint32_t); }
 
+using TrajFn = void (*)(const Geom, const PhiloxKeys, const JobDesc*, int, const LaunchShape,
+                       uint32_t*);
+
 template <int D, bool FAST, int CW, int CLY, int CLT = 0, int CTS = 0>
-static cudaError_t launch_traj_t(const Geom& g, const PhiloxKeys& K, const JobDesc* jobs,
-                                 int n_jobs, long long n_cta, const LaunchShape& sh,
-                                 cudaStream_t st, uint32_t* gS)
+static TrajFn pick_traj(const LaunchShape& sh, bool hbm)
 {
-    const size_t smem = gS ? 0 : traj_smem_bytes(g) * sh.teams;
-    auto kern = gS ? (sh.warp ? traj_kernel<D, FAST, CW, CLY, true, true>
-                              : traj_kernel<D, FAST, CW, CLY, false, true>)
-                   : (sh.warp ? traj_kernel<D, FAST, CW, CLY, true, false, CLT, CTS>
-                              : traj_kernel<D, FAST, CW, CLY, false, false>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<(unsigned)n_cta, sh.cta_threads, smem, st>>>(g, K, jobs, n_jobs, sh, gS);
-    return cudaGetLastError();
+    return hbm ? (sh.warp ? traj_kernel<D, FAST, CW, CLY, true, true>
+                          : traj_kernel<D, FAST, CW, CLY, false, true>)
+               : (sh.warp ? traj_kernel<D, FAST, CW, CLY, true, false, CLT, CTS>
+                          : traj_kernel<D, FAST, CW, CLY, false, false>);
 }
 
 // Shapes with compile-time row geometry: 2D L = 16 and 64 (GW = 1, 4) and 3D
 // L = 16 (GW = 1, L_y = 16); the 2D L = L_t = 64 warp teams (eight time slices
 // per thread) also fix L_t and the slice step.  Every other shape runs the
 // generic instantiation.
+static TrajFn select_traj(int D, const Geom& g, const LaunchShape& sh, bool hbm)
+{
+    const bool fast = (g.Lh % 8) == 0;
+    if (D == 2) {
+        if (fast && g.GW == 4 && g.Lt == 64 && sh.warp && sh.team_threads == 32 && !hbm)
+            return pick_traj<2, true, 4, 1, 64, 8>(sh, hbm);
+        if (fast && g.GW == 4) return pick_traj<2, true, 4, 1>(sh, hbm);
+        if (fast && g.GW == 1) return pick_traj<2, true, 1, 1>(sh, hbm);
+        return fast ? pick_traj<2, true, 0, 0>(sh, hbm) : pick_traj<2, false, 0, 0>(sh, hbm);
+    }
+    if (fast && g.GW == 1 && g.Ly == 16) return pick_traj<3, true, 1, 16>(sh, hbm);
+    return fast ? pick_traj<3, true, 0, 0>(sh, hbm) : pick_traj<3, false, 0, 0>(sh, hbm);
+}
+
+// Lets kern take up to the per-CTA maximum of dynamic shared memory.  The
+// attribute is raised once to that maximum, never lowered, so that launches
+// and occupancy queries of the same kernel from several host threads with
+// different lattice sizes cannot narrow it under one another.
+static cudaError_t open_smem(TrajFn kern)
+{
+    cudaFuncAttributes fa;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const int max_dyn = optin - (int)fa.sharedSizeBytes;
+    if (fa.maxDynamicSharedSizeBytes >= max_dyn) return cudaSuccess;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
+}
+
 cudaError_t launch_traj(int D, const Geom& g, const PhiloxKeys& K, const JobDesc* jobs,
                         int n_jobs, long long n_cta, const LaunchShape& sh, cudaStream_t st,
                         uint32_t* gS)
 {
-    const bool fast = (g.Lh % 8) == 0;
-    if (D == 2) {
-        if (fast && g.GW == 4 && g.Lt == 64 && sh.warp && sh.team_threads == 32 && !gS)
-            return launch_traj_t<2, true, 4, 1, 64, 8>(g, K, jobs, n_jobs, n_cta, sh, st, gS);
-        if (fast && g.GW == 4)
-            return launch_traj_t<2, true, 4, 1>(g, K, jobs, n_jobs, n_cta, sh, st, gS);
-        if (fast && g.GW == 1)
-            return launch_traj_t<2, true, 1, 1>(g, K, jobs, n_jobs, n_cta, sh, st, gS);
-        return fast ? launch_traj_t<2, true, 0, 0>(g, K, jobs, n_jobs, n_cta, sh, st, gS)
-                    : launch_traj_t<2, false, 0, 0>(g, K, jobs, n_jobs, n_cta, sh, st, gS);
-    }
-    if (fast && g.GW == 1 && g.Ly == 16)
-        return launch_traj_t<3, true, 1, 16>(g, K, jobs, n_jobs, n_cta, sh, st, gS);
-    return fast ? launch_traj_t<3, true, 0, 0>(g, K, jobs, n_jobs, n_cta, sh, st, gS)
-                : launch_traj_t<3, false, 0, 0>(g, K, jobs, n_jobs, n_cta, sh, st, gS);
+    const size_t smem = gS ? 0 : traj_smem_bytes(g) * sh.teams;
+    const TrajFn kern = select_traj(D, g, sh, gS != nullptr);
+    const cudaError_t e = open_smem(kern);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)n_cta, sh.cta_threads, smem, st>>>(g, K, jobs, n_jobs, sh, gS);
+    return cudaGetLastError();
+}
+
+cudaError_t traj_occupancy(int D, const Geom& g, const LaunchShape& sh, int* ctas_per_sm)
+{
+    const TrajFn kern = select_traj(D, g, sh, false);
+    const cudaError_t e = open_smem(kern);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, kern, sh.cta_threads,
+                                                         traj_smem_bytes(g) * sh.teams);
 }
 
 cudaError_t bounds_status_traj(unsigned int out[2], bool clear)

@@ -158,7 +158,7 @@ int jz_server::launch(Slot& s, Job& j)
     J.w_out = d_work;
     J.spins_out = nullptr;
     const jz::PhiloxKeys K = key_schedule(p.seed);
-    const jz::LaunchShape sh = ctx_shape(ctx, p.d, g);
+    const jz::LaunchShape sh = p.update == 1 ? shape_for(g, 0) : ctx_shape(ctx, p.d, g, p.n_traj);
     const int B = p.n_traj < 32 ? p.n_traj : 32;
     if ((rc = cuda_err(cudaMemcpyAsync(d_tcut, s.h_tcut, n_tcut * sizeof(uint32_t),
                                        cudaMemcpyHostToDevice, s.stream))) ||

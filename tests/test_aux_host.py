@@ -33,17 +33,18 @@ def test_tune_cache_buckets_by_log2_trajectories():
 def test_tune_cache_file_round_trip(tmp_path):
     c = jz.TuneCache()
     entries = [("NVIDIA GB300", 2, 64, 64, 2, 16384, 512), ("NVIDIA GB300", 3, 16, 16, 2, 4096, 256),
-               ("NVIDIA GB300", 2, 16, 16, 2, 1000, 32), ("Other GPU", 2, 32, 32, 3, 1024, 128)]
+               ("NVIDIA GB300", 2, 16, 16, 2, 1000, 32), ("Other GPU", 2, 32, 32, 3, 1024, 128),
+               ("NVIDIA GB300", 2, 200, 200, 2, 4096, 0)]      # 0: the default shape won
     for e in entries:
         c.put(*e)
     path = tmp_path / "tune.json"
     c.save(path)
     doc = json.loads(path.read_text())             # the file is JSON
-    assert doc["version"] == 1 and len(doc["entries"]) == 4
+    assert doc["version"] == 1 and len(doc["entries"]) == 5
     assert {"gpu", "d", "L", "L_t", "n_replica", "traj_bucket", "cta_threads"} == set(doc["entries"][0])
     d = jz.TuneCache()
     d.load(path)
-    assert len(d) == 4
+    assert len(d) == 5
     for gpu, dd, L, Lt, n, nt, t in entries:
         assert d.get(gpu, dd, L, Lt, n, nt) == t
     # loading merges, later files win
@@ -51,7 +52,9 @@ def test_tune_cache_file_round_trip(tmp_path):
     e.put("NVIDIA GB300", 2, 64, 64, 2, 16384, 64)
     e.put("NVIDIA GB300", 2, 8, 8, 2, 16, 32)
     e.load(path)
-    assert len(e) == 5 and e.get("NVIDIA GB300", 2, 64, 64, 2, 16384) == 512
+    assert len(e) == 6 and e.get("NVIDIA GB300", 2, 64, 64, 2, 16384) == 512
+    with pytest.raises(jz.IsingError):
+        e.put("NVIDIA GB300", 2, 64, 64, 2, 16384, -1)   # no negative CTA size
 
 
 def test_tune_cache_rejects_bad_files(tmp_path):
