@@ -1130,6 +1130,34 @@ cudaError_t launch_persistent(const BatchJob* jobs, const int2* items, int n_ite
 cudaError_t launch_estimator_batch(const EstJob* jobs, int n_jobs, double* out, cudaStream_t st);
 }  // namespace jz
 
+// A job's layout inside the plan's CTAs of cta threads: the warp teams of
+// shape_for, or one team of the whole CTA when that keeps more of the CTA's
+// lanes busy (shape_score's barrier term).  A large lattice leaves most warps
+// of a warp-team CTA idle -- 2D L = 128 fits seven 32 KB lattices in a
+// 384-thread CTA -- and its shared memory would then set every CTA's, one
+// CTA per SM; as one team it holds one lattice.
+jz::LaunchShape plan_shape(const jz::Geom& g, int cta)
+{
+    const jz::LaunchShape w = shape_for(g, cta);
+    const int col = g.GW * g.Ly;
+    const int ts = std::min(cta / col, g.Lt);
+    if (ts < 1 || col * ts < 32) return w;
+    auto busy = [&](const jz::LaunchShape& sh) {
+        double b = (double)sh.teams * sh.team_threads / cta;
+        if (!sh.warp) {
+            const double rows = (double)g.nrep * g.Lt / std::min(sh.team_threads / col, g.Lt);
+            b *= rows / (rows + kBarrierRows);
+        }
+        return b;
+    };
+    jz::LaunchShape c{};
+    c.team_threads = col * ts;
+    c.teams = 1;
+    c.cta_threads = col * ts;
+    c.warp = 0;
+    return busy(c) > kKeepMargin * busy(w) ? c : w;
+}
+
 struct jz_plan {
     ising_ctx* ctx = nullptr;
     int n_jobs = 0, n_items = 0, threads = 0, grid = 0;
@@ -1236,7 +1264,7 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
         B.g = make_geom(p.d, p.L, p.L_t, nrep_of(p));
         B.D = p.d;
         B.fast = (B.g.Lh % 8) == 0;   // rows of whole 8-site words
-        B.sh = shape_for(B.g, cta);
+        B.sh = plan_shape(B.g, cta);
         B.lattice_words = 2 * B.g.NR * B.g.GW;
         if (!shape_fits(B.g) || B.sh.team_threads > cta || (B.sh.warp && B.sh.cta_threads > cta)) {
             plan_release(pl);

@@ -100,6 +100,26 @@ def test_persistent_batch_matches_oracle_sample(ctx):
         np.testing.assert_array_equal(o.cpu().numpy(), Wo)
 
 
+def test_plan_runs_a_wide_lattice_as_one_cta_team(ctx):
+    """2D L = 200 (41.6 KB per lattice): a 384-thread CTA holds only five of its
+    warp teams, so the plan runs it as one team of the whole CTA, beside small
+    lattices in warp teams; every job keeps the oracle's bits."""
+    jobs = [wl.Job(2, 200, 200, wl.BETA_C_2D, 50, 2, 1, 3, seed=7, n_therm=2, traj0=1 << 20),
+            wl.Job(2, 32, 32, wl.BETA_C_2D, 9, 6, 1, 40, seed=7, n_therm=5),
+            wl.Job(3, 8, 8, wl.BETA_C_3D, 3, 5, 1, 21, seed=7, n_therm=4, traj0=2 << 20)]
+    outs = [torch.empty(j.n_traj, dtype=torch.int64, device="cuda") for j in jobs]
+    plan = jz.jz_plan_create(ctx, [_params(j) for j in jobs], outs, None, 384)
+    try:
+        jz.jz_plan_launch(plan)
+        jz.ising_sync(ctx)
+    finally:
+        jz.jz_plan_free(plan)
+    for j, o in zip(jobs, outs):
+        Wo, _ = oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj, j.seed,
+                           n_therm=j.n_therm, direction=j.direction, traj0=j.traj0)
+        np.testing.assert_array_equal(o.cpu().numpy(), Wo)
+
+
 def test_plan_rejects_mixed_seeds_and_host_outputs(ctx):
     jobs = _uneven_jobs()[:3]
     outs = [torch.empty(j.n_traj, dtype=torch.int64, device="cuda") for j in jobs]
