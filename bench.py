@@ -822,6 +822,9 @@ def run_serve(args):
     updates = sum(r.updates for r in results)
     pct = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
 
+    waits = [r.start_s - r.submit_s for r in results]    # arrival order
+    pct_of = lambda v, q: sorted(v)[min(len(v) - 1, int(round(q * (len(v) - 1))))]
+
     def halves_p99(v):
         v = sorted(v)
         return v[min(len(v) - 1, int(round(0.99 * (len(v) - 1))))] if v else None
@@ -836,6 +839,11 @@ def run_serve(args):
             # a stable rate keeps the late arrivals' latency near the early ones'
             "latency_p99_by_half_s": [halves_p99(in_order[:len(in_order) // 2]),
                                       halves_p99(in_order[len(in_order) // 2:])],
+            # time from submission to admission (a free slot and memory); a stable
+            # rate keeps it bounded, whatever the sizes of the jobs
+            "queue_wait_s": {"p50": pct_of(waits, 0.50), "p99": pct_of(waits, 0.99)},
+            "queue_wait_p99_by_half_s": [halves_p99(waits[:len(waits) // 2]),
+                                         halves_p99(waits[len(waits) // 2:])],
             "trajectories_per_s": sum(j.n_traj for _, j in arrivals) / makespan,
             "jobs_failed": len(bad), "makespan_s": makespan, "clocks": clocks}
     print(json.dumps(line), flush=True)
