@@ -221,7 +221,8 @@ bool sw_fits(const jz::Geom& g)
     return jz::sw_smem_bytes(g) <= jz::kMaxSmemPerCta;
 }
 
-// Launch shape for lattices g in CTAs of cta_threads (0 = the default).  With
+// Launch shape for lattices g in CTAs of cta_threads (0: the base layout
+// that default_shape starts from, and the layout of lattices in HBM).  With
 // col = GW * L_y words per time slice, each thread owns one word column of
 // every TS-th slice.  col <= 32: warp teams of col * TS threads, TS =
 // min(32 / col, L_t), as many per CTA as fit (default CTA 128 threads).
