@@ -108,6 +108,13 @@ def _declare(lib):
         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
         ctypes.c_uint64, ctypes.c_longlong,
         ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.oracle_run_therm.restype = ctypes.c_int
+    lib.oracle_run_therm.argtypes = [
+        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+        ctypes.c_uint64, ctypes.c_longlong,
+        ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     lib.oracle_bond_threshold.restype = ctypes.c_uint32
     lib.oracle_bond_threshold.argtypes = [ctypes.c_double]
 
@@ -141,7 +148,7 @@ def bond_threshold(x: float) -> int:
 
 def run(d, L, L_t, beta, l, n_step, n_sweep, n_traj, seed, *, n_therm=1000,
         direction=1, traj0=0, n_threads=0, want_spins=False, lib=None, update=0,
-        protocol=1, n_replica=2, whole=False):
+        protocol=1, n_replica=2, whole=False, therm_update=None):
     """Run trajectories traj0..traj0+n_traj-1 of the transformation l -> l+1
     (direction=+1) or l+1 -> l (direction=-1); update 0 = checkerboard
     Metropolis, 1 = Swendsen-Wang clusters; protocol 1 switches every column
@@ -149,6 +156,8 @@ def run(d, L, L_t, beta, l, n_step, n_sweep, n_traj, seed, *, n_therm=1000,
     a multiple of L_y).  n_replica replicas; whole=True runs Alba et al.'s
     whole-cut transformation (columns x < l switch from decoupled to glued,
     1 <= l <= L) instead of moving the end of region A by one column.
+    therm_update (default: `update`) is the update of the n_therm
+    thermalisation sweeps; Appendix A needs only an equilibrium start.
 
     Returns (W_int int64[n_traj], spins int8[n_traj, n_replica, L_t, L_y, L] or None).
     Follows section 3 (replica geometry and linear protocol) and Appendix A
@@ -159,12 +168,13 @@ def run(d, L, L_t, beta, l, n_step, n_sweep, n_traj, seed, *, n_therm=1000,
     L_y = L if d == 3 else 1
     spins = (np.zeros((n_traj, n_replica, L_t, L_y, L), dtype=np.int8) if want_spins
              else None)
-    rc = lib.oracle_run_general(int(d), int(L), int(L_t), float(beta), int(l), int(n_step),
-                                int(n_sweep), int(n_therm), int(direction), int(update),
-                                int(protocol), int(n_replica), int(bool(whole)),
-                                int(seed) & 0xFFFFFFFFFFFFFFFF, int(traj0),
-                                int(n_traj), int(n_threads), work.ctypes.data,
-                                spins.ctypes.data if spins is not None else None)
+    th = int(update) if therm_update is None else int(therm_update)
+    rc = lib.oracle_run_therm(int(d), int(L), int(L_t), float(beta), int(l), int(n_step),
+                              int(n_sweep), int(n_therm), int(direction), int(update), th,
+                              int(protocol), int(n_replica), int(bool(whole)),
+                              int(seed) & 0xFFFFFFFFFFFFFFFF, int(traj0),
+                              int(n_traj), int(n_threads), work.ctypes.data,
+                              spins.ctypes.data if spins is not None else None)
     if rc != 0:
         raise ValueError("oracle_run rejected its arguments")
     return work, spins

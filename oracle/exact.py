@@ -435,19 +435,29 @@ def _propagate(F, de):
 
 
 def exact_path_measure(d, L, L_t, l, beta, n_step, n_sweep, n_therm, *, direction=1,
-                       quantised=True, start="hot", protocol=1, n=N_REPLICA, whole=False):
+                       quantised=True, start="hot", protocol=1, n=N_REPLICA, whole=False,
+                       therm="metropolis"):
     """Exact joint law of (W_int, final state) of the non-equilibrium dynamics.
 
     start="hot": uniform start (independent random spins) followed by n_therm
-    sweeps at the start geometry, as the Monte Carlo trajectories do;
-    start="equilibrium": exact Boltzmann weights pi_{lambda_0} (Appendix A,
-    eq. equilibrium_distribution), for the Jarzynski identity.
+    sweeps at the start geometry, as the Monte Carlo trajectories do --
+    Metropolis sweeps, or with therm="sw" exact Swendsen-Wang steps (Appendix A
+    asks only for an equilibrium start; section 4 thermalises with cluster
+    steps); start="equilibrium": exact Boltzmann weights pi_{lambda_0}
+    (Appendix A, eq. equilibrium_distribution), for the Jarzynski identity.
+    The protocol sweeps are Metropolis sweeps.
     Returns (w_values, F) with F[w_index, state] the probability.
     """
     dyn = _Dynamics(d, L, L_t, l, beta, n_step, direction, quantised, protocol, n, whole)
     n_states = 1 << dyn.V
     lam0 = 0.0 if direction > 0 else 1.0
-    if start == "hot":
+    if start == "hot" and therm == "sw":
+        f = np.full(n_states, 1.0 / n_states)
+        T0 = _SWDynamics(d, L, L_t, l, beta, n_step, direction, quantised, protocol, n,
+                         whole).kernel(None)
+        for _ in range(n_therm):
+            f = f @ T0
+    elif start == "hot":
         f = np.full(n_states, 1.0 / n_states)
         for _ in range(n_therm):
             f = dyn.sweep(f, None)

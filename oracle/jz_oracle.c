@@ -19,7 +19,9 @@
  *   - the column x = l is switched: its self links carry beta (1 - lambda), its
  *     glue links beta lambda, lambda_k = k/N (section 3, linear protocol);
  *   - each trajectory: independent hot start, n_therm checkerboard Metropolis
- *     sweeps at lambda_0, then for k = 0..N-1: accumulate
+ *     sweeps at lambda_0 (or Swendsen-Wang sweeps, therm_upd = 1: Appendix A
+ *     asks only for an equilibrium start, and section 4 thermalises with
+ *     cluster steps), then for k = 0..N-1: accumulate
  *     dW_k = H_{lambda_{k+1}}[phi_k] - H_{lambda_k}[phi_k] (Appendix A, eq.
  *     work_in_one_MC_step) and update with the kernel at lambda_{k+1} (the
  *     remark after eq. discretized_average_exp_work).
@@ -231,6 +233,7 @@ typedef struct {
     int prot;             /* 1 all columns together, 2 one column y at a time */
     int m;                /* protocol 2: steps per column, N / L_y; protocol 1: N */
     int update;           /* 0 checkerboard Metropolis, 1 Swendsen-Wang */
+    int therm_update;     /* the update of the thermalisation sweeps */
     uint32_t key[2];
     uint32_t bulk_T[8];   /* indexed by m/2 for m = 2, 4, ..., 2d */
     const uint32_t *cut_T; /* [n_step][table], see cut_index() */
@@ -457,22 +460,22 @@ static void hot_start(const run_t *R, int8_t *s, long long traj)
     }
 }
 
-static void update(const run_t *R, int8_t *s, int *parent, long long traj, int sweep_index,
-                   int k)
+static void update(const run_t *R, int upd, int8_t *s, int *parent, long long traj,
+                   int sweep_index, int k)
 {
-    if (R->update == 1) sw_sweep(R, s, parent, traj, sweep_index, k);
+    if (upd == 1) sw_sweep(R, s, parent, traj, sweep_index, k);
     else sweep(R, s, traj, sweep_index, k);
 }
 
 static long long run_trajectory(const run_t *R, long long traj, int8_t *s, int *parent)
 {
     hot_start(R, s, traj);
-    for (int i = 0; i < R->n_therm; ++i) update(R, s, parent, traj, i, -1);
+    for (int i = 0; i < R->n_therm; ++i) update(R, R->therm_update, s, parent, traj, i, -1);
     long long w = 0;
     for (int k = 0; k < R->n_step; ++k) {
         if (ORACLE_MUTANT != 2) w += work_increment(R, s, k);
         for (int i = 0; i < R->n_sweep; ++i)
-            update(R, s, parent, traj, R->n_therm + k * R->n_sweep + i, k);
+            update(R, R->update, s, parent, traj, R->n_therm + k * R->n_sweep + i, k);
         if (ORACLE_MUTANT == 2) w += work_increment(R, s, k);
     }
     return w;
@@ -490,15 +493,18 @@ static long long run_trajectory(const run_t *R, long long traj, int8_t *s, int *
  * l switching); whole = 1: Alba et al.'s whole-cut transformation from n
  * decoupled replicas to replicas glued along x < l (columns 0 .. l-1 switching,
  * 1 <= l <= L; section 3, eq. off-equilibrium_evolution_of_the_couplings).
- * n_threads > 0 sets the OpenMP thread count (trajectories are independent, so
- * the result does not depend on it).  Returns 0, or -1 on bad arguments. */
-int oracle_run_general(int d, int L, int Lt, double beta, int l, int n_step, int n_sweep,
-                       int n_therm, int dir, int upd, int prot, int n_rep, int whole,
-                       uint64_t seed, long long traj0, int n_traj, int n_threads,
-                       long long *work_out, int8_t *spins_out)
+ * therm_upd selects the update of the thermalisation sweeps (0 Metropolis, 1
+ * Swendsen-Wang).  n_threads > 0 sets the OpenMP thread count (trajectories are
+ * independent, so the result does not depend on it).  Returns 0, or -1 on bad
+ * arguments. */
+int oracle_run_therm(int d, int L, int Lt, double beta, int l, int n_step, int n_sweep,
+                     int n_therm, int dir, int upd, int therm_upd, int prot, int n_rep,
+                     int whole, uint64_t seed, long long traj0, int n_traj, int n_threads,
+                     long long *work_out, int8_t *spins_out)
 {
     if ((d != 2 && d != 3) || L < 2 || Lt < 2 || (L & 1) || (Lt & 1)) return -1;
     if (upd != 0 && upd != 1) return -1;
+    if (therm_upd != 0 && therm_upd != 1) return -1;
     if (prot != 1 && prot != 2) return -1;
     if (n_rep < 2 || n_rep > 16 || (whole != 0 && whole != 1)) return -1;
     if (whole ? (l < 1 || l > L || prot != 1) : (l < 0 || l >= L)) return -1;
@@ -534,6 +540,7 @@ int oracle_run_general(int d, int L, int Lt, double beta, int l, int n_step, int
     /* Swendsen-Wang bond thresholds: full links x = 2 beta, switched links at
      * step k: x = (2 beta w)/den with w = w_self or w_glue of lambda_{k+1} */
     R.update = upd;
+    R.therm_update = therm_upd;
     R.bond_full = quantise_bond(2.0 * beta);
     uint32_t *bonds = (uint32_t *)malloc(sizeof(uint32_t) * 2 * (size_t)n_step);
     if (!bonds) { free(cut); return -1; }
@@ -573,6 +580,16 @@ int oracle_run_general(int d, int L, int Lt, double beta, int l, int n_step, int
     free(cut);
     free(bonds);
     return failed ? -1 : 0;
+}
+
+/* Thermalisation with the protocol's own update. */
+int oracle_run_general(int d, int L, int Lt, double beta, int l, int n_step, int n_sweep,
+                       int n_therm, int dir, int upd, int prot, int n_rep, int whole,
+                       uint64_t seed, long long traj0, int n_traj, int n_threads,
+                       long long *work_out, int8_t *spins_out)
+{
+    return oracle_run_therm(d, L, Lt, beta, l, n_step, n_sweep, n_therm, dir, upd, upd, prot,
+                            n_rep, whole, seed, traj0, n_traj, n_threads, work_out, spins_out);
 }
 
 /* Two replicas, shift mode. */
