@@ -372,7 +372,8 @@ def fractions(ops_per_s, updates_per_s, ceil):
 
 def job_params(jz, j, **over):
     kw = dict(n_therm=j.n_therm, direction=j.direction, traj0=j.traj0, update=j.update,
-              protocol=j.protocol, n_replica=j.n_replica, whole=j.whole)
+              protocol=j.protocol, n_replica=j.n_replica, whole=j.whole,
+              therm_update=j.therm_update)
     kw.update(over)
     return jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj, j.seed,
                           **kw)
@@ -537,17 +538,19 @@ def pulls(test, ref):
 
 def bias_and_cost(jz, torch, ctx, stream, dev, headline_w, headline_cfun, headline_ms, args):
     """Thermalisation bias of the 2D L = 64 scan and the cost of a c-function
-    at fixed error for both updates.  A Jarzynski estimate is unbiased only from
+    at fixed error for both updates, and for Metropolis protocols started by
+    Swendsen-Wang thermalisation.  A Jarzynski estimate is unbiased only from
     an equilibrium start (Appendix A), so each scan's per-l c-function is pulled
     against a Swendsen-Wang reference with 1000 cluster sweeps of
     thermalisation (the paper's set-up, section 4) on independent
-    trajectories; each update's cost is the time to reach the headline's rms
+    trajectories; each choice's cost is the time to reach the headline's rms
     c-function error at the smallest tested n_therm whose pulls pass."""
     nref = args.bias_traj
     base = headline_w.jobs
 
-    def run(tag, update, n_therm, n_traj, traj0):
-        jobs = [j.with_(update=update, n_therm=n_therm, n_traj=n_traj, traj0=traj0) for j in base]
+    def run(tag, update, n_therm, n_traj, traj0, therm_update=0):
+        jobs = [j.with_(update=update, n_therm=n_therm, n_traj=n_traj, traj0=traj0,
+                        therm_update=therm_update) for j in base]
         w = wl.Workload(f"{headline_w.name}_{tag}", jobs)
         outs = [torch.empty(n_traj, dtype=torch.int64, device=dev) for _ in jobs]
         ps = [job_params(jz, j) for j in jobs]
@@ -567,7 +570,8 @@ def bias_and_cost(jz, torch, ctx, stream, dev, headline_w, headline_cfun, headli
     head = {"cfun": headline_cfun, "kernel_ms": headline_ms, "n_traj_per_l": base[0].n_traj,
             "n_therm": base[0].n_therm}
     cands = {"metropolis": [head, run("m4000", 0, 4000, 2 * nref, 2 << 28)],
-             "sw": [run("sw100", 1, 100, nref, 3 << 28)]}
+             "sw": [run("sw100", 1, 100, nref, 3 << 28)],
+             "sw_therm_metropolis": [run("h100", 0, 100, 2 * nref, 4 << 28, therm_update=1)]}
     target = rms(headline_cfun)
     out = {"reference": f"Swendsen-Wang, n_therm = 1000, {nref} trajectories per l "
                         f"(independent of the headline's)",
@@ -595,9 +599,14 @@ def bias_and_cost(jz, torch, ctx, stream, dev, headline_w, headline_cfun, headli
                           "trajectories_per_l_at_target": need,
                           "seconds_at_target": seconds})
         cost[upd] = entry
-    if all("seconds_at_target" in c for c in cost.values()):
+    if "seconds_at_target" in cost["sw"] and "seconds_at_target" in cost["metropolis"]:
         cost["sw_over_metropolis_time_at_target"] = (cost["sw"]["seconds_at_target"] /
                                                      cost["metropolis"]["seconds_at_target"])
+    if ("seconds_at_target" in cost["sw_therm_metropolis"] and
+            "seconds_at_target" in cost["metropolis"]):
+        cost["sw_therm_over_metropolis_time_at_target"] = (
+            cost["sw_therm_metropolis"]["seconds_at_target"] /
+            cost["metropolis"]["seconds_at_target"])
     out["cost_at_fixed_error"] = cost
     return out
 

@@ -117,7 +117,21 @@ typedef struct ising_ctx ising_ctx;
  *              switch together from n decoupled replicas to glued ones
  *              (1 <= l <= L, protocol 1 only), so <e^-W> = Z_n(l)/Z^n and
  *              -ln<e^-W> = (n-1) S_n(l).  jarzynski_run_plain refuses
- *              n_replica != 2 and whole = 1 (ISING_ERR_UNSUPPORTED). */
+ *              n_replica != 2 and whole = 1 (ISING_ERR_UNSUPPORTED).
+ *   therm_update  the update of the n_therm thermalisation sweeps: 0 (the
+ *              default) the protocol's own `update`; 1 Swendsen-Wang clusters
+ *              before a Metropolis protocol.  Jarzynski's identity needs only
+ *              an equilibrium start and sweeps that keep each step's Boltzmann
+ *              weight (Appendix A), and section 4 thermalises with cluster
+ *              steps, which decorrelate at criticality where Metropolis sweeps
+ *              do not.  The thermalisation sweeps then take the Swendsen-Wang
+ *              random stream of their sweep indices 0 .. n_therm-1, the
+ *              protocol sweeps the Metropolis stream of theirs, as in one run
+ *              of each update.  Served by jarzynski_run_ex, jarzynski_run_batch
+ *              and jarzynski_run_segment (a segment from k_begin = 0), for
+ *              lattices whose Swendsen-Wang state fits shared memory; the other
+ *              entry points return ISING_ERR_UNSUPPORTED.  Other values:
+ *              ISING_ERR_ARG. */
 typedef struct jz_params {
     int d, L, L_t;
     int update;
@@ -131,10 +145,12 @@ typedef struct jz_params {
     int protocol;
     int n_replica;
     int whole;
+    int therm_update;
 } jz_params;
 
 /* Fills *p with defaults (n_therm = 1000, direction = +1, traj0 = 0, n_sweep = 1,
- * seed = 0, update = 0, protocol = 1, n_replica = 2, whole = 0) and zero sizes;
+ * seed = 0, update = 0, protocol = 1, n_replica = 2, whole = 0, therm_update = 0)
+ * and zero sizes;
  * returns ISING_OK or ISING_ERR_ARG for p == NULL. */
 int jz_params_default(jz_params* p);
 

@@ -50,7 +50,7 @@ class JzParams(ctypes.Structure):
         ("n_step", ctypes.c_int), ("n_sweep", ctypes.c_int), ("n_therm", ctypes.c_int),
         ("n_traj", ctypes.c_int), ("direction", ctypes.c_int),
         ("traj0", ctypes.c_longlong), ("seed", ctypes.c_uint64), ("protocol", ctypes.c_int),
-        ("n_replica", ctypes.c_int), ("whole", ctypes.c_int),
+        ("n_replica", ctypes.c_int), ("whole", ctypes.c_int), ("therm_update", ctypes.c_int),
     ]
 
 
@@ -225,13 +225,17 @@ def jarzynski_run(ctx, d, L, L_t, beta, l, n_step, n_sweep, n_traj, seed, work_i
 
 
 METROPOLIS, SWENDSEN_WANG = 0, 1
+SW_THERM = 1   # jz_params.therm_update: Swendsen-Wang thermalisation
 
 
 def make_params(d, L, L_t, beta, l, n_step, n_sweep, n_traj, seed=0, *, n_therm=1000,
                 direction=1, traj0=0, update=METROPOLIS, protocol=1, n_replica=2,
-                whole=False) -> JzParams:
+                whole=False, therm_update=0) -> JzParams:
+    """therm_update=SW_THERM thermalises with Swendsen-Wang clusters before a
+    Metropolis protocol (see include/isingjz.h)."""
     p = jz_params_default()
     p.update = int(update)
+    p.therm_update = int(therm_update)
     p.protocol = int(protocol)
     p.n_replica = int(n_replica)
     p.whole = int(bool(whole))

@@ -73,6 +73,7 @@ int check_params(const jz_params* p)
     if (p->whole ? (p->l < 1 || p->l > p->L) : (p->l < 0 || p->l > p->L - 1))
         return ISING_ERR_L_RANGE;
     if (p->whole && p->protocol == 2) return ISING_ERR_ARG;
+    if (p->therm_update != 0 && p->therm_update != 1) return ISING_ERR_ARG;
     if (p->n_step < 1 || p->n_sweep < 1 || p->n_therm < 0 || p->n_traj < 1)
         return ISING_ERR_ARG;
     if (p->direction != 1 && p->direction != -1) return ISING_ERR_ARG;
@@ -93,6 +94,10 @@ int check_params(const jz_params* p)
 }
 
 int nrep_of(const jz_params& p) { return p.n_replica == 0 ? 2 : p.n_replica; }
+
+// Whether p thermalises with Swendsen-Wang clusters before a Metropolis
+// protocol (with no thermalisation sweeps the two are the same run).
+bool sw_therm(const jz_params& p) { return p.update == 0 && p.therm_update == 1 && p.n_therm > 0; }
 
 // Switching columns of a job: [l, l+1) when the end of region A moves by one
 // column, [0, l) for the whole-cut transformation.
@@ -420,6 +425,11 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
     if (!sw && !threads_fit(g)) return ISING_ERR_UNSUPPORTED;
     // lattices beyond shared memory run from HBM, one slice per CTA
     const bool in_hbm = sw ? !sw_fits(g) : !shape_fits(g);
+    // Swendsen-Wang thermalisation before a Metropolis protocol run from k = 0:
+    // a thermalisation-only sw_kernel launch leaves every trajectory's spins in
+    // ctx->therm, from which the Metropolis protocol starts
+    const bool hybrid = sw_therm(p0) && (!seg || seg->k_begin == 0);
+    if (hybrid && !sw_fits(g)) return ISING_ERR_UNSUPPORTED;
     long long n_traj_launch = 0;
     for (int j : idx) n_traj_launch += jobs[j].n_traj;
     jz::LaunchShape sh = sw ? shape_for(g, 0) : ctx_shape(ctx, p0.d, g, n_traj_launch);
@@ -445,6 +455,10 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
     if (n_spin_traj && !spins_on_device &&
         (rc = ensure(ctx, ctx->spins, (size_t)n_spin_traj * V)))
         return rc;
+    if (hybrid) {
+        if ((rc = ensure(ctx, ctx->therm, (size_t)n_traj_all * V))) return rc;
+        if ((rc = ensure(ctx, ctx->jobs, (size_t)2 * n_jobs * sizeof(jz::JobDesc)))) return rc;
+    }
 
     const Range nv_group("jz run group");
     nvtxRangePushA("jz tables");   // host FP64 threshold tables (popped after the loop)
@@ -467,6 +481,11 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
         J.k_end = seg ? seg->k_end : p.n_step;
         J.spins_in = seg ? seg->spins_in : nullptr;
         J.w_in = seg ? seg->w_in : nullptr;
+        J.start_in = 0;
+        if (hybrid) {
+            J.spins_in = (const int8_t*)ctx->therm.ptr + traj_off * (long long)V;
+            J.start_in = 1;
+        }
         J.n_traj = p.n_traj;
         J.traj0 = p.traj0;
         J.cta0 = cta;
@@ -484,19 +503,48 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
         cta += (p.n_traj + sh.teams - 1) / sh.teams;
         traj_off += p.n_traj;
     }
+    if (hybrid) {
+        // the thermalisation jobs: Swendsen-Wang bulk bond threshold at the
+        // start geometry, no protocol steps (k_end = 0, so no step table is
+        // read), final spins into ctx->therm; their W_int (zero) lands in the
+        // outputs that the protocol launch then overwrites
+        ctx->h_jobs.resize((size_t)2 * n_jobs);
+        std::vector<uint32_t> bt;
+        long long sw_cta = 0;
+        for (int i = 0; i < n_jobs; ++i) {
+            const jz_params& p = jobs[idx[i]];
+            jz::JobDesc T = ctx->h_jobs[i];
+            bt.assign((size_t)2 * p.n_step, 0u);
+            build_bond_tables(p, T.tb, bt, 0);
+            T.k_begin = 0;
+            T.k_end = 0;
+            T.start_in = 0;
+            T.spins_in = nullptr;
+            T.w_in = nullptr;
+            T.spins_out = (int8_t*)ctx->h_jobs[i].spins_in;   // this job's slice of ctx->therm
+            T.cta0 = sw_cta;
+            sw_cta += T.n_traj;
+            ctx->h_jobs[n_jobs + i] = T;
+        }
+    }
     nvtxRangePop();
     cudaStream_t st = ctx->stream;
     if ((rc = cuda_err(cudaMemcpyAsync(ctx->tcut.ptr, ctx->h_tcut.data(),
                                        n_tcut * sizeof(uint32_t), cudaMemcpyHostToDevice, st))))
         return rc;
     if ((rc = cuda_err(cudaMemcpyAsync(ctx->jobs.ptr, ctx->h_jobs.data(),
-                                       n_jobs * sizeof(jz::JobDesc), cudaMemcpyHostToDevice, st))))
+                                       ctx->h_jobs.size() * sizeof(jz::JobDesc),
+                                       cudaMemcpyHostToDevice, st))))
         return rc;
     const jz::PhiloxKeys K = key_schedule(p0.seed);
     if (ctx->k_open) {
         if ((rc = cuda_err(cudaEventRecord(ctx->ev_k0, st)))) return rc;
         ctx->k_open = false;
     }
+    if (hybrid &&
+        (rc = cuda_err(jz::launch_sw(p0.d, g, K, (const jz::JobDesc*)ctx->jobs.ptr + n_jobs,
+                                     n_jobs, n_traj_all, st, nullptr))))
+        return rc;
     if (sw) {
         uint32_t* gS = nullptr;
         if (in_hbm) {
@@ -568,12 +616,14 @@ int run_jobs(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const* 
             if (first) { spins_dev = dv; first = false; }
             else if (dv != spins_dev) return ISING_ERR_ARG;
         }
-    // one launch per (d, L, L_t, seed, update, n), jobs kept in call order within a group
-    std::map<std::tuple<int, int, int, uint64_t, int, int>, std::vector<int>> groups;
-    std::vector<std::tuple<int, int, int, uint64_t, int, int>> order;
+    // one launch per (d, L, L_t, seed, update, n, thermalising update), jobs
+    // kept in call order within a group
+    using Key = std::tuple<int, int, int, uint64_t, int, int, int>;
+    std::map<Key, std::vector<int>> groups;
+    std::vector<Key> order;
     for (int j = 0; j < n_jobs; ++j) {
         auto key = std::make_tuple(jobs[j].d, jobs[j].L, jobs[j].L_t, jobs[j].seed,
-                                   jobs[j].update, nrep_of(jobs[j]));
+                                   jobs[j].update, nrep_of(jobs[j]), (int)sw_therm(jobs[j]));
         auto it = groups.find(key);
         if (it == groups.end()) {
             order.push_back(key);
@@ -759,6 +809,7 @@ int ising_autotune(ising_ctx* ctx, const jz_params* p, int* threads)
     s.n_therm = 16;
     s.n_step = 16;
     s.n_sweep = 1;
+    s.therm_update = 0;   // the launch shape is the protocol kernel's
     s.n_traj = p->n_traj < 4864 ? p->n_traj : 4864;
     s.traj0 = 0;
     if ((rc = ensure(ctx, ctx->est_in, (size_t)s.n_traj * sizeof(long long)))) return rc;
@@ -849,7 +900,8 @@ int jarzynski_run_plain(ising_ctx* ctx, const jz_params* p, int64_t* work_int_ou
     if (ctx->cancel.load()) return ISING_ERR_CANCELLED;
     int rc = check_params(p);
     if (rc) return rc;
-    if (p->update != 0 || (p->protocol == 2 && p->d == 3) || nrep_of(*p) != 2 || p->whole)
+    if (p->update != 0 || (p->protocol == 2 && p->d == 3) || nrep_of(*p) != 2 || p->whole ||
+        sw_therm(*p))
         return ISING_ERR_UNSUPPORTED;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ISING_ERR_CUDA;
     const jz::Geom g = make_geom(p->d, p->L, p->L_t, 2);
@@ -1071,6 +1123,7 @@ extern "C" int jarzynski_run_noalloc(const jz_params* p, int64_t* work_int_out, 
     if (!p || !work_int_out) return ISING_ERR_ARG;
     int rc = check_params(p);
     if (rc) return rc;
+    if (sw_therm(*p)) return ISING_ERR_UNSUPPORTED;
     const bool sw = p->update == 1;   // Swendsen-Wang: one trajectory per CTA
     const size_t n_tcut = (size_t)p->n_step * (sw ? 2 : 8 * (size_t)p->d);
     if (n_tcut > kNoAllocMaxThresholds) return ISING_ERR_SCRATCH_LIMIT;
@@ -1445,6 +1498,7 @@ int jz_plan_create(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* c
     for (int j = 0; j < n_jobs; ++j) {
         const int rc = check_params(&jobs[j]);
         if (rc) return rc;
+        if (sw_therm(jobs[j])) return ISING_ERR_UNSUPPORTED;
         if (jobs[j].seed != jobs[0].seed || !work_outs[j] || !is_device_ptr(work_outs[j]))
             return ISING_ERR_ARG;
     }

@@ -80,7 +80,8 @@ struct JobDesc {
     int prot;           // 1: every switched column together; 2: one column y at a time
     int g0, g1;         // columns x < g0 glued, g0 <= x < g1 switching, x >= g1 self
     int k_begin, k_end; // protocol steps run: [k_begin, k_end); 0 starts from the hot start
-    const int8_t* spins_in;     // k_begin > 0: [n_traj][V] state after step k_begin - 1
+    int start_in;       // 1: step k_begin = 0 starts from spins_in (thermalised elsewhere)
+    const int8_t* spins_in;     // k_begin > 0 or start_in: [n_traj][V] state after step k_begin - 1
     const long long* w_in;      // k_begin > 0: [n_traj] W_int of steps 0 .. k_begin - 1
     long long traj0;    // global index of the job's first trajectory
     long long cta0;     // first CTA of the job in the launch grid

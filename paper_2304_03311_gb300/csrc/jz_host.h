@@ -66,6 +66,7 @@ struct ising_ctx {
     size_t used = 0;
     DevBuf tcut, jobs, work, spins, est_in, est_out;
     DevBuf lattice;   // HBM lattices of shapes too large for shared memory
+    DevBuf therm;     // spins after Swendsen-Wang thermalisation (therm_update = 1)
     std::vector<uint32_t> h_tcut;
     std::vector<jz::JobDesc> h_jobs;
     std::map<std::tuple<int, int, int>, int> threads;   // per-shape CTA size (tuned)
@@ -105,6 +106,7 @@ void step_weights(const jz_params& p, long long k, long long* den, long long* w_
 void build_bond_tables(const jz_params& p, uint32_t tb[4], std::vector<uint32_t>& tcut,
                        size_t off);
 bool sw_fits(const jz::Geom& g);
+bool sw_therm(const jz_params& p);
 jz::LaunchShape shape_for(const jz::Geom& g, int cta_threads);
 bool shape_fits(const jz::Geom& g);
 bool threads_fit(const jz::Geom& g);

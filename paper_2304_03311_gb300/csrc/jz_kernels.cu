@@ -55,7 +55,7 @@ traj_kernel(const Geom g, const PhiloxKeys K, const JobDesc* __restrict__ jobs, 
     __syncthreads();
     const long long traj = __ldg(&J.traj0) + local;
     const long long V = (long long)g.nrep * g.Lt * g.Ly * g.L;
-    const int8_t* sin = (has && tj.k_begin > 0) ? J.spins_in + local * V : nullptr;
+    const int8_t* sin = (has && (tj.k_begin > 0 || tj.start_in)) ? J.spins_in + local * V : nullptr;
     int dE;
     // The one-row pipeline is compiled into the 2D GW = 1 variant (L <= 16),
     // the only lattice whose warp team can hold a thread per word.

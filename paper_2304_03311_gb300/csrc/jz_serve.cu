@@ -306,6 +306,7 @@ int jz_submit(jz_server* s, const jz_params* p, uint64_t* job_id)
     if (!s || !p || !job_id) return ISING_ERR_ARG;
     int rc = check_params(p);
     if (rc) return rc;
+    if (sw_therm(*p)) return ISING_ERR_UNSUPPORTED;
     const jz::Geom g = make_geom(p->d, p->L, p->L_t, nrep_of(*p));
     if (p->update == 1 ? !sw_fits(g) : !shape_fits(g)) return ISING_ERR_UNSUPPORTED;
     std::unique_ptr<Job> j(new (std::nothrow) Job());

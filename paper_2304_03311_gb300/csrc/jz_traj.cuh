@@ -70,6 +70,7 @@ __device__ __forceinline__ uint32_t word8(const uint4& ua, const uint4& ub, int 
 struct TeamJob {
     int l, n_step, n_sweep, n_therm, dir;
     int k_begin, k_end;   // protocol steps run; k_begin > 0 resumes from stored spins
+    int start_in;         // 1: step k_begin = 0 starts from stored (thermalised) spins
     int g0, g1;   // columns x < g0 glued, g0 <= x < g1 switching, x >= g1 self
     int prot;     // 1: every switched column together; 2: one column y at a time
     int den;      // steps of one column's run: N (protocol 1), N / L_y (protocol 2)
@@ -434,7 +435,7 @@ struct WarpBarrier {
 // marks a thread without sites.  Returns this thread's share of sum_k dE_k
 // (the caller applies the direction's sign and, in protocol 2, the factor L_y
 // that makes W = (beta/N) W_int).
-// sin: the stored state to resume from when J.k_begin > 0 (else unused).
+// sin: the stored state to start from when J.k_begin > 0 or J.start_in (else unused).
 // ROW: every thread owns one row of each colour (the team has a thread per
 // word); each half-sweep then draws the next one's Philox blocks beside its
 // own update, so the independent chains cover the latency of the
@@ -451,8 +452,8 @@ __device__ __forceinline__ int run_trajectory(const Geom& g, const PhiloxKeys& K
     int dE = 0;
     // the global sweep index: thermalisation sweeps 0 .. n_therm - 1, then
     // protocol sweep i of step k is n_therm + k n_sweep + i
-    uint32_t s = J.k_begin > 0 ? (uint32_t)J.n_therm + (uint32_t)J.k_begin * (uint32_t)J.n_sweep
-                               : 0u;
+    const bool resume = J.k_begin > 0 || J.start_in;
+    uint32_t s = resume ? (uint32_t)J.n_therm + (uint32_t)J.k_begin * (uint32_t)J.n_sweep : 0u;
     uint4 ua, ub;   // ROW: the blocks of the coming half-sweep
     if constexpr (ROW) tr.row_draw(s, 0, ua, ub);
     auto half = [&](int c, int kk, int lg, int ws, int wg, bool rec) {
@@ -467,7 +468,7 @@ __device__ __forceinline__ int run_trajectory(const Geom& g, const PhiloxKeys& K
         }
         bar();
     };
-    if (J.k_begin > 0) {
+    if (resume) {
         if (tid >= 0) tr.import_spins(sin);
         bar();
     } else {
@@ -533,6 +534,7 @@ __device__ __forceinline__ TeamJob team_job(const JobDesc& J, int ly)
     t.prot = __ldg(&J.prot);
     t.k_begin = __ldg(&J.k_begin);
     t.k_end = __ldg(&J.k_end);
+    t.start_in = __ldg(&J.start_in);
     t.g0 = __ldg(&J.g0);
     t.g1 = __ldg(&J.g1);
     t.den = t.prot == 2 ? t.n_step / ly : t.n_step;

@@ -38,6 +38,7 @@ class Job:
     protocol: int = 1        # 1 every switched column together, 2 one column at a time
     n_replica: int = 2       # replicas n
     whole: bool = False      # True: whole-cut transformation of the columns x < l
+    therm_update: int = 0    # 1: Swendsen-Wang thermalisation before a Metropolis protocol
 
     @property
     def sites(self) -> int:

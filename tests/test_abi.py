@@ -55,17 +55,41 @@ def test_device_code_is_built_for_sm103a_only():
 
 
 def test_struct_layout_matches_header(lib):
-    # jz_params: 4 ints, double, 6 ints, long long, uint64, 3 ints (+4 padding) -> 80 bytes
+    # jz_params: 4 ints, double, 6 ints, long long, uint64, 4 ints -> 80 bytes
     assert ctypes.sizeof(jz.JzParams) == 80
     offs = {name: getattr(jz.JzParams, name).offset for name, _ in jz.JzParams._fields_}
     assert offs == {"d": 0, "L": 4, "L_t": 8, "update": 12, "beta": 16, "l": 24, "n_step": 28,
                     "n_sweep": 32, "n_therm": 36, "n_traj": 40, "direction": 44, "traj0": 48,
-                    "seed": 56, "protocol": 64, "n_replica": 68, "whole": 72}
+                    "seed": 56, "protocol": 64, "n_replica": 68, "whole": 72,
+                    "therm_update": 76}
     p = jz.jz_params_default()
     assert (p.n_therm, p.n_sweep, p.direction, p.traj0, p.seed) == (1000, 1, 1, 0, 0)
     assert p.update == jz.METROPOLIS
     assert p.protocol == 1
-    assert (p.n_replica, p.whole) == (2, 0)
+    assert (p.n_replica, p.whole, p.therm_update) == (2, 0, 0)
+
+
+def test_struct_layout_as_the_c_compiler_lays_it_out(tmp_path):
+    """The ctypes mirror of jz_params against offsetof / sizeof from gcc on the
+    header itself."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    names = [n for n, _ in jz.JzParams._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"isingjz.h\"\n"
+                   "int main(void) {\n  printf(\"%zu\\n\", sizeof(jz_params));\n" +
+                   "".join(f'  printf("%zu\\n", offsetof(jz_params, {n}));\n' for n in names) +
+                   "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([gcc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    assert got[0] == ctypes.sizeof(jz.JzParams)
+    assert got[1:] == [getattr(jz.JzParams, n).offset for n in names]
 
 
 def test_strerror_and_host_only_entry_points(lib):

@@ -1,0 +1,153 @@
+"""GPU parity of the Swendsen-Wang thermalisation option (therm_update = 1):
+a thermalisation-only sw_kernel launch, then the Metropolis protocol from its
+spins, against the oracle's single trajectory of the same composition.
+
+Bit-exact W_int and final spins on 2D and 3D shapes (ragged rows, reverse,
+protocol 2, n = 3 replicas, whole cuts), inside a batch beside plain jobs, as
+segments resumed mid-protocol, and with no thermalisation sweeps (then the
+plain Metropolis run).  Entry points that do not serve it refuse it.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="no CUDA device")]
+
+import paper_2304_03311_gb300 as jz  # noqa: E402
+from paper_2304_03311_gb300 import build as jzbuild  # noqa: E402
+from paper_2304_03311_gb300 import workloads as wl  # noqa: E402
+
+BC2, BC3 = wl.BETA_C_2D, wl.BETA_C_3D
+H = jz.SW_THERM
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    jzbuild.build()
+    c = jz.ising_replica_init(0, 0, None)
+    yield c
+    jz.ising_replica_free(c)
+
+
+def params(j, **kw):
+    return jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep,
+                          kw.get("n_traj", j.n_traj), j.seed, n_therm=j.n_therm,
+                          direction=j.direction, traj0=j.traj0, protocol=j.protocol,
+                          n_replica=j.n_replica, whole=j.whole,
+                          therm_update=kw.get("therm_update", j.therm_update))
+
+
+def oracle_run(j, therm_update=None):
+    W, S = oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj, j.seed,
+                      n_therm=j.n_therm, direction=j.direction, traj0=j.traj0,
+                      want_spins=True, protocol=j.protocol, n_replica=j.n_replica,
+                      whole=j.whole,
+                      therm_update=j.therm_update if therm_update is None else therm_update)
+    return W, S.reshape(len(W), -1)
+
+
+def gpu_run(ctx, j, **kw):
+    w = torch.empty(j.n_traj, dtype=torch.int64, device="cuda")
+    s = torch.empty(j.n_traj * j.sites, dtype=torch.int8, device="cuda")
+    jz.jarzynski_run_ex(ctx, params(j, **kw), w, s)
+    jz.ising_sync(ctx)
+    return w.cpu().numpy(), s.cpu().numpy().reshape(j.n_traj, -1)
+
+
+JOBS = [
+    wl.Job(2, 16, 16, BC2, 4, 12, 1, 40, seed=1, n_therm=20, therm_update=H),
+    wl.Job(2, 12, 6, 0.5, 0, 7, 2, 33, seed=5, n_therm=5, direction=-1, therm_update=H),
+    wl.Job(2, 64, 64, BC2, 30, 5, 2, 6, seed=0, n_therm=8, therm_update=H),
+    wl.Job(2, 34, 8, 0.45, 17, 5, 1, 6, seed=9, n_therm=3, therm_update=H),
+    wl.Job(3, 4, 4, BC3, 1, 6, 1, 20, seed=11, n_therm=5, therm_update=H),
+    wl.Job(3, 6, 4, 0.25, 5, 4, 1, 9, seed=12, n_therm=3, direction=-1, therm_update=H),
+    wl.Job(3, 4, 4, BC3, 2, 8, 1, 10, seed=13, n_therm=4, protocol=2, therm_update=H),
+    wl.Job(2, 8, 8, BC2, 3, 6, 1, 12, seed=14, n_therm=6, n_replica=3, therm_update=H),
+    wl.Job(2, 8, 8, BC2, 3, 6, 1, 12, seed=15, n_therm=6, whole=True, therm_update=H),
+    wl.Job(2, 16, 8, BC2, 3, 9, 1, 12, seed=2**64 - 1, n_therm=3, traj0=123456,
+           therm_update=H),
+]
+
+
+@pytest.mark.parametrize("job", JOBS, ids=lambda j: f"d{j.d}L{j.L}Lt{j.L_t}l{j.l}n{j.n_replica}"
+                         f"p{j.protocol}w{int(j.whole)}dir{j.direction}")
+def test_bit_exact_with_the_oracle(ctx, job):
+    Wg, Sg = gpu_run(ctx, job)
+    Wo, So = oracle_run(job)
+    np.testing.assert_array_equal(Wg, Wo)
+    np.testing.assert_array_equal(Sg, So)
+
+
+def test_thermalisation_changes_the_trajectories(ctx):
+    j = JOBS[0]
+    Wh, Sh = gpu_run(ctx, j)
+    Wm, Sm = gpu_run(ctx, j, therm_update=0)
+    assert not np.array_equal(Sh, Sm)
+    Wo, So = oracle_run(j, therm_update=0)
+    np.testing.assert_array_equal(Sm, So)
+
+
+def test_no_thermalisation_sweeps_is_the_plain_run(ctx):
+    j = JOBS[0].with_(n_therm=0)
+    Wh, Sh = gpu_run(ctx, j)
+    Wm, Sm = gpu_run(ctx, j, therm_update=0)
+    np.testing.assert_array_equal(Wh, Wm)
+    np.testing.assert_array_equal(Sh, Sm)
+
+
+def test_batch_mixes_the_two_starts(ctx):
+    """A scan-like batch: the same l values with and without the option, one
+    call; each job keeps its own bits."""
+    jobs = [wl.Job(2, 16, 16, BC2, l, 10, 1, 17, seed=3, n_therm=12, therm_update=t)
+            for l in (2, 5) for t in (0, H)]
+    outs = [torch.empty(j.n_traj, dtype=torch.int64, device="cuda") for j in jobs]
+    jz.jarzynski_run_batch(ctx, [params(j) for j in jobs], outs)
+    jz.ising_sync(ctx)
+    assert jz.ising_last_launch_ms(ctx) > 0
+    for j, o in zip(jobs, outs):
+        Wo, _ = oracle_run(j)
+        np.testing.assert_array_equal(o.cpu().numpy(), Wo)
+
+
+def test_segments_resume_to_the_one_run(ctx):
+    j = JOBS[4]
+    w = torch.zeros(j.n_traj, dtype=torch.int64, device="cuda")
+    s = torch.zeros(j.n_traj * j.sites, dtype=torch.int8, device="cuda")
+    p = params(j)
+    jz.jarzynski_run_segment(ctx, p, 0, 2, w, s)
+    jz.jarzynski_run_segment(ctx, p, 2, j.n_step, w, s)
+    jz.ising_sync(ctx)
+    Wo, So = oracle_run(j)
+    np.testing.assert_array_equal(w.cpu().numpy(), Wo)
+    np.testing.assert_array_equal(s.cpu().numpy().reshape(j.n_traj, -1), So)
+
+
+def test_entry_points_that_do_not_serve_it_refuse(ctx):
+    j = JOBS[0]
+    p = params(j)
+    w = torch.empty(j.n_traj, dtype=torch.int64, device="cuda")
+    for call in (lambda: jz.jarzynski_run_plain(ctx, p, w),
+                 lambda: jz.jarzynski_run_noalloc(p, w, None),
+                 lambda: jz.jz_plan_create(ctx, [p], [w])):
+        with pytest.raises(jz.IsingError) as e:
+            call()
+        assert e.value.code == jz.ISING_ERR_UNSUPPORTED
+    server = jz.jz_server_create(ctx, 1 << 30, 2)
+    try:
+        with pytest.raises(jz.IsingError) as e:
+            jz.jz_submit(server, p)
+        assert e.value.code == jz.ISING_ERR_UNSUPPORTED
+    finally:
+        jz.jz_server_free(server)
+    # a Swendsen-Wang state beyond shared memory (2D L = 128, L_t = 8L)
+    big = jz.make_params(2, 128, 1024, BC2, 5, 2, 1, 2, 0, n_therm=2, therm_update=H)
+    with pytest.raises(jz.IsingError) as e:
+        jz.jarzynski_run_ex(ctx, big, torch.empty(2, dtype=torch.int64, device="cuda"))
+    assert e.value.code == jz.ISING_ERR_UNSUPPORTED
+    bad = jz.make_params(2, 8, 8, BC2, 1, 2, 1, 2, 0, therm_update=2)
+    with pytest.raises(jz.IsingError) as e:
+        jz.jarzynski_run_ex(ctx, bad, torch.empty(2, dtype=torch.int64, device="cuda"))
+    assert e.value.code == jz.ISING_ERR_ARG
