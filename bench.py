@@ -903,10 +903,11 @@ def run_reference(args):
 
 
 def run_therm_study(args):
-    """The same scan with both updates and several thermalisation lengths:
-    the Jarzynski estimate is unbiased only from an equilibrium start, so a
-    start that has not thermalised shows up as a pull against a reference
-    that has (Swendsen-Wang with 1000 cluster sweeps)."""
+    """The same scan with both updates, and Swendsen-Wang starts before
+    Metropolis protocols, at several thermalisation lengths: the Jarzynski
+    estimate is unbiased only from an equilibrium start, so a start that has
+    not thermalised shows up as a pull against a reference that has
+    (Swendsen-Wang with 1000 cluster sweeps)."""
     import torch
     from paper_2304_03311_gb300 import build as jzbuild
     jzbuild.build()
@@ -914,16 +915,19 @@ def run_therm_study(args):
     n = args.traj_per_l or 512
     ctx = jz.ising_replica_init(0, 0, None)
     runs = {}
-    for name, upd, nth, seed in [("metropolis_therm1000", 0, 1000, 0),
-                                 ("metropolis_therm1000_seed7", 0, 1000, 7),
-                                 ("metropolis_therm4000", 0, 4000, 0),
-                                 ("metropolis_therm16000", 0, 16000, 0),
-                                 ("sw_therm1000", 1, 1000, 0), ("sw_therm100", 1, 100, 3)]:
+    for name, upd, nth, seed, th in [("metropolis_therm1000", 0, 1000, 0, 0),
+                                     ("metropolis_therm1000_seed7", 0, 1000, 7, 0),
+                                     ("metropolis_therm4000", 0, 4000, 0, 0),
+                                     ("metropolis_therm16000", 0, 16000, 0, 0),
+                                     ("sw_therm1000", 1, 1000, 0, 0), ("sw_therm100", 1, 100, 3, 0),
+                                     ("sw_therm100_metropolis", 0, 100, 5, 1),
+                                     ("sw_therm25_metropolis", 0, 25, 6, 1)]:
         w = wl.CONFIGS[args.config]()
-        jobs = [j.with_(n_traj=n, n_therm=nth, seed=seed, update=upd) for j in w.jobs]
+        jobs = [j.with_(n_traj=n, n_therm=nth, seed=seed, update=upd, therm_update=th)
+                for j in w.jobs]
         outs = [torch.empty(n, dtype=torch.int64, device="cuda") for _ in jobs]
         ps = [jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj, j.seed,
-                             n_therm=j.n_therm, update=upd) for j in jobs]
+                             n_therm=j.n_therm, update=upd, therm_update=th) for j in jobs]
         t0 = time.perf_counter()
         jz.jarzynski_run_batch(ctx, ps, outs)
         jz.ising_sync(ctx)
