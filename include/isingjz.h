@@ -127,11 +127,14 @@ typedef struct ising_ctx ising_ctx;
  *              do not.  The thermalisation sweeps then take the Swendsen-Wang
  *              random stream of their sweep indices 0 .. n_therm-1, the
  *              protocol sweeps the Metropolis stream of theirs, as in one run
- *              of each update.  Served by jarzynski_run_ex, jarzynski_run_batch
- *              and jarzynski_run_segment (a segment from k_begin = 0), for
- *              lattices whose Swendsen-Wang state fits shared memory; the other
- *              entry points return ISING_ERR_UNSUPPORTED.  Other values:
- *              ISING_ERR_ARG. */
+ *              of each update.  Served by jarzynski_run_ex, jarzynski_run_batch,
+ *              jarzynski_run_segment (a segment from k_begin = 0), the
+ *              persistent plans (a thermalisation launch per lattice shape
+ *              ahead of the persistent kernel) and the server (jz_submit; the
+ *              job's memory then includes n_traj V bytes of thermalised spins),
+ *              for lattices whose Swendsen-Wang state fits shared memory;
+ *              jarzynski_run_plain and jarzynski_run_noalloc return
+ *              ISING_ERR_UNSUPPORTED.  Other values: ISING_ERR_ARG. */
 typedef struct jz_params {
     int d, L, L_t;
     int update;

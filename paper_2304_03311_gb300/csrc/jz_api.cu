@@ -1231,6 +1231,10 @@ struct jz_plan {
     };
     std::vector<SwGroup> sw;
     DevBuf sw_tcut;
+    // therm_update = 1: thermalisation-only Swendsen-Wang launches (one per
+    // lattice shape) ahead of the persistent kernel, their spins in therm_spins
+    std::vector<SwGroup> therm;
+    DevBuf therm_spins;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -1246,6 +1250,8 @@ void plan_release(jz_plan* pl)
     std::vector<DevBuf*> bufs = {&pl->jobs, &pl->items, &pl->tcut, &pl->counter, &pl->est_jobs,
                                  &pl->sw_tcut};
     for (auto& G : pl->sw) bufs.push_back(&G.jobs);
+    for (auto& G : pl->therm) bufs.push_back(&G.jobs);
+    bufs.push_back(&pl->therm_spins);
     for (DevBuf* b : bufs)
         if (b->ptr) {
             cudaFree(b->ptr);
@@ -1271,6 +1277,21 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
     std::vector<std::pair<double, int2>> items;
     std::vector<uint32_t> sw_tcut;
     size_t smem = 0;
+    // therm_update = 1 jobs: byte offset of each job's spins in therm_spins
+    std::vector<long long> therm_off(n_jobs, -1);
+    size_t therm_bytes = 0;
+    auto group_of = [](std::vector<jz_plan::SwGroup>& gs, int d, const jz::Geom& g) {
+        size_t gi = 0;
+        while (gi < gs.size() && !(gs[gi].d == d && gs[gi].g.L == g.L && gs[gi].g.Lt == g.Lt &&
+                                   gs[gi].g.nrep == g.nrep))
+            ++gi;
+        if (gi == gs.size()) {
+            gs.emplace_back();
+            gs.back().g = g;
+            gs.back().d = d;
+        }
+        return gi;
+    };
     for (int j = 0; j < n_jobs; ++j) {
         const jz_params& p = jobs[j];
         if (p.update == 1) {   // Swendsen-Wang: grouped by lattice shape
@@ -1279,17 +1300,7 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
                 plan_release(pl);
                 return ISING_ERR_UNSUPPORTED;
             }
-            size_t gi = 0;
-            while (gi < pl->sw.size() &&
-                   !(pl->sw[gi].d == p.d && pl->sw[gi].g.L == g.L && pl->sw[gi].g.Lt == g.Lt &&
-                     pl->sw[gi].g.nrep == g.nrep))
-                ++gi;
-            if (gi == pl->sw.size()) {
-                pl->sw.emplace_back();
-                pl->sw.back().g = g;
-                pl->sw.back().d = p.d;
-            }
-            jz_plan::SwGroup& G = pl->sw[gi];
+            jz_plan::SwGroup& G = pl->sw[group_of(pl->sw, p.d, g)];
             jz::JobDesc J{};
             J.l = p.l;
             J.n_step = p.n_step;
@@ -1348,6 +1359,27 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
         build_tables(p, J.tb, tcut, toff[j]);
         J.w_out = (long long*)work_outs[j];
         J.spins_out = nullptr;
+        if (sw_therm(p)) {
+            // its Swendsen-Wang thermalisation: no protocol steps, spins into
+            // its slice of therm_spins, from which the persistent kernel starts
+            if (!sw_fits(B.g)) {
+                plan_release(pl);
+                return ISING_ERR_UNSUPPORTED;
+            }
+            jz_plan::SwGroup& G = pl->therm[group_of(pl->therm, p.d, B.g)];
+            jz::JobDesc T = J;
+            std::vector<uint32_t> bt((size_t)2 * p.n_step);
+            build_bond_tables(p, T.tb, bt, 0);
+            T.k_end = 0;
+            T.cta0 = G.n_cta;
+            G.h_jobs.push_back(T);
+            G.toff.push_back((size_t)j);   // the job whose spins it writes
+            G.n_cta += p.n_traj;
+            ++G.n_jobs;
+            therm_off[j] = (long long)therm_bytes;
+            therm_bytes += (size_t)p.n_traj * (size_t)(B.g.nrep * p.L_t * B.g.Ly * p.L);
+            J.start_in = 1;
+        }
         const double per_traj = (double)(B.g.nrep * p.L_t * B.g.Ly * p.L) *
                                 ((double)p.n_therm + (double)p.n_step * p.n_sweep);
         for (int lo = 0; lo < p.n_traj; lo += B.sh.teams) {
@@ -1373,6 +1405,26 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
     }
     uint32_t* d_tcut = (uint32_t*)pl->tcut.ptr;
     for (int j = 0; j < n_jobs; ++j) bj[j].J.tcut = d_tcut + toff[j];
+    if (!pl->therm.empty()) {
+        if ((rc = ensure(ctx, pl->therm_spins, therm_bytes))) {
+            plan_release(pl);
+            return rc;
+        }
+        int8_t* base = (int8_t*)pl->therm_spins.ptr;
+        for (int j = 0; j < n_jobs; ++j)
+            if (therm_off[j] >= 0) bj[j].J.spins_in = base + therm_off[j];
+        for (auto& G : pl->therm) {
+            for (size_t i = 0; i < G.h_jobs.size(); ++i) {
+                const size_t j = G.toff[i];
+                G.h_jobs[i].tcut = bj[j].J.tcut;   // not read: no protocol steps
+                G.h_jobs[i].spins_out = base + therm_off[j];
+            }
+            if ((rc = ensure(ctx, G.jobs, G.h_jobs.size() * sizeof(jz::JobDesc)))) {
+                plan_release(pl);
+                return rc;
+            }
+        }
+    }
     if (!pl->sw.empty()) {
         if ((rc = ensure(ctx, pl->sw_tcut, sw_tcut.size() * sizeof(uint32_t)))) {
             plan_release(pl);
@@ -1407,6 +1459,8 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
         {pl->sw_tcut.ptr, sw_tcut.data(), sw_tcut.size() * sizeof(uint32_t)}};
     for (auto& G : pl->sw)
         copies.emplace_back(G.jobs.ptr, G.h_jobs.data(), G.h_jobs.size() * sizeof(jz::JobDesc));
+    for (auto& G : pl->therm)
+        copies.emplace_back(G.jobs.ptr, G.h_jobs.data(), G.h_jobs.size() * sizeof(jz::JobDesc));
     for (const auto& c : copies) {
         if (std::get<2>(c) == 0) continue;
         if ((rc = cuda_err(cudaMemcpyAsync(std::get<0>(c), std::get<1>(c), std::get<2>(c),
@@ -1440,6 +1494,10 @@ int plan_enqueue(jz_plan* pl)
 {
     cudaStream_t st = pl->ctx->stream;
     int rc;
+    for (const auto& G : pl->therm)
+        if ((rc = cuda_err(jz::launch_sw(G.d, G.g, pl->K, (const jz::JobDesc*)G.jobs.ptr,
+                                         G.n_jobs, G.n_cta, st))))
+            return rc;
     if (pl->n_items > 0) {
         if ((rc = cuda_err(cudaMemsetAsync(pl->counter.ptr, 0, sizeof(unsigned int), st))))
             return rc;
@@ -1498,7 +1556,6 @@ int jz_plan_create(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* c
     for (int j = 0; j < n_jobs; ++j) {
         const int rc = check_params(&jobs[j]);
         if (rc) return rc;
-        if (sw_therm(jobs[j])) return ISING_ERR_UNSUPPORTED;
         if (jobs[j].seed != jobs[0].seed || !work_outs[j] || !is_device_ptr(work_outs[j]))
             return ISING_ERR_ARG;
     }

@@ -31,8 +31,11 @@ __device__ __forceinline__ void run_item(const BatchJob& B, const PhiloxKeys& K,
     const int tm = has ? team : 0;
     uint32_t* St = S + (size_t)tm * B.lattice_words;
     const long long local = (long long)traj_lo + tm;
+    const long long V = (long long)B.g.nrep * B.g.Lt * B.g.Ly * B.g.L;
+    // therm_update = 1: the job starts from its thermalised spins
+    const int8_t* sin = (has && tj.start_in) ? B.J.spins_in + local * V : nullptr;
     const int dE = run_trajectory<D, FAST, 0, 0>(B.g, K, tj, B.J.traj0 + local, St, tab, tid,
-                                                 B.sh.team_threads, bar);
+                                                 B.sh.team_threads, bar, sin);
     if (has && dE != 0) atomicAdd(&s_work[tm], dE);
     __syncthreads();
     if (has && tid == 0)

@@ -47,7 +47,7 @@ struct Slot {
     std::vector<uint32_t> tcut;        // host table build area
     uint32_t* h_tcut = nullptr;        // pinned staging
     size_t h_tcut_cap = 0;             // words
-    jz::JobDesc* h_desc = nullptr;     // pinned
+    jz::JobDesc* h_desc = nullptr;     // pinned, two descriptors
     double* h_est = nullptr;           // pinned, 3 doubles
     int64_t* h_work = nullptr;         // pinned
     size_t h_work_cap = 0;             // entries
@@ -60,10 +60,18 @@ size_t tcut_words(const jz_params& p)
     return (size_t)p.n_step * (p.update == 1 ? 2 : 8 * p.d);
 }
 
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// A job's device memory, in order: its thresholds, two job descriptors (the
+// second for a Swendsen-Wang thermalisation launch), W_int, the estimator's
+// output, and for therm_update = 1 the thermalised spins (n_traj V bytes).
+constexpr size_t kDescBytes = (2 * sizeof(jz::JobDesc) + 255) & ~(size_t)255;
 size_t job_bytes(const jz_params& p)
 {
     const size_t tcut = tcut_words(p) * sizeof(uint32_t);
-    return ((tcut + 255) & ~(size_t)255) + 256 + (size_t)p.n_traj * sizeof(int64_t) + 256;
+    const size_t V = (size_t)nrep_of(p) * p.L_t * (p.d == 3 ? p.L : 1) * p.L;
+    return round256(tcut) + kDescBytes + round256((size_t)p.n_traj * sizeof(int64_t)) + 256 +
+           (sw_therm(p) ? (size_t)p.n_traj * V : 0);
 }
 
 int grow_pinned(void** p, size_t* cap, size_t want, size_t elem)
@@ -137,11 +145,14 @@ int jz_server::launch(Slot& s, Job& j)
     std::memcpy(s.h_tcut, s.tcut.data(), n_tcut * sizeof(uint32_t));
     char* d = nullptr;
     if ((rc = cuda_err(cudaMallocAsync((void**)&d, j.need, s.stream)))) return rc;
-    const size_t tcut_bytes = (n_tcut * sizeof(uint32_t) + 255) & ~(size_t)255;
+    const size_t tcut_bytes = round256(n_tcut * sizeof(uint32_t));
+    const size_t work_bytes = round256((size_t)p.n_traj * sizeof(int64_t));
     uint32_t* d_tcut = (uint32_t*)d;
     jz::JobDesc* d_desc = (jz::JobDesc*)(d + tcut_bytes);
-    long long* d_work = (long long*)(d + tcut_bytes + 256);
-    double* d_est = (double*)(d + tcut_bytes + 256 + (size_t)p.n_traj * sizeof(int64_t));
+    long long* d_work = (long long*)(d + tcut_bytes + kDescBytes);
+    double* d_est = (double*)(d + tcut_bytes + kDescBytes + work_bytes);
+    int8_t* d_spins = (int8_t*)(d + tcut_bytes + kDescBytes + work_bytes + 256);
+    const bool hybrid = sw_therm(p);
     J.l = p.l;
     J.n_step = p.n_step;
     J.n_sweep = p.n_sweep;
@@ -157,13 +168,27 @@ int jz_server::launch(Slot& s, Job& j)
     J.tcut = d_tcut;
     J.w_out = d_work;
     J.spins_out = nullptr;
+    if (hybrid) {
+        // Swendsen-Wang thermalisation (no protocol steps) into d_spins, from
+        // which the Metropolis protocol starts
+        jz::JobDesc& T = s.h_desc[1];
+        T = J;
+        std::vector<uint32_t> bt((size_t)2 * p.n_step);
+        build_bond_tables(p, T.tb, bt, 0);
+        T.k_end = 0;
+        T.spins_out = d_spins;
+        J.start_in = 1;
+        J.spins_in = d_spins;
+    }
     const jz::PhiloxKeys K = key_schedule(p.seed);
     const jz::LaunchShape sh = p.update == 1 ? shape_for(g, 0) : ctx_shape(ctx, p.d, g, p.n_traj);
     const int B = p.n_traj < 32 ? p.n_traj : 32;
     if ((rc = cuda_err(cudaMemcpyAsync(d_tcut, s.h_tcut, n_tcut * sizeof(uint32_t),
                                        cudaMemcpyHostToDevice, s.stream))) ||
-        (rc = cuda_err(cudaMemcpyAsync(d_desc, s.h_desc, sizeof(jz::JobDesc),
+        (rc = cuda_err(cudaMemcpyAsync(d_desc, s.h_desc, (hybrid ? 2 : 1) * sizeof(jz::JobDesc),
                                        cudaMemcpyHostToDevice, s.stream))) ||
+        (hybrid &&
+         (rc = cuda_err(jz::launch_sw(p.d, g, K, d_desc + 1, 1, p.n_traj, s.stream)))) ||
         (rc = cuda_err(p.update == 1   // Swendsen-Wang: one trajectory per CTA
                            ? jz::launch_sw(p.d, g, K, d_desc, 1, p.n_traj, s.stream)
                            : jz::launch_traj(p.d, g, K, d_desc, 1,
@@ -282,7 +307,7 @@ int jz_server_create(ising_ctx* ctx, size_t hbm_budget_bytes, int max_inflight, 
     for (Slot& sl : s->slots) {
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
-            cudaMallocHost((void**)&sl.h_desc, sizeof(jz::JobDesc)) != cudaSuccess ||
+            cudaMallocHost((void**)&sl.h_desc, 2 * sizeof(jz::JobDesc)) != cudaSuccess ||
             cudaMallocHost((void**)&sl.h_est, 4 * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
             for (Slot& t : s->slots) {
@@ -306,9 +331,9 @@ int jz_submit(jz_server* s, const jz_params* p, uint64_t* job_id)
     if (!s || !p || !job_id) return ISING_ERR_ARG;
     int rc = check_params(p);
     if (rc) return rc;
-    if (sw_therm(*p)) return ISING_ERR_UNSUPPORTED;
     const jz::Geom g = make_geom(p->d, p->L, p->L_t, nrep_of(*p));
     if (p->update == 1 ? !sw_fits(g) : !shape_fits(g)) return ISING_ERR_UNSUPPORTED;
+    if (sw_therm(*p) && !sw_fits(g)) return ISING_ERR_UNSUPPORTED;
     std::unique_ptr<Job> j(new (std::nothrow) Job());
     if (!j) return ISING_ERR_NOMEM;
     j->p = *p;

@@ -4,8 +4,9 @@ spins, against the oracle's single trajectory of the same composition.
 
 Bit-exact W_int and final spins on 2D and 3D shapes (ragged rows, reverse,
 protocol 2, n = 3 replicas, whole cuts), inside a batch beside plain jobs, as
-segments resumed mid-protocol, and with no thermalisation sweeps (then the
-plain Metropolis run).  Entry points that do not serve it refuse it.
+segments resumed mid-protocol, through the server, and with no thermalisation
+sweeps (then the plain Metropolis run).  Entry points that do not serve it
+refuse it.
 """
 import numpy as np
 import pytest
@@ -125,23 +126,61 @@ def test_segments_resume_to_the_one_run(ctx):
     np.testing.assert_array_equal(s.cpu().numpy().reshape(j.n_traj, -1), So)
 
 
+def test_server_serves_it(ctx):
+    """Jobs with and without the option through the continuous-batching
+    server, concurrently: each keeps the oracle's bits."""
+    jobs = [JOBS[0], JOBS[4], JOBS[0].with_(therm_update=0), JOBS[7]]
+    server = jz.jz_server_create(ctx, 1 << 30, 3)
+    try:
+        ids = [jz.jz_submit(server, params(j)) for j in jobs]
+        res = [jz.jz_wait(server, i, 600.0) for i in ids]
+        assert all(r.status == 0 for r in res)
+        for j, i in zip(jobs, ids):
+            w = np.empty(j.n_traj, dtype=np.int64)
+            jz.jz_server_work(server, i, w)
+            Wo, _ = oracle_run(j)
+            np.testing.assert_array_equal(w, Wo)
+    finally:
+        jz.jz_server_free(server)
+
+
+@pytest.mark.parametrize("cta", [256, 0])
+def test_persistent_plan_serves_it(ctx, cta):
+    """An uneven plan of 2D and 3D jobs with and without the option (and a
+    Swendsen-Wang job), replayed twice from its graph: the oracle's bits."""
+    jobs = [JOBS[0], JOBS[4], JOBS[5], JOBS[0].with_(therm_update=0, traj0=1 << 20),
+            wl.Job(2, 8, 8, BC2, 2, 5, 1, 9, seed=1, n_therm=4, update=1, traj0=2 << 20)]
+    jobs = [j.with_(seed=1) for j in jobs]
+    outs = [torch.full((j.n_traj,), -9, dtype=torch.int64, device="cuda") for j in jobs]
+    ps = [params(j) for j in jobs]
+    for p, j in zip(ps, jobs):
+        p.update = j.update
+    plan = jz.jz_plan_create(ctx, ps, outs, None, cta)
+    try:
+        for _ in range(2):
+            for o in outs:
+                o.fill_(-9)
+            jz.jz_plan_launch(plan)
+            jz.ising_sync(ctx)
+            for j, o in zip(jobs, outs):
+                W, _ = oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj,
+                                  j.seed, n_therm=j.n_therm, direction=j.direction,
+                                  traj0=j.traj0, update=j.update, protocol=j.protocol,
+                                  therm_update=j.therm_update if j.update == 0 else None)
+                np.testing.assert_array_equal(o.cpu().numpy(), W)
+    finally:
+        jz.jz_plan_free(plan)
+
+
 def test_entry_points_that_do_not_serve_it_refuse(ctx):
     j = JOBS[0]
     p = params(j)
     w = torch.empty(j.n_traj, dtype=torch.int64, device="cuda")
     for call in (lambda: jz.jarzynski_run_plain(ctx, p, w),
-                 lambda: jz.jarzynski_run_noalloc(p, w, None),
-                 lambda: jz.jz_plan_create(ctx, [p], [w])):
+                 lambda: jz.jarzynski_run_noalloc(p, w, None)):
         with pytest.raises(jz.IsingError) as e:
             call()
         assert e.value.code == jz.ISING_ERR_UNSUPPORTED
-    server = jz.jz_server_create(ctx, 1 << 30, 2)
-    try:
-        with pytest.raises(jz.IsingError) as e:
-            jz.jz_submit(server, p)
-        assert e.value.code == jz.ISING_ERR_UNSUPPORTED
-    finally:
-        jz.jz_server_free(server)
     # a Swendsen-Wang state beyond shared memory (2D L = 128, L_t = 8L)
     big = jz.make_params(2, 128, 1024, BC2, 5, 2, 1, 2, 0, n_therm=2, therm_update=H)
     with pytest.raises(jz.IsingError) as e:
