@@ -186,12 +186,14 @@ int jz_result_json(uint64_t job_id, const jz_params* p, const jz_result* r, char
         buf, n,
         "{\"job\": %llu, \"d\": %d, \"L\": %d, \"L_t\": %d, \"beta\": %.17g, \"l\": %d, "
         "\"n_step\": %d, \"n_sweep\": %d, \"n_therm\": %d, \"n_traj\": %d, \"direction\": %d, "
-        "\"update\": %d, \"protocol\": %d, \"n_replica\": %d, \"whole\": %d, \"seed\": %llu, "
+        "\"update\": %d, \"therm_update\": %d, \"protocol\": %d, \"n_replica\": %d, "
+        "\"whole\": %d, \"seed\": %llu, "
         "\"status\": %d, \"log_ratio\": %s, \"delta_S2\": %s, \"delta_S2_err\": %s, "
         "\"submit_s\": %.6f, \"start_s\": %.6f, \"done_s\": %.6f, \"latency_s\": %.6f, "
         "\"spin_updates\": %lld, \"spin_updates_per_s\": %s}",
         (unsigned long long)job_id, p->d, p->L, p->L_t, p->beta, p->l, p->n_step, p->n_sweep,
-        p->n_therm, p->n_traj, p->direction, p->update, p->protocol, nrep_of(*p), p->whole,
+        p->n_therm, p->n_traj, p->direction, p->update, p->therm_update, p->protocol,
+        nrep_of(*p), p->whole,
         (unsigned long long)p->seed, r->status, lr, ds, de, r->submit_s, r->start_s, r->done_s,
         latency, r->updates, rate);
     if (len < 0 || (size_t)len >= n) return ISING_ERR_ARG;

@@ -75,13 +75,15 @@ def test_tune_cache_rejects_bad_files(tmp_path):
 
 
 def test_result_json_line():
-    p = jz.make_params(2, 64, 64, 0.44068679350977147, 7, 1000, 2, 256, seed=11)
+    p = jz.make_params(2, 64, 64, 0.44068679350977147, 7, 1000, 2, 256, seed=11,
+                       therm_update=jz.SW_THERM)
     r = jz.JzResult(status=0, log_ratio=-0.0123, delta_S2=0.0123, delta_S2_err=0.0004,
                     submit_s=1.0, start_s=1.5, done_s=3.5, updates=10**12)
     line = jz.jz_result_json(42, p, r)
     doc = json.loads(line)
     assert doc["job"] == 42 and doc["L"] == 64 and doc["l"] == 7 and doc["n_traj"] == 256
     assert doc["seed"] == 11 and doc["n_replica"] == 2 and doc["status"] == 0
+    assert doc["update"] == 0 and doc["therm_update"] == 1
     assert doc["delta_S2"] == 0.0123 and doc["delta_S2_err"] == 0.0004
     assert math.isclose(doc["latency_s"], 2.5) and doc["spin_updates"] == 10**12
     assert math.isclose(doc["spin_updates_per_s"], 10**12 / 2.0)
