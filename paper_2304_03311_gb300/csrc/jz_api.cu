@@ -400,11 +400,24 @@ bool threads_ok(const jz::Geom& g, int threads)
 
 // The context's launch shape for this lattice: the tuned / fixed CTA size,
 // else the default for a launch of n_traj trajectories.
-jz::LaunchShape ctx_shape(const ising_ctx* ctx, int d, const jz::Geom& g, long long n_traj)
+jz::LaunchShape ctx_shape(ising_ctx* ctx, int d, const jz::Geom& g, long long n_traj)
 {
-    auto it = ctx->threads.find(std::make_tuple(d, g.L, g.Lt));
-    const int t = (it != ctx->threads.end() && threads_ok(g, it->second)) ? it->second : 0;
-    return t ? shape_for(g, t) : default_shape(d, g, n_traj);
+    const auto key = std::make_tuple(d, g.L, g.Lt, g.nrep, n_traj);
+    {
+        std::lock_guard<std::mutex> lk(ctx->shapes_mu);
+        auto it = ctx->threads.find(std::make_tuple(d, g.L, g.Lt));
+        const int t = (it != ctx->threads.end() && threads_ok(g, it->second)) ? it->second : 0;
+        if (t) return shape_for(g, t);
+        auto c = ctx->default_shapes.find(key);
+        if (c != ctx->default_shapes.end()) return c->second;
+    }
+    // scored without the lock (occupancy queries); a concurrent caller may
+    // score the same key, with the same result
+    const jz::LaunchShape sh = default_shape(d, g, n_traj);
+    std::lock_guard<std::mutex> lk(ctx->shapes_mu);
+    if (ctx->default_shapes.size() >= 4096) ctx->default_shapes.clear();
+    ctx->default_shapes[key] = sh;
+    return sh;
 }
 
 int cuda_err(cudaError_t e)
@@ -762,12 +775,10 @@ int ising_set_threads(ising_ctx* ctx, int d, int L, int L_t, int threads)
     if (!ctx || (d != 2 && d != 3) || L < 2 || L_t < 2 || (L & 1) || (L_t & 1))
         return ISING_ERR_ARG;
     const auto key = std::make_tuple(d, L, L_t);
-    if (threads == 0) {
-        ctx->threads.erase(key);
-        return ISING_OK;
-    }
-    if (!threads_ok(make_geom(d, L, L_t, 2), threads)) return ISING_ERR_ARG;
-    ctx->threads[key] = threads;
+    if (threads != 0 && !threads_ok(make_geom(d, L, L_t, 2), threads)) return ISING_ERR_ARG;
+    std::lock_guard<std::mutex> lk(ctx->shapes_mu);
+    if (threads == 0) ctx->threads.erase(key);
+    else ctx->threads[key] = threads;
     return ISING_OK;
 }
 
@@ -846,8 +857,11 @@ int ising_autotune(ising_ctx* ctx, const jz_params* p, int* threads)
     float best_ms = 1e30f;
     int64_t* outs[1] = {out};
     for (int t : cands) {
-        if (t) ctx->threads[key] = t;
-        else ctx->threads.erase(key);
+        {
+            std::lock_guard<std::mutex> lk(ctx->shapes_mu);
+            if (t) ctx->threads[key] = t;
+            else ctx->threads.erase(key);
+        }
         if ((rc = run_jobs(ctx, &s, 1, outs, nullptr))) break;           // warm-up
         cudaEventRecord(e0, ctx->stream);
         if ((rc = run_jobs(ctx, &s, 1, outs, nullptr))) break;
@@ -862,8 +876,11 @@ int ising_autotune(ising_ctx* ctx, const jz_params* p, int* threads)
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (best) ctx->threads[key] = best;
-    else ctx->threads.erase(key);
+    {
+        std::lock_guard<std::mutex> lk(ctx->shapes_mu);
+        if (best) ctx->threads[key] = best;
+        else ctx->threads.erase(key);
+    }
     if (rc) return rc;
     if (threads) *threads = best;
     return ISING_OK;

@@ -10,6 +10,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <map>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -69,7 +70,12 @@ struct ising_ctx {
     DevBuf therm;     // spins after Swendsen-Wang thermalisation (therm_update = 1)
     std::vector<uint32_t> h_tcut;
     std::vector<jz::JobDesc> h_jobs;
+    // Launch shapes, guarded by shapes_mu (a server's worker thread reads them
+    // while the context's own thread may tune or fix them):
+    std::mutex shapes_mu;
     std::map<std::tuple<int, int, int>, int> threads;   // per-shape CTA size (tuned)
+    // default shapes already scored, by (d, L, L_t, n, trajectories per launch)
+    std::map<std::tuple<int, int, int, int, long long>, jz::LaunchShape> default_shapes;
     // device time of the last run call's kernel launches (ising_last_launch_ms):
     // ev_k0 before its first launch, ev_k1 after its last one
     cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;
@@ -112,7 +118,7 @@ bool shape_fits(const jz::Geom& g);
 bool threads_fit(const jz::Geom& g);
 bool threads_ok(const jz::Geom& g, int threads);
 jz::LaunchShape default_shape(int d, const jz::Geom& g, long long n_traj);
-jz::LaunchShape ctx_shape(const ising_ctx* ctx, int d, const jz::Geom& g, long long n_traj);
+jz::LaunchShape ctx_shape(ising_ctx* ctx, int d, const jz::Geom& g, long long n_traj);
 int cuda_err(cudaError_t e);
 int run_jobs(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const* outs,
              int8_t* const* spins);
