@@ -89,6 +89,9 @@ def parse_args():
                          "end of region A by one column")
     ap.add_argument("--n-therm", type=int, default=None,
                     help="override the thermalisation sweeps")
+    ap.add_argument("--therm-update", type=int, choices=[0, 1], default=0,
+                    help="1: thermalise with Swendsen-Wang clusters before the Metropolis "
+                         "protocol (jz_params.therm_update)")
     ap.add_argument("--therm-study", action="store_true",
                     help="run the scan with Metropolis (n_therm 1000, 4000, 16000) and "
                          "Swendsen-Wang (n_therm 100, 1000) and print the c-function pulls "
@@ -119,7 +122,8 @@ def dist_env():
 
 
 def workload_for(config: int, rank: int, traj_per_l=None, n_step=None, update="metropolis",
-                 protocol=1, n_therm=None, n_replica=2, whole=False, lattice=None):
+                 protocol=1, n_therm=None, n_replica=2, whole=False, lattice=None,
+                 therm_update=0):
     w = wl.CONFIGS[config]()
     if lattice:
         L, L_t = (int(v) for v in lattice.split(","))
@@ -140,6 +144,9 @@ def workload_for(config: int, rank: int, traj_per_l=None, n_step=None, update="m
     if n_therm is not None:
         w.jobs = [j.with_(n_therm=n_therm) for j in w.jobs]
         w.name += f"_therm{n_therm}"
+    if therm_update and update != "sw":
+        w.jobs = [j.with_(therm_update=1) for j in w.jobs]
+        w.name += "_swtherm"
     if traj_per_l:
         w.jobs = [j.with_(n_traj=traj_per_l) for j in w.jobs]
         w.name += f"_traj{traj_per_l}"
@@ -250,6 +257,7 @@ def cpu_oracle_rate(w, seconds: float):
     t0 = time.perf_counter()
     oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, threads, j.seed,
                n_therm=j.n_therm, traj0=j.traj0, n_threads=threads, update=j.update,
+               therm_update=j.therm_update,
                protocol=j.protocol, n_replica=j.n_replica, whole=j.whole)
     t_round = time.perf_counter() - t0
     rounds = max(1, int(seconds / max(t_round, 1e-3) / len(jobs)))
@@ -259,6 +267,7 @@ def cpu_oracle_rate(w, seconds: float):
     for j in jobs:
         oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, n_per_job, j.seed,
                    n_therm=j.n_therm, traj0=j.traj0, n_threads=threads, update=j.update,
+                   therm_update=j.therm_update,
                    protocol=j.protocol, n_replica=j.n_replica, whole=j.whole)
         updates += j.with_(n_traj=n_per_job).updates
     dt = time.perf_counter() - t0
@@ -269,6 +278,7 @@ def cpu_oracle_rate(w, seconds: float):
     t1 = time.perf_counter()
     oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, 1, j.seed,
                n_therm=j.n_therm, traj0=j.traj0, n_threads=1, update=j.update,
+               therm_update=j.therm_update,
                protocol=j.protocol, n_replica=j.n_replica, whole=j.whole)
     single = j.with_(n_traj=1).updates / (time.perf_counter() - t1)
     return updates / dt, len(jobs) * n_per_job / dt, threads, sample, single
@@ -650,7 +660,8 @@ def run_ours(args):
     import paper_2304_03311_gb300 as jz
 
     w = workload_for(args.config, rank, args.traj_per_l, args.n_step, args.update, args.protocol,
-                     args.n_therm, args.n_replica, args.whole, args.lattice)
+                     args.n_therm, args.n_replica, args.whole, args.lattice,
+                     args.therm_update)
     sw = args.update == "sw"
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
@@ -737,7 +748,7 @@ def run_ours(args):
     # headline (one GPU only; the headline alone under torchrun)
     default_run = (args.config == 2 and not sw and args.protocol == 1 and args.n_replica == 2
                    and not args.whole and not args.lattice and not args.traj_per_l
-                   and not args.n_step and args.n_therm is None)
+                   and not args.n_step and args.n_therm is None and not args.therm_update)
     extras = world == 1 and not args.no_extras and default_run
     configs = None
     plain = None
@@ -755,7 +766,8 @@ def run_ours(args):
             plain = plain_baseline(jz, torch, ctx, dev, w, value, args.plain)
         if args.bias_traj > 0:
             bias = bias_and_cost(jz, torch, ctx, stream, dev, w, cfun, kernel_ms, args)
-    elif args.plain > 0 and all(j.update == 0 and j.n_replica == 2 and not j.whole and
+    elif args.plain > 0 and all(j.update == 0 and j.therm_update == 0 and j.n_replica == 2 and
+                                not j.whole and
                                 (j.protocol == 1 or j.d == 2) for j in w.jobs):
         # the plain form serves Metropolis, two replicas and moving ends only
         plain = plain_baseline(jz, torch, ctx, dev, w, value, args.plain)
@@ -781,7 +793,8 @@ def run_ours(args):
                 "configs": configs, "plain_gpu_baseline": plain, "bias_check": bias,
                 "ceilings": ceil, "device": facts,
                 "cta_threads": scan.tuned or "default",
-                "update": args.update, "protocol": args.protocol,
+                "update": args.update, "therm_update": args.therm_update,
+                "protocol": args.protocol,
                 "n_replica": args.n_replica, "whole_cut": args.whole,
                 "equal_error_vs_metropolis": equal_error,
                 "gpu_launches": args.steps * scan.launches_per_step(),
@@ -867,7 +880,8 @@ def run_reference(args):
     oracle.build()
     threads = oracle.max_threads()
     w = workload_for(args.config, 0, args.traj_per_l, args.n_step, args.update, args.protocol,
-                     args.n_therm, args.n_replica, args.whole, args.lattice)
+                     args.n_therm, args.n_replica, args.whole, args.lattice,
+                     args.therm_update)
     jobs = w.jobs[:: max(1, len(w.jobs) // 2)][:2]
     n_per = threads
 
@@ -876,6 +890,7 @@ def run_reference(args):
         for j in jobs:
             oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, n_per, j.seed,
                        n_therm=j.n_therm, traj0=j.traj0, n_threads=threads, update=j.update,
+                       therm_update=j.therm_update,
                        protocol=j.protocol, n_replica=j.n_replica, whole=j.whole)
             u += j.with_(n_traj=n_per).updates
         return u
