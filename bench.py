@@ -744,7 +744,7 @@ def run_ours(args):
             "c_function_pull_max": pl["max_abs_pull"], "c_function_chi2_per_l": pl["chi2_per_l"],
             "basis": "same trajectories, N, sweeps and n_therm; cost at equal error ~ err^2 x time"}
 
-    # the other spec workloads and the plain baseline, beside the
+    # the other benchmark workloads and the plain baseline, beside the
     # headline (one GPU only; the headline alone under torchrun)
     default_run = (args.config == 2 and not sw and args.protocol == 1 and args.n_replica == 2
                    and not args.whole and not args.lattice and not args.traj_per_l
