@@ -70,6 +70,9 @@ JOBS = [
     wl.Job(2, 8, 8, BC2, 3, 6, 1, 12, seed=15, n_therm=6, whole=True, therm_update=H),
     wl.Job(2, 16, 8, BC2, 3, 9, 1, 12, seed=2**64 - 1, n_therm=3, traj0=123456,
            therm_update=H),
+    wl.Job(2, 6, 4, BC2, 2, 5, 1, 7, seed=16, n_therm=4, n_replica=8, therm_update=H),
+    wl.Job(2, 8, 8, BC2, 5, 6, 1, 9, seed=17, n_therm=5, whole=True, direction=-1,
+           therm_update=H),
 ]
 
 
@@ -170,6 +173,23 @@ def test_persistent_plan_serves_it(ctx, cta):
                 np.testing.assert_array_equal(o.cpu().numpy(), W)
     finally:
         jz.jz_plan_free(plan)
+
+
+def test_server_charges_the_thermalised_spins(ctx):
+    """A job whose thermalised spins (n_traj V bytes) alone exceed the server's
+    budget finishes with ISING_ERR_NOMEM; the same job without the option
+    fits and runs."""
+    j = wl.Job(2, 64, 64, BC2, 5, 4, 1, 512, seed=1, n_therm=4, therm_update=H)
+    budget = 1 << 20   # 1 MiB: W_int and tables fit, 512 x 8192 bytes of spins do not
+    server = jz.jz_server_create(ctx, budget, 2)
+    try:
+        a = jz.jz_submit(server, params(j))
+        b = jz.jz_submit(server, params(j, therm_update=0))
+        ra, rb = jz.jz_wait(server, a, 600.0), jz.jz_wait(server, b, 600.0)
+        assert ra.status == jz.ISING_ERR_NOMEM
+        assert rb.status == 0
+    finally:
+        jz.jz_server_free(server)
 
 
 def test_entry_points_that_do_not_serve_it_refuse(ctx):
