@@ -192,6 +192,31 @@ def test_server_charges_the_thermalised_spins(ctx):
         jz.jz_server_free(server)
 
 
+def test_full_scan_from_a_swendsen_wang_start_sampled(ctx):
+    """The 2D L = 64 scan at full size (31 x 16384 trajectories, N = 1000 x 2
+    sweeps) from 100 Swendsen-Wang thermalisation sweeps, one launch pair as
+    `bench.py --therm-update 1 --n-therm 100` runs it with 512-thread CTAs:
+    the first and last trajectory of l = 0, 15 and 30 against the oracle."""
+    w = wl.config2()
+    jobs = [j.with_(n_therm=100, therm_update=H) for j in w.jobs]
+    c = jz.ising_replica_init(0, 0, None)
+    try:
+        jz.ising_set_threads(c, 2, 64, 64, 512)
+        outs = [torch.empty(j.n_traj, dtype=torch.int64, device="cuda") for j in jobs]
+        jz.jarzynski_run_batch(c, [params(j) for j in jobs], outs)
+        jz.ising_sync(c)
+        res = [o.cpu().numpy() for o in outs]
+    finally:
+        jz.ising_replica_free(c)
+    for l in (0, 15, 30):
+        j = jobs[l]
+        assert np.all(res[l] % 2 == 0) and len(np.unique(res[l])) > 1
+        for t in (0, j.n_traj - 1):
+            Wo, _ = oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, 1, j.seed,
+                               n_therm=j.n_therm, traj0=j.traj0 + t, therm_update=H)
+            assert res[l][t] == Wo[0], (l, t)
+
+
 def test_entry_points_that_do_not_serve_it_refuse(ctx):
     j = JOBS[0]
     p = params(j)
