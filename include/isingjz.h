@@ -128,11 +128,14 @@ typedef struct ising_ctx ising_ctx;
  *              random stream of their sweep indices 0 .. n_therm-1, the
  *              protocol sweeps the Metropolis stream of theirs, as in one run
  *              of each update.  Served by jarzynski_run_ex, jarzynski_run_batch,
- *              jarzynski_run_segment (a segment from k_begin = 0), the
- *              persistent plans (a thermalisation launch per lattice shape
- *              ahead of the persistent kernel) and the server (jz_submit; the
- *              job's memory then includes n_traj V bytes of thermalised spins),
- *              for lattices whose Swendsen-Wang state fits shared memory;
+ *              jarzynski_run_segment (a segment from k_begin = 0) and the
+ *              server (jz_submit; the job's memory then includes n_traj V
+ *              bytes of thermalised spins): a Swendsen-Wang state beyond
+ *              shared memory is thermalised from HBM slices, in launches of
+ *              one resident wave of trajectories, whose slices the server also
+ *              charges to the job.  The persistent plans serve it for lattices
+ *              whose Swendsen-Wang state fits shared memory (a thermalisation
+ *              launch per lattice shape ahead of the persistent kernel).
  *              jarzynski_run_plain and jarzynski_run_noalloc return
  *              ISING_ERR_UNSUPPORTED.  Other values: ISING_ERR_ARG. */
 typedef struct jz_params {

@@ -439,10 +439,14 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
     // lattices beyond shared memory run from HBM, one slice per CTA
     const bool in_hbm = sw ? !sw_fits(g) : !shape_fits(g);
     // Swendsen-Wang thermalisation before a Metropolis protocol run from k = 0:
-    // a thermalisation-only sw_kernel launch leaves every trajectory's spins in
-    // ctx->therm, from which the Metropolis protocol starts
+    // thermalisation-only sw_kernel launches leave every trajectory's spins in
+    // ctx->therm, from which the Metropolis protocol starts.  A Swendsen-Wang
+    // state beyond shared memory is thermalised from HBM slices, one resident
+    // wave of trajectories (a chunk) per launch, so its HBM state stays one
+    // wave whatever the trajectory count.
     const bool hybrid = sw_therm(p0) && (!seg || seg->k_begin == 0);
-    if (hybrid && !sw_fits(g)) return ISING_ERR_UNSUPPORTED;
+    const bool therm_hbm = hybrid && !sw_fits(g);
+    const long long chunk = therm_hbm ? jz::sw_hbm_wave(p0.d) : 0;
     long long n_traj_launch = 0;
     for (int j : idx) n_traj_launch += jobs[j].n_traj;
     jz::LaunchShape sh = sw ? shape_for(g, 0) : ctx_shape(ctx, p0.d, g, n_traj_launch);
@@ -468,10 +472,22 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
     if (n_spin_traj && !spins_on_device &&
         (rc = ensure(ctx, ctx->spins, (size_t)n_spin_traj * V)))
         return rc;
+    size_t n_therm_desc = 0;   // thermalisation launches' job descriptors
     if (hybrid) {
+        for (int j : idx)
+            n_therm_desc += therm_hbm ? (size_t)((jobs[j].n_traj + chunk - 1) / chunk) : 1;
         if ((rc = ensure(ctx, ctx->therm, (size_t)n_traj_all * V))) return rc;
-        if ((rc = ensure(ctx, ctx->jobs, (size_t)2 * n_jobs * sizeof(jz::JobDesc)))) return rc;
+        if ((rc = ensure(ctx, ctx->jobs, (n_jobs + n_therm_desc) * sizeof(jz::JobDesc))))
+            return rc;
     }
+    // one HBM lattice buffer serves the thermalisation chunks and then, on the
+    // same stream, the protocol: sized for both before either launches
+    size_t hbm_bytes = 0;
+    if (in_hbm)
+        hbm_bytes = sw ? (size_t)n_cta * jz::sw_smem_bytes(g)
+                       : (size_t)n_cta * sh.teams * 2 * g.NR * g.GW * sizeof(uint32_t);
+    if (therm_hbm) hbm_bytes = std::max(hbm_bytes, (size_t)chunk * jz::sw_smem_bytes(g));
+    if (hbm_bytes && (rc = ensure(ctx, ctx->lattice, hbm_bytes))) return rc;
 
     const Range nv_group("jz run group");
     nvtxRangePushA("jz tables");   // host FP64 threshold tables (popped after the loop)
@@ -521,9 +537,10 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
         // start geometry, no protocol steps (k_end = 0, so no step table is
         // read), final spins into ctx->therm; their W_int (zero) lands in the
         // outputs that the protocol launch then overwrites
-        ctx->h_jobs.resize((size_t)2 * n_jobs);
+        ctx->h_jobs.resize(n_jobs + n_therm_desc);
         std::vector<uint32_t> bt;
         long long sw_cta = 0;
+        size_t t = n_jobs;
         for (int i = 0; i < n_jobs; ++i) {
             const jz_params& p = jobs[idx[i]];
             jz::JobDesc T = ctx->h_jobs[i];
@@ -534,10 +551,18 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
             T.start_in = 0;
             T.spins_in = nullptr;
             T.w_in = nullptr;
-            T.spins_out = (int8_t*)ctx->h_jobs[i].spins_in;   // this job's slice of ctx->therm
-            T.cta0 = sw_cta;
-            sw_cta += T.n_traj;
-            ctx->h_jobs[n_jobs + i] = T;
+            int8_t* so = (int8_t*)ctx->h_jobs[i].spins_in;   // this job's slice of ctx->therm
+            const long long step = therm_hbm ? chunk : p.n_traj;
+            for (long long off = 0; off < p.n_traj; off += step) {
+                jz::JobDesc C = T;
+                C.n_traj = (int)std::min<long long>(step, p.n_traj - off);
+                C.traj0 = T.traj0 + off;
+                C.w_out = T.w_out + off;
+                C.spins_out = so + off * (long long)V;
+                C.cta0 = therm_hbm ? 0 : sw_cta;   // HBM chunks launch one at a time
+                sw_cta += C.n_traj;
+                ctx->h_jobs[t++] = C;
+            }
         }
     }
     nvtxRangePop();
@@ -554,26 +579,25 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
         if ((rc = cuda_err(cudaEventRecord(ctx->ev_k0, st)))) return rc;
         ctx->k_open = false;
     }
-    if (hybrid &&
+    if (hybrid && !therm_hbm &&
         (rc = cuda_err(jz::launch_sw(p0.d, g, K, (const jz::JobDesc*)ctx->jobs.ptr + n_jobs,
                                      n_jobs, n_traj_all, st, nullptr))))
         return rc;
+    for (size_t t = 0; therm_hbm && t < n_therm_desc; ++t)
+        if ((rc = cuda_err(jz::launch_sw(p0.d, g, K,
+                                         (const jz::JobDesc*)ctx->jobs.ptr + n_jobs + t, 1,
+                                         ctx->h_jobs[n_jobs + t].n_traj, st,
+                                         (uint32_t*)ctx->lattice.ptr))))
+            return rc;
     if (sw) {
         uint32_t* gS = nullptr;
-        if (in_hbm) {
-            if ((rc = ensure(ctx, ctx->lattice, (size_t)n_cta * jz::sw_smem_bytes(g)))) return rc;
-            gS = (uint32_t*)ctx->lattice.ptr;
-        }
+        if (in_hbm) gS = (uint32_t*)ctx->lattice.ptr;
         if ((rc = cuda_err(jz::launch_sw(p0.d, g, K, (const jz::JobDesc*)ctx->jobs.ptr, n_jobs,
                                          n_cta, st, gS))))
             return rc;
     } else {
         uint32_t* gS = nullptr;
-        if (in_hbm) {
-            const size_t words = (size_t)n_cta * sh.teams * 2 * g.NR * g.GW;
-            if ((rc = ensure(ctx, ctx->lattice, words * sizeof(uint32_t)))) return rc;
-            gS = (uint32_t*)ctx->lattice.ptr;
-        }
+        if (in_hbm) gS = (uint32_t*)ctx->lattice.ptr;
         if ((rc = cuda_err(jz::launch_traj(p0.d, g, K, (const jz::JobDesc*)ctx->jobs.ptr,
                                            n_jobs, n_cta, sh, st, gS))))
             return rc;

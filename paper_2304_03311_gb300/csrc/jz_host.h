@@ -33,6 +33,10 @@ cudaError_t launch_estimator(const long long* w_int, int n, double scale, int di
 size_t sw_smem_bytes(const Geom& g);
 // Threads of one Swendsen-Wang CTA (one trajectory) for dimension D.
 int sw_cta_threads(int D);
+// Trajectories one launch of the HBM Swendsen-Wang variant keeps resident on
+// the device at once (its occupancy x SMs): the chunk in which lattices beyond
+// shared memory are thermalised, so that their HBM state stays one wave.
+long long sw_hbm_wave(int D);
 // gS: nullptr to keep each trajectory's state in shared memory, else an HBM
 // buffer of n_cta * sw_smem_bytes(g) bytes, one slice per CTA.
 cudaError_t launch_sw(int D, const Geom& g, const PhiloxKeys& K, const JobDesc* jobs,

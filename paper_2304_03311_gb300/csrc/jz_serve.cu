@@ -47,7 +47,8 @@ struct Slot {
     std::vector<uint32_t> tcut;        // host table build area
     uint32_t* h_tcut = nullptr;        // pinned staging
     size_t h_tcut_cap = 0;             // words
-    jz::JobDesc* h_desc = nullptr;     // pinned, two descriptors
+    jz::JobDesc* h_desc = nullptr;     // pinned descriptors: the job's, then its
+    size_t h_desc_cap = 0;             // thermalisation launches' (capacity)
     double* h_est = nullptr;           // pinned, 3 doubles
     int64_t* h_work = nullptr;         // pinned
     size_t h_work_cap = 0;             // entries
@@ -62,16 +63,43 @@ size_t tcut_words(const jz_params& p)
 
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// A job's device memory, in order: its thresholds, two job descriptors (the
-// second for a Swendsen-Wang thermalisation launch), W_int, the estimator's
-// output, and for therm_update = 1 the thermalised spins (n_traj V bytes).
-constexpr size_t kDescBytes = (2 * sizeof(jz::JobDesc) + 255) & ~(size_t)255;
-size_t job_bytes(const jz_params& p)
+// A job's device memory, in order (byte offsets, 256-byte aligned): its
+// thresholds, its job descriptors (its own, then one per thermalisation
+// launch), W_int, the estimator's output, and for therm_update = 1 the
+// thermalised spins (n_traj V bytes) and, when the Swendsen-Wang state does
+// not fit shared memory, the HBM slices of one thermalisation chunk (one
+// resident wave of trajectories, wave[d - 2]).
+struct JobMem {
+    size_t desc = 0, work = 0, est = 0, spins = 0, lattice = 0, total = 0;
+    long long chunk = 0;      // trajectories per thermalisation launch (0: none)
+    size_t n_desc = 1;
+    bool therm_hbm = false;
+};
+
+JobMem job_mem(const jz_params& p, const long long wave[2])
 {
-    const size_t tcut = tcut_words(p) * sizeof(uint32_t);
-    const size_t V = (size_t)nrep_of(p) * p.L_t * (p.d == 3 ? p.L : 1) * p.L;
-    return round256(tcut) + kDescBytes + round256((size_t)p.n_traj * sizeof(int64_t)) + 256 +
-           (sw_therm(p) ? (size_t)p.n_traj * V : 0);
+    JobMem m;
+    const jz::Geom g = make_geom(p.d, p.L, p.L_t, nrep_of(p));
+    const size_t V = (size_t)g.nrep * g.Lt * g.Ly * g.L;
+    const bool hybrid = sw_therm(p);
+    m.therm_hbm = hybrid && !sw_fits(g);
+    if (hybrid) {
+        m.chunk = m.therm_hbm ? std::min<long long>(p.n_traj, wave[p.d - 2]) : p.n_traj;
+        m.n_desc = 1 + (size_t)((p.n_traj + m.chunk - 1) / m.chunk);
+    }
+    size_t o = round256(tcut_words(p) * sizeof(uint32_t));
+    m.desc = o;
+    o += round256(m.n_desc * sizeof(jz::JobDesc));
+    m.work = o;
+    o += round256((size_t)p.n_traj * sizeof(int64_t));
+    m.est = o;
+    o += 256;
+    m.spins = o;
+    o += hybrid ? round256((size_t)p.n_traj * V) : 0;
+    m.lattice = o;
+    o += m.therm_hbm ? (size_t)m.chunk * jz::sw_smem_bytes(g) : 0;
+    m.total = o;
+    return m;
 }
 
 int grow_pinned(void** p, size_t* cap, size_t want, size_t elem)
@@ -102,6 +130,7 @@ struct jz_server {
     bool stop = false;
     std::thread worker;
     Clock::time_point t0;
+    long long wave[2] = {1, 1};   // resident HBM Swendsen-Wang CTAs on the device, 2D and 3D
     FILE* log = nullptr;      // jz_server_set_log: one JSON line per finished job
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
@@ -125,6 +154,19 @@ void jz_server::finish(uint64_t id, Job& j)
     cv_done.notify_all();
 }
 
+// The thermalisation launches of a job (none without therm_update = 1), on
+// its slot's stream: descriptors 1 .. n_desc - 1, one chunk each.
+int therm_launches(const jz_params& p, const jz::Geom& g, const jz::PhiloxKeys& K,
+                   const jz::JobDesc* d_desc, const JobMem& m, uint32_t* d_lat, const Slot& s)
+{
+    for (size_t c = 1; c < m.n_desc; ++c) {
+        const int rc = cuda_err(jz::launch_sw(p.d, g, K, d_desc + c, 1, s.h_desc[c].n_traj,
+                                              s.stream, d_lat));
+        if (rc) return rc;
+    }
+    return ISING_OK;
+}
+
 // Enqueues one job on its slot's stream.  Called without the lock; the job
 // record is stable (held by unique_ptr) and not touched by other threads
 // while it is running.
@@ -134,8 +176,10 @@ int jz_server::launch(Slot& s, Job& j)
     const jz::Geom g = make_geom(p.d, p.L, p.L_t, nrep_of(p));
     const size_t n_tcut = tcut_words(p);
     int rc;
+    const JobMem m = job_mem(p, wave);
     if ((rc = grow_pinned((void**)&s.h_tcut, &s.h_tcut_cap, n_tcut, sizeof(uint32_t))) ||
-        (rc = grow_pinned((void**)&s.h_work, &s.h_work_cap, (size_t)p.n_traj, sizeof(int64_t))))
+        (rc = grow_pinned((void**)&s.h_work, &s.h_work_cap, (size_t)p.n_traj, sizeof(int64_t))) ||
+        (rc = grow_pinned((void**)&s.h_desc, &s.h_desc_cap, m.n_desc, sizeof(jz::JobDesc))))
         return rc;
     s.tcut.assign(n_tcut, 0);
     jz::JobDesc& J = *s.h_desc;
@@ -145,14 +189,14 @@ int jz_server::launch(Slot& s, Job& j)
     std::memcpy(s.h_tcut, s.tcut.data(), n_tcut * sizeof(uint32_t));
     char* d = nullptr;
     if ((rc = cuda_err(cudaMallocAsync((void**)&d, j.need, s.stream)))) return rc;
-    const size_t tcut_bytes = round256(n_tcut * sizeof(uint32_t));
-    const size_t work_bytes = round256((size_t)p.n_traj * sizeof(int64_t));
     uint32_t* d_tcut = (uint32_t*)d;
-    jz::JobDesc* d_desc = (jz::JobDesc*)(d + tcut_bytes);
-    long long* d_work = (long long*)(d + tcut_bytes + kDescBytes);
-    double* d_est = (double*)(d + tcut_bytes + kDescBytes + work_bytes);
-    int8_t* d_spins = (int8_t*)(d + tcut_bytes + kDescBytes + work_bytes + 256);
+    jz::JobDesc* d_desc = (jz::JobDesc*)(d + m.desc);
+    long long* d_work = (long long*)(d + m.work);
+    double* d_est = (double*)(d + m.est);
+    int8_t* d_spins = (int8_t*)(d + m.spins);
+    uint32_t* d_lat = m.therm_hbm ? (uint32_t*)(d + m.lattice) : nullptr;
     const bool hybrid = sw_therm(p);
+    const long long V = (long long)g.nrep * g.Lt * g.Ly * g.L;
     J.l = p.l;
     J.n_step = p.n_step;
     J.n_sweep = p.n_sweep;
@@ -169,14 +213,22 @@ int jz_server::launch(Slot& s, Job& j)
     J.w_out = d_work;
     J.spins_out = nullptr;
     if (hybrid) {
-        // Swendsen-Wang thermalisation (no protocol steps) into d_spins, from
-        // which the Metropolis protocol starts
-        jz::JobDesc& T = s.h_desc[1];
-        T = J;
+        // Swendsen-Wang thermalisation (no protocol steps) into d_spins, one
+        // launch per chunk of trajectories, from which the Metropolis
+        // protocol starts
+        jz::JobDesc T = J;
         std::vector<uint32_t> bt((size_t)2 * p.n_step);
         build_bond_tables(p, T.tb, bt, 0);
         T.k_end = 0;
-        T.spins_out = d_spins;
+        for (size_t c = 1; c < m.n_desc; ++c) {
+            const long long off = (long long)(c - 1) * m.chunk;
+            jz::JobDesc& C = s.h_desc[c];
+            C = T;
+            C.n_traj = (int)std::min<long long>(m.chunk, p.n_traj - off);
+            C.traj0 = T.traj0 + off;
+            C.w_out = d_work + off;
+            C.spins_out = d_spins + off * V;
+        }
         J.start_in = 1;
         J.spins_in = d_spins;
     }
@@ -185,10 +237,9 @@ int jz_server::launch(Slot& s, Job& j)
     const int B = p.n_traj < 32 ? p.n_traj : 32;
     if ((rc = cuda_err(cudaMemcpyAsync(d_tcut, s.h_tcut, n_tcut * sizeof(uint32_t),
                                        cudaMemcpyHostToDevice, s.stream))) ||
-        (rc = cuda_err(cudaMemcpyAsync(d_desc, s.h_desc, (hybrid ? 2 : 1) * sizeof(jz::JobDesc),
+        (rc = cuda_err(cudaMemcpyAsync(d_desc, s.h_desc, m.n_desc * sizeof(jz::JobDesc),
                                        cudaMemcpyHostToDevice, s.stream))) ||
-        (hybrid &&
-         (rc = cuda_err(jz::launch_sw(p.d, g, K, d_desc + 1, 1, p.n_traj, s.stream)))) ||
+        (rc = therm_launches(p, g, K, d_desc, m, d_lat, s)) ||
         (rc = cuda_err(p.update == 1   // Swendsen-Wang: one trajectory per CTA
                            ? jz::launch_sw(p.d, g, K, d_desc, 1, p.n_traj, s.stream)
                            : jz::launch_traj(p.d, g, K, d_desc, 1,
@@ -307,7 +358,7 @@ int jz_server_create(ising_ctx* ctx, size_t hbm_budget_bytes, int max_inflight, 
     for (Slot& sl : s->slots) {
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
-            cudaMallocHost((void**)&sl.h_desc, 2 * sizeof(jz::JobDesc)) != cudaSuccess ||
+            grow_pinned((void**)&sl.h_desc, &sl.h_desc_cap, 2, sizeof(jz::JobDesc)) != ISING_OK ||
             cudaMallocHost((void**)&sl.h_est, 4 * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
             for (Slot& t : s->slots) {
@@ -320,6 +371,8 @@ int jz_server_create(ising_ctx* ctx, size_t hbm_budget_bytes, int max_inflight, 
         }
     }
     s->t0 = Clock::now();
+    s->wave[0] = jz::sw_hbm_wave(2);
+    s->wave[1] = jz::sw_hbm_wave(3);
     jz_server* raw = s.release();
     raw->worker = std::thread([raw] { raw->run(); });
     *out = raw;
@@ -333,11 +386,10 @@ int jz_submit(jz_server* s, const jz_params* p, uint64_t* job_id)
     if (rc) return rc;
     const jz::Geom g = make_geom(p->d, p->L, p->L_t, nrep_of(*p));
     if (p->update == 1 ? !sw_fits(g) : !shape_fits(g)) return ISING_ERR_UNSUPPORTED;
-    if (sw_therm(*p) && !sw_fits(g)) return ISING_ERR_UNSUPPORTED;
     std::unique_ptr<Job> j(new (std::nothrow) Job());
     if (!j) return ISING_ERR_NOMEM;
     j->p = *p;
-    j->need = job_bytes(*p);
+    j->need = job_mem(*p, s->wave).total;
     j->res.status = ISING_ERR_PENDING;
     j->res.updates = (long long)p->n_traj * ((long long)g.nrep * p->L_t * g.Ly * p->L) *
                      ((long long)p->n_therm + (long long)p->n_step * p->n_sweep);

@@ -432,6 +432,20 @@ SwGeom make_swgeom(int D, const Geom& geo)
 
 int sw_cta_threads(int D) { return sw_threads(D); }
 
+long long sw_hbm_wave(int D)
+{
+    int dev = 0, n_sm = 0, per_sm = 0;
+    auto kern = D == 3 ? sw_kernel<3, true> : sw_kernel<2, true>;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, sw_threads(D), 0) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return sw_min_ctas(D, true);
+    }
+    return (long long)n_sm * (per_sm > 0 ? per_sm : 1);
+}
+
 cudaError_t bounds_status_sw(unsigned int out[2], bool clear)
 {
 #ifdef JZ_BOUNDS_CHECK

@@ -217,6 +217,39 @@ def test_full_scan_from_a_swendsen_wang_start_sampled(ctx):
             assert res[l][t] == Wo[0], (l, t)
 
 
+def test_state_beyond_shared_memory_thermalises_from_hbm_in_chunks(ctx):
+    """2D L = 128, L_t = 8L: its Swendsen-Wang state (1.2 MB) lives in HBM
+    slices, one resident wave of trajectories per thermalisation launch; 770
+    trajectories span two launches on GB300.  Trajectories on both sides of
+    the chunk boundary, and the last one, keep the oracle's bits."""
+    j = wl.Job(2, 128, 1024, BC2, 40, 2, 1, 770, seed=21, n_therm=2, therm_update=H)
+    w = torch.empty(j.n_traj, dtype=torch.int64, device="cuda")
+    jz.jarzynski_run_ex(ctx, params(j), w)
+    jz.ising_sync(ctx)
+    W = w.cpu().numpy()
+    for t in (0, 1, 758, 759, 760, 761, 769):
+        Wo, _ = oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, 1, j.seed,
+                           n_therm=j.n_therm, traj0=j.traj0 + t, therm_update=H)
+        assert W[t] == Wo[0], t
+
+
+def test_server_thermalises_a_large_state_from_hbm(ctx):
+    """2D L = 96, L_t = 4L (73,728 sites: a Swendsen-Wang state beyond shared
+    memory, a Metropolis lattice within it) through the server: spins and
+    HBM slices charged to the job, the oracle's bits."""
+    j = wl.Job(2, 96, 384, BC2, 30, 3, 1, 5, seed=23, n_therm=3, therm_update=H)
+    server = jz.jz_server_create(ctx, 1 << 30, 2)
+    try:
+        i = jz.jz_submit(server, params(j))
+        assert jz.jz_wait(server, i, 600.0).status == 0
+        w = np.empty(j.n_traj, dtype=np.int64)
+        jz.jz_server_work(server, i, w)
+    finally:
+        jz.jz_server_free(server)
+    Wo, _ = oracle_run(j)
+    np.testing.assert_array_equal(w, Wo)
+
+
 def test_entry_points_that_do_not_serve_it_refuse(ctx):
     j = JOBS[0]
     p = params(j)
@@ -226,10 +259,11 @@ def test_entry_points_that_do_not_serve_it_refuse(ctx):
         with pytest.raises(jz.IsingError) as e:
             call()
         assert e.value.code == jz.ISING_ERR_UNSUPPORTED
-    # a Swendsen-Wang state beyond shared memory (2D L = 128, L_t = 8L)
+    # persistent plans: a Swendsen-Wang state beyond shared memory (2D L = 128,
+    # L_t = 8L)
     big = jz.make_params(2, 128, 1024, BC2, 5, 2, 1, 2, 0, n_therm=2, therm_update=H)
     with pytest.raises(jz.IsingError) as e:
-        jz.jarzynski_run_ex(ctx, big, torch.empty(2, dtype=torch.int64, device="cuda"))
+        jz.jz_plan_create(ctx, [big], [torch.empty(2, dtype=torch.int64, device="cuda")])
     assert e.value.code == jz.ISING_ERR_UNSUPPORTED
     bad = jz.make_params(2, 8, 8, BC2, 1, 2, 1, 2, 0, therm_update=2)
     with pytest.raises(jz.IsingError) as e:
