@@ -815,11 +815,15 @@ def run_serve(args):
     import paper_2304_03311_gb300 as jz
 
     arrivals = wl.config5(n_jobs=args.serve_jobs, rate=args.rate)
+    if args.n_therm is not None:
+        arrivals = [(t, j.with_(n_therm=args.n_therm)) for t, j in arrivals]
+    if args.therm_update:
+        arrivals = [(t, j.with_(therm_update=1)) for t, j in arrivals]
     ctx = jz.ising_replica_init(0, 0, None)
     server = jz.jz_server_create(ctx, args.serve_budget_mb << 20, args.inflight)
     mk = lambda j: jz.make_params(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, j.n_traj,
                                   j.seed, n_therm=j.n_therm, direction=j.direction,
-                                  traj0=j.traj0)
+                                  traj0=j.traj0, therm_update=j.therm_update)
     # warm-up: one small job per dimension through the same server
     for j in (wl.Job(2, 32, 32, wl.BETA_C_2D, 3, 20, 1, 64), wl.Job(3, 8, 8, wl.BETA_C_3D, 2, 20, 1, 64)):
         jz.jz_wait(server, jz.jz_submit(server, mk(j)))
@@ -854,7 +858,9 @@ def run_serve(args):
             "steps": 1, "warmup": 1, "ms_per_step": makespan * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic (Philox hot starts; no dataset)",
-            "config": {"workload": f"served_stream_poisson{args.rate:g}_jobs{len(ids)}",
+            "config": {"workload": f"served_stream_poisson{args.rate:g}_jobs{len(ids)}" +
+                                   (f"_therm{args.n_therm}" if args.n_therm is not None else "") +
+                                   ("_swtherm" if args.therm_update else ""),
                        "inflight_slots": args.inflight, "hbm_budget_mb": args.serve_budget_mb,
                        "source_config": 5},
             "latency_s": {"p50": pct(0.50), "p99": pct(0.99), "max": lat[-1]},
