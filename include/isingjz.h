@@ -130,13 +130,12 @@ typedef struct ising_ctx ising_ctx;
  *              of each update.  Served by jarzynski_run_ex, jarzynski_run_batch,
  *              jarzynski_run_segment (a segment from k_begin = 0) and the
  *              server (jz_submit; the job's memory then includes n_traj V
- *              bytes of thermalised spins): a Swendsen-Wang state beyond
- *              shared memory is thermalised from HBM slices, in launches of
- *              one resident wave of trajectories, whose slices the server also
- *              charges to the job.  The persistent plans serve it for lattices
- *              whose Swendsen-Wang state fits shared memory (a thermalisation
- *              launch per lattice shape ahead of the persistent kernel).
- *              jarzynski_run_plain and jarzynski_run_noalloc return
+ *              bytes of thermalised spins) and the persistent plans (the
+ *              thermalisation launches ahead of the persistent kernel, in its
+ *              graph).  A Swendsen-Wang state beyond shared memory is
+ *              thermalised from HBM slices, in launches of one resident wave
+ *              of trajectories, whose slices the server also charges to the
+ *              job.  jarzynski_run_plain and jarzynski_run_noalloc return
  *              ISING_ERR_UNSUPPORTED.  Other values: ISING_ERR_ARG. */
 typedef struct jz_params {
     int d, L, L_t;

@@ -1266,6 +1266,7 @@ struct jz_plan {
         jz::Geom g{};
         int d = 0, n_jobs = 0;
         long long n_cta = 0;
+        bool hbm = false;   // thermalisation from HBM slices: one launch per descriptor
         DevBuf jobs;
         std::vector<jz::JobDesc> h_jobs;
         std::vector<size_t> toff;
@@ -1276,6 +1277,7 @@ struct jz_plan {
     // lattice shape) ahead of the persistent kernel, their spins in therm_spins
     std::vector<SwGroup> therm;
     DevBuf therm_spins;
+    DevBuf therm_lattice;   // HBM slices of one thermalisation wave (the largest one)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -1293,6 +1295,7 @@ void plan_release(jz_plan* pl)
     for (auto& G : pl->sw) bufs.push_back(&G.jobs);
     for (auto& G : pl->therm) bufs.push_back(&G.jobs);
     bufs.push_back(&pl->therm_spins);
+    bufs.push_back(&pl->therm_lattice);
     for (DevBuf* b : bufs)
         if (b->ptr) {
             cudaFree(b->ptr);
@@ -1321,6 +1324,7 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
     // therm_update = 1 jobs: byte offset of each job's spins in therm_spins
     std::vector<long long> therm_off(n_jobs, -1);
     size_t therm_bytes = 0;
+    size_t therm_lattice_bytes = 0;
     auto group_of = [](std::vector<jz_plan::SwGroup>& gs, int d, const jz::Geom& g) {
         size_t gi = 0;
         while (gi < gs.size() && !(gs[gi].d == d && gs[gi].g.L == g.L && gs[gi].g.Lt == g.Lt &&
@@ -1330,6 +1334,7 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
             gs.emplace_back();
             gs.back().g = g;
             gs.back().d = d;
+            gs.back().hbm = !sw_fits(g);
         }
         return gi;
     };
@@ -1402,21 +1407,30 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
         J.spins_out = nullptr;
         if (sw_therm(p)) {
             // its Swendsen-Wang thermalisation: no protocol steps, spins into
-            // its slice of therm_spins, from which the persistent kernel starts
-            if (!sw_fits(B.g)) {
-                plan_release(pl);
-                return ISING_ERR_UNSUPPORTED;
-            }
+            // its slice of therm_spins, from which the persistent kernel
+            // starts; a state beyond shared memory runs from HBM slices in
+            // launches of one resident wave of trajectories
             jz_plan::SwGroup& G = pl->therm[group_of(pl->therm, p.d, B.g)];
             jz::JobDesc T = J;
             std::vector<uint32_t> bt((size_t)2 * p.n_step);
             build_bond_tables(p, T.tb, bt, 0);
             T.k_end = 0;
-            T.cta0 = G.n_cta;
-            G.h_jobs.push_back(T);
-            G.toff.push_back((size_t)j);   // the job whose spins it writes
-            G.n_cta += p.n_traj;
-            ++G.n_jobs;
+            const long long step = G.hbm ? jz::sw_hbm_wave(p.d) : p.n_traj;
+            if (G.hbm)
+                therm_lattice_bytes = std::max(therm_lattice_bytes,
+                                               (size_t)std::min<long long>(step, p.n_traj) *
+                                                   jz::sw_smem_bytes(B.g));
+            for (long long off = 0; off < p.n_traj; off += step) {
+                jz::JobDesc C = T;
+                C.n_traj = (int)std::min<long long>(step, p.n_traj - off);
+                C.traj0 = T.traj0 + off;
+                C.w_out = T.w_out + off;
+                C.cta0 = G.hbm ? 0 : G.n_cta;
+                G.h_jobs.push_back(C);
+                G.toff.push_back(((size_t)j << 32) | (size_t)off);   // job, first trajectory
+                G.n_cta += C.n_traj;
+                ++G.n_jobs;
+            }
             therm_off[j] = (long long)therm_bytes;
             therm_bytes += (size_t)p.n_traj * (size_t)(B.g.nrep * p.L_t * B.g.Ly * p.L);
             J.start_in = 1;
@@ -1451,14 +1465,19 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
             plan_release(pl);
             return rc;
         }
+        if (therm_lattice_bytes && (rc = ensure(ctx, pl->therm_lattice, therm_lattice_bytes))) {
+            plan_release(pl);
+            return rc;
+        }
         int8_t* base = (int8_t*)pl->therm_spins.ptr;
         for (int j = 0; j < n_jobs; ++j)
             if (therm_off[j] >= 0) bj[j].J.spins_in = base + therm_off[j];
         for (auto& G : pl->therm) {
             for (size_t i = 0; i < G.h_jobs.size(); ++i) {
-                const size_t j = G.toff[i];
+                const size_t j = G.toff[i] >> 32, off = G.toff[i] & 0xFFFFFFFFu;
+                const long long V = (long long)G.g.nrep * G.g.Lt * G.g.Ly * G.g.L;
                 G.h_jobs[i].tcut = bj[j].J.tcut;   // not read: no protocol steps
-                G.h_jobs[i].spins_out = base + therm_off[j];
+                G.h_jobs[i].spins_out = base + therm_off[j] + (long long)off * V;
             }
             if ((rc = ensure(ctx, G.jobs, G.h_jobs.size() * sizeof(jz::JobDesc)))) {
                 plan_release(pl);
@@ -1535,10 +1554,20 @@ int plan_enqueue(jz_plan* pl)
 {
     cudaStream_t st = pl->ctx->stream;
     int rc;
-    for (const auto& G : pl->therm)
-        if ((rc = cuda_err(jz::launch_sw(G.d, G.g, pl->K, (const jz::JobDesc*)G.jobs.ptr,
-                                         G.n_jobs, G.n_cta, st))))
-            return rc;
+    for (const auto& G : pl->therm) {
+        if (!G.hbm) {
+            if ((rc = cuda_err(jz::launch_sw(G.d, G.g, pl->K, (const jz::JobDesc*)G.jobs.ptr,
+                                             G.n_jobs, G.n_cta, st))))
+                return rc;
+            continue;
+        }
+        for (int i = 0; i < G.n_jobs; ++i)
+            if ((rc = cuda_err(jz::launch_sw(G.d, G.g, pl->K,
+                                             (const jz::JobDesc*)G.jobs.ptr + i, 1,
+                                             G.h_jobs[i].n_traj, st,
+                                             (uint32_t*)pl->therm_lattice.ptr))))
+                return rc;
+    }
     if (pl->n_items > 0) {
         if ((rc = cuda_err(cudaMemsetAsync(pl->counter.ptr, 0, sizeof(unsigned int), st))))
             return rc;

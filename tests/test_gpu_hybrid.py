@@ -233,6 +233,33 @@ def test_state_beyond_shared_memory_thermalises_from_hbm_in_chunks(ctx):
         assert W[t] == Wo[0], t
 
 
+def test_plan_thermalises_a_large_state_from_hbm(ctx):
+    """A persistent plan with a 2D L = 128, L_t = 8L job from a Swendsen-Wang
+    start (HBM thermalisation waves inside the plan's graph) beside a small
+    one, replayed twice: trajectories on both sides of the chunk boundary
+    keep the oracle's bits."""
+    jobs = [wl.Job(2, 128, 1024, BC2, 40, 2, 1, 770, seed=21, n_therm=2, therm_update=H),
+            wl.Job(2, 16, 16, BC2, 4, 6, 1, 33, seed=21, n_therm=5, therm_update=H,
+                   traj0=1 << 20)]
+    outs = [torch.empty(j.n_traj, dtype=torch.int64, device="cuda") for j in jobs]
+    plan = jz.jz_plan_create(ctx, [params(j) for j in jobs], outs, None, 512)
+    try:
+        for _ in range(2):
+            for o in outs:
+                o.fill_(-9)
+            jz.jz_plan_launch(plan)
+            jz.ising_sync(ctx)
+            W0 = outs[0].cpu().numpy()
+            for t in (0, 759, 760, 769):
+                Wo, _ = oracle.run(2, 128, 1024, BC2, 40, 2, 1, 1, 21, n_therm=2, traj0=t,
+                                   therm_update=H)
+                assert W0[t] == Wo[0], t
+            Wo, _ = oracle_run(jobs[1])
+            np.testing.assert_array_equal(outs[1].cpu().numpy(), Wo)
+    finally:
+        jz.jz_plan_free(plan)
+
+
 def test_server_thermalises_a_large_state_from_hbm(ctx):
     """2D L = 96, L_t = 4L (73,728 sites: a Swendsen-Wang state beyond shared
     memory, a Metropolis lattice within it) through the server: spins and
@@ -259,12 +286,6 @@ def test_entry_points_that_do_not_serve_it_refuse(ctx):
         with pytest.raises(jz.IsingError) as e:
             call()
         assert e.value.code == jz.ISING_ERR_UNSUPPORTED
-    # persistent plans: a Swendsen-Wang state beyond shared memory (2D L = 128,
-    # L_t = 8L)
-    big = jz.make_params(2, 128, 1024, BC2, 5, 2, 1, 2, 0, n_therm=2, therm_update=H)
-    with pytest.raises(jz.IsingError) as e:
-        jz.jz_plan_create(ctx, [big], [torch.empty(2, dtype=torch.int64, device="cuda")])
-    assert e.value.code == jz.ISING_ERR_UNSUPPORTED
     bad = jz.make_params(2, 8, 8, BC2, 1, 2, 1, 2, 0, therm_update=2)
     with pytest.raises(jz.IsingError) as e:
         jz.jarzynski_run_ex(ctx, bad, torch.empty(2, dtype=torch.int64, device="cuda"))
