@@ -447,6 +447,13 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
     const bool hybrid = sw_therm(p0) && (!seg || seg->k_begin == 0);
     const bool therm_hbm = hybrid && !sw_fits(g);
     const long long chunk = therm_hbm ? jz::sw_hbm_wave(p0.d) : 0;
+    // HBM thermalisation launches: descriptors [first, first + n_desc) of the
+    // job table (pieces of consecutive jobs, CTAs numbered within the wave)
+    struct ThermWave {
+        size_t first, n_desc;
+        long long n_cta;
+    };
+    std::vector<ThermWave> therm_waves;
     long long n_traj_launch = 0;
     for (int j : idx) n_traj_launch += jobs[j].n_traj;
     jz::LaunchShape sh = sw ? shape_for(g, 0) : ctx_shape(ctx, p0.d, g, n_traj_launch);
@@ -474,8 +481,21 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
         return rc;
     size_t n_therm_desc = 0;   // thermalisation launches' job descriptors
     if (hybrid) {
-        for (int j : idx)
-            n_therm_desc += therm_hbm ? (size_t)((jobs[j].n_traj + chunk - 1) / chunk) : 1;
+        // HBM: the trajectories of all jobs, in order, cut into waves of
+        // `chunk`; a job contributes one descriptor per wave it reaches
+        long long fill = 0;
+        for (int j : idx) {
+            if (!therm_hbm) {
+                ++n_therm_desc;
+                continue;
+            }
+            for (long long off = 0; off < jobs[j].n_traj;) {
+                const long long take = std::min(chunk - fill, jobs[j].n_traj - off);
+                ++n_therm_desc;
+                off += take;
+                fill = (fill + take) % chunk;
+            }
+        }
         if ((rc = ensure(ctx, ctx->therm, (size_t)n_traj_all * V))) return rc;
         if ((rc = ensure(ctx, ctx->jobs, (n_jobs + n_therm_desc) * sizeof(jz::JobDesc))))
             return rc;
@@ -538,8 +558,9 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
         // read), final spins into ctx->therm; their W_int (zero) lands in the
         // outputs that the protocol launch then overwrites
         ctx->h_jobs.resize(n_jobs + n_therm_desc);
+        therm_waves.clear();
         std::vector<uint32_t> bt;
-        long long sw_cta = 0;
+        long long sw_cta = 0;   // HBM: CTAs filled in the current wave
         size_t t = n_jobs;
         for (int i = 0; i < n_jobs; ++i) {
             const jz_params& p = jobs[idx[i]];
@@ -552,16 +573,24 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
             T.spins_in = nullptr;
             T.w_in = nullptr;
             int8_t* so = (int8_t*)ctx->h_jobs[i].spins_in;   // this job's slice of ctx->therm
-            const long long step = therm_hbm ? chunk : p.n_traj;
-            for (long long off = 0; off < p.n_traj; off += step) {
+            for (long long off = 0; off < p.n_traj;) {
+                const long long take =
+                    therm_hbm ? std::min(chunk - sw_cta, (long long)p.n_traj - off) : p.n_traj;
                 jz::JobDesc C = T;
-                C.n_traj = (int)std::min<long long>(step, p.n_traj - off);
+                C.n_traj = (int)take;
                 C.traj0 = T.traj0 + off;
                 C.w_out = T.w_out + off;
                 C.spins_out = so + off * (long long)V;
-                C.cta0 = therm_hbm ? 0 : sw_cta;   // HBM chunks launch one at a time
-                sw_cta += C.n_traj;
+                C.cta0 = sw_cta;
+                if (therm_hbm && sw_cta == 0) therm_waves.push_back({t, 0, 0});
+                if (therm_hbm) {
+                    ++therm_waves.back().n_desc;
+                    therm_waves.back().n_cta += take;
+                }
                 ctx->h_jobs[t++] = C;
+                sw_cta += take;
+                if (therm_hbm && sw_cta == chunk) sw_cta = 0;   // the wave is full
+                off += take;
             }
         }
     }
@@ -583,10 +612,9 @@ int run_group(ising_ctx* ctx, const jz_params* jobs, const std::vector<int>& idx
         (rc = cuda_err(jz::launch_sw(p0.d, g, K, (const jz::JobDesc*)ctx->jobs.ptr + n_jobs,
                                      n_jobs, n_traj_all, st, nullptr))))
         return rc;
-    for (size_t t = 0; therm_hbm && t < n_therm_desc; ++t)
-        if ((rc = cuda_err(jz::launch_sw(p0.d, g, K,
-                                         (const jz::JobDesc*)ctx->jobs.ptr + n_jobs + t, 1,
-                                         ctx->h_jobs[n_jobs + t].n_traj, st,
+    for (const ThermWave& w : therm_waves)
+        if ((rc = cuda_err(jz::launch_sw(p0.d, g, K, (const jz::JobDesc*)ctx->jobs.ptr + w.first,
+                                         (int)w.n_desc, w.n_cta, st,
                                          (uint32_t*)ctx->lattice.ptr))))
             return rc;
     if (sw) {
@@ -1266,7 +1294,13 @@ struct jz_plan {
         jz::Geom g{};
         int d = 0, n_jobs = 0;
         long long n_cta = 0;
-        bool hbm = false;   // thermalisation from HBM slices: one launch per descriptor
+        bool hbm = false;   // thermalisation from HBM slices, in waves
+        long long wave = 0, fill = 0;   // hbm: trajectories per wave, CTAs in the open one
+        struct Wave {
+            int first, n_desc;
+            long long n_cta;
+        };
+        std::vector<Wave> waves;        // hbm: descriptor ranges launched together
         DevBuf jobs;
         std::vector<jz::JobDesc> h_jobs;
         std::vector<size_t> toff;
@@ -1335,6 +1369,7 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
             gs.back().g = g;
             gs.back().d = d;
             gs.back().hbm = !sw_fits(g);
+            if (gs.back().hbm) gs.back().wave = jz::sw_hbm_wave(d);
         }
         return gi;
     };
@@ -1415,21 +1450,30 @@ int plan_build(ising_ctx* ctx, const jz_params* jobs, int n_jobs, int64_t* const
             std::vector<uint32_t> bt((size_t)2 * p.n_step);
             build_bond_tables(p, T.tb, bt, 0);
             T.k_end = 0;
-            const long long step = G.hbm ? jz::sw_hbm_wave(p.d) : p.n_traj;
             if (G.hbm)
                 therm_lattice_bytes = std::max(therm_lattice_bytes,
-                                               (size_t)std::min<long long>(step, p.n_traj) *
-                                                   jz::sw_smem_bytes(B.g));
-            for (long long off = 0; off < p.n_traj; off += step) {
+                                               (size_t)G.wave * jz::sw_smem_bytes(B.g));
+            // pieces of this job's trajectories; in HBM they fill waves of
+            // G.wave CTAs shared with the group's other jobs
+            for (long long off = 0; off < p.n_traj;) {
+                const long long take =
+                    G.hbm ? std::min(G.wave - G.fill, (long long)p.n_traj - off) : p.n_traj;
                 jz::JobDesc C = T;
-                C.n_traj = (int)std::min<long long>(step, p.n_traj - off);
+                C.n_traj = (int)take;
                 C.traj0 = T.traj0 + off;
                 C.w_out = T.w_out + off;
-                C.cta0 = G.hbm ? 0 : G.n_cta;
+                C.cta0 = G.hbm ? G.fill : G.n_cta;
+                if (G.hbm && G.fill == 0) G.waves.push_back({G.n_jobs, 0, 0});
+                if (G.hbm) {
+                    ++G.waves.back().n_desc;
+                    G.waves.back().n_cta += take;
+                    G.fill = (G.fill + take) % G.wave;
+                }
                 G.h_jobs.push_back(C);
                 G.toff.push_back(((size_t)j << 32) | (size_t)off);   // job, first trajectory
-                G.n_cta += C.n_traj;
+                G.n_cta += take;
                 ++G.n_jobs;
+                off += take;
             }
             therm_off[j] = (long long)therm_bytes;
             therm_bytes += (size_t)p.n_traj * (size_t)(B.g.nrep * p.L_t * B.g.Ly * p.L);
@@ -1561,11 +1605,10 @@ int plan_enqueue(jz_plan* pl)
                 return rc;
             continue;
         }
-        for (int i = 0; i < G.n_jobs; ++i)
+        for (const auto& w : G.waves)
             if ((rc = cuda_err(jz::launch_sw(G.d, G.g, pl->K,
-                                             (const jz::JobDesc*)G.jobs.ptr + i, 1,
-                                             G.h_jobs[i].n_traj, st,
-                                             (uint32_t*)pl->therm_lattice.ptr))))
+                                             (const jz::JobDesc*)G.jobs.ptr + w.first, w.n_desc,
+                                             w.n_cta, st, (uint32_t*)pl->therm_lattice.ptr))))
                 return rc;
     }
     if (pl->n_items > 0) {

@@ -233,6 +233,35 @@ def test_state_beyond_shared_memory_thermalises_from_hbm_in_chunks(ctx):
         assert W[t] == Wo[0], t
 
 
+@pytest.mark.parametrize("how", ["batch", "plan"])
+def test_waves_pack_pieces_of_several_jobs(ctx, how):
+    """Three 2D L = 128, L_t = 8L jobs of 300 trajectories from a
+    Swendsen-Wang start: their 900 trajectories fill the thermalisation waves
+    in order (on GB300 the first wave holds all of the first two jobs and 160
+    of the third), through the batch call and a plan; trajectories on every
+    piece boundary keep the oracle's bits."""
+    jobs = [wl.Job(2, 128, 1024, BC2, l, 2, 1, 300, seed=29, n_therm=2, therm_update=H,
+                   traj0=i << 20) for i, l in enumerate((10, 40, 70))]
+    outs = [torch.empty(j.n_traj, dtype=torch.int64, device="cuda") for j in jobs]
+    if how == "batch":
+        jz.jarzynski_run_batch(ctx, [params(j) for j in jobs], outs)
+        jz.ising_sync(ctx)
+    else:
+        plan = jz.jz_plan_create(ctx, [params(j) for j in jobs], outs, None, 512)
+        try:
+            jz.jz_plan_launch(plan)
+            jz.ising_sync(ctx)
+        finally:
+            jz.jz_plan_free(plan)
+    for i, ts in enumerate([(0, 299), (0, 299), (0, 159, 160, 299)]):
+        j = jobs[i]
+        W = outs[i].cpu().numpy()
+        for t in ts:
+            Wo, _ = oracle.run(j.d, j.L, j.L_t, j.beta, j.l, j.n_step, j.n_sweep, 1, j.seed,
+                               n_therm=j.n_therm, traj0=j.traj0 + t, therm_update=H)
+            assert W[t] == Wo[0], (i, t)
+
+
 def test_plan_thermalises_a_large_state_from_hbm(ctx):
     """A persistent plan with a 2D L = 128, L_t = 8L job from a Swendsen-Wang
     start (HBM thermalisation waves inside the plan's graph) beside a small
