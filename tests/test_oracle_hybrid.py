@@ -8,7 +8,8 @@ thermalises with cluster steps.  The oracle composes its two pinned updates:
 * Joint law of (W_int, final energy) over many oracle trajectories against the
   exact path measure of a hot start, n_therm exact Swendsen-Wang steps and the
   exact Metropolis protocol (2D L = L_t = 2, enumeration of all 256 states),
-  forward and reverse.  The same trajectories with Metropolis thermalisation
+  forward and reverse, for a moving end of region A and a whole cut.  The
+  same trajectories with Metropolis thermalisation
   fail it: from a hot start one or two steps of the two updates leave
   different laws.
 * With no thermalisation sweeps the option changes nothing (bit for bit).
@@ -36,11 +37,11 @@ CASES = [(2, 2, 2, 1, 3, 1, 1, 1), (2, 2, 2, 0, 2, 2, 2, -1)]
 
 
 @functools.lru_cache(maxsize=None)
-def _exact_joint(case, therm):
+def _exact_joint(case, therm, whole=False):
     d, L, L_t, l, N, ns, nth, dirn = case
     wv, F = ex.exact_path_measure(d, L, L_t, l, BETA_2D, N, ns, nth, direction=dirn,
-                                  therm=therm)
-    dyn = ex._Dynamics(d, L, L_t, l, BETA_2D, N, dirn, True, 1, 2, False)
+                                  therm=therm, whole=whole)
+    dyn = ex._Dynamics(d, L, L_t, l, BETA_2D, N, dirn, True, 1, 2, whole)
     e_vals, e_idx = np.unique(dyn.energy(1.0).astype(np.int64), return_inverse=True)
     P = np.zeros((len(wv), len(e_vals)))
     for j in range(len(e_vals)):
@@ -48,11 +49,11 @@ def _exact_joint(case, therm):
     return wv, P, e_idx
 
 
-def _pvalue(case, therm_update, exact_therm, n_traj=100_000, seed=9):
+def _pvalue(case, therm_update, exact_therm, n_traj=100_000, seed=9, whole=False):
     d, L, L_t, l, N, ns, nth, dirn = case
-    wv, P, e_idx = _exact_joint(case, exact_therm)
+    wv, P, e_idx = _exact_joint(case, exact_therm, whole)
     W, S = oracle.run(d, L, L_t, BETA_2D, l, N, ns, n_traj, seed, n_therm=nth, direction=dirn,
-                      want_spins=True, therm_update=therm_update)
+                      want_spins=True, therm_update=therm_update, whole=whole)
     flat = S.reshape(n_traj, -1)
     state = ((flat < 0).astype(np.int64) << np.arange(flat.shape[1])).sum(axis=1)
     O = np.zeros_like(P)
@@ -75,6 +76,16 @@ def test_exact_laws_of_the_two_thermalisations_differ():
 @pytest.mark.parametrize("case", CASES)
 def test_joint_law_matches_exact_path_measure(case):
     p, stray, stray_expected = _pvalue(case, SW, "sw")
+    assert p > 1e-4
+    assert stray <= stray_expected + 6 * math.sqrt(stray_expected + 1)
+
+
+@pytest.mark.parametrize("direction", [1, -1])
+def test_whole_cut_joint_law_matches_exact_path_measure(direction):
+    """The whole-cut transformation (both columns of 2D L = 2 switch from
+    decoupled to glued replicas) from a Swendsen-Wang start."""
+    case = (2, 2, 2, 2, 3, 1, 1, direction)
+    p, stray, stray_expected = _pvalue(case, SW, "sw", whole=True)
     assert p > 1e-4
     assert stray <= stray_expected + 6 * math.sqrt(stray_expected + 1)
 
