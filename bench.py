@@ -350,8 +350,9 @@ def device_facts(torch, local_rank):
     props = torch.cuda.get_device_properties(local_rank)
     mhz = None
     try:
-        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits",
-                              "-i", str(local_rank)], capture_output=True, text=True, timeout=20).stdout
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits", "-i", str(local_rank)],
+                             capture_output=True, text=True, timeout=20).stdout
         mhz = float(out.strip().splitlines()[0])
     except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
         mhz = None
@@ -428,7 +429,8 @@ class Scan:
                     self.tuned[str(shape)] = threads
                 elif autotune and j.update == 0:
                     try:
-                        self.tuned[str(shape)] = jz.ising_autotune(ctx, self.params[w.jobs.index(j)])
+                        p = self.params[w.jobs.index(j)]
+                        self.tuned[str(shape)] = jz.ising_autotune(ctx, p)
                     except jz.IsingError:   # lattices beyond shared memory are not tuned
                         self.tuned[str(shape)] = "default (lattice in HBM)"
 
@@ -636,7 +638,8 @@ def plain_baseline(jz, torch, ctx, dev, w, value, n):
     fw = torch.empty_like(pw)
     jz.jarzynski_run_ex(ctx, pp, fw)
     jz.ising_sync(ctx)
-    return {"value": j.updates / dt, "unit": UNIT, "sample": f"{j.n_traj} trajectories of l = {j.l}",
+    return {"value": j.updates / dt, "unit": UNIT,
+            "sample": f"{j.n_traj} trajectories of l = {j.l}",
             "seconds": dt, "bit_identical_to_fused": bool(torch.equal(pw, fw)),
             "speedup_of_fused": value / (j.updates / dt)}
 
@@ -825,7 +828,8 @@ def run_serve(args):
                                   j.seed, n_therm=j.n_therm, direction=j.direction,
                                   traj0=j.traj0, therm_update=j.therm_update)
     # warm-up: one small job per dimension through the same server
-    for j in (wl.Job(2, 32, 32, wl.BETA_C_2D, 3, 20, 1, 64), wl.Job(3, 8, 8, wl.BETA_C_3D, 2, 20, 1, 64)):
+    for j in (wl.Job(2, 32, 32, wl.BETA_C_2D, 3, 20, 1, 64),
+              wl.Job(3, 8, 8, wl.BETA_C_3D, 2, 20, 1, 64)):
         jz.jz_wait(server, jz.jz_submit(server, mk(j)))
     torch.cuda.synchronize()
     sampler = ClockSampler(0)
