@@ -412,7 +412,13 @@ class Scan:
         self.sw = all(j.update == 1 for j in w.jobs)
         self.outs = [torch.empty(j.n_traj, dtype=torch.int64, device=dev) for j in w.jobs]
         self.params = [job_params(jz, j) for j in w.jobs]
-        self.n_groups = len({(j.d, j.L, j.L_t, j.seed, j.update, j.n_replica) for j in w.jobs})
+        self.n_groups = len({(j.d, j.L, j.L_t, j.seed, j.update, j.n_replica, j.therm_update)
+                             for j in w.jobs})
+        # a launch group starting from Swendsen-Wang thermalisation adds its
+        # thermalisation launch (one while the state fits shared memory; a
+        # state beyond it adds one per wave of resident trajectories)
+        self.n_therm_launches = len({(j.d, j.L, j.L_t, j.seed, j.n_replica) for j in w.jobs
+                                     if j.therm_update and j.update == 0 and j.n_therm > 0})
         self.tuned = {}
         self.plan = None
         self.est = None
@@ -435,7 +441,9 @@ class Scan:
                         self.tuned[str(shape)] = "default (lattice in HBM)"
 
     def launches_per_step(self):
-        return 2 if self.plan is not None else self.n_groups + len(self.w.jobs)
+        if self.plan is not None:
+            return 2
+        return self.n_groups + self.n_therm_launches + len(self.w.jobs)
 
     def estimate(self, buffers):
         res = []
