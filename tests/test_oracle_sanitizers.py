@@ -1,7 +1,8 @@
 """The oracle under AddressSanitizer and UndefinedBehaviorSanitizer (host only).
 
 A copy of jz_oracle.c instrumented with -fsanitize=address,undefined (errors
-abort the process) runs small trajectories of every method option in a child
+abort the process) runs small trajectories of every method option (the
+Swendsen-Wang thermalisation before a Metropolis protocol included) in a child
 process that preloads the ASan runtime; it must finish cleanly and give the
 bits of the uninstrumented oracle."""
 import json
@@ -23,7 +24,7 @@ import oracle
 lib = oracle.load_library(sys.argv[2])
 cases = [dict(), dict(update=1), dict(protocol=2, d=3, L=4, L_t=4, l=1, n_step=8),
          dict(n_replica=3), dict(whole=True, update=1, l=4), dict(direction=-1),
-         dict(L=6, L_t=4, l=5)]
+         dict(L=6, L_t=4, l=5), dict(therm_update=1), dict(therm_update=1, d=3, L=4, L_t=4, l=1)]
 out = []
 for c in cases:
     kw = dict(d=2, L=8, L_t=8, beta=0.44068679350977147, l=3, n_step=6, n_sweep=1, n_traj=5, seed=9)
