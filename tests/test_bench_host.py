@@ -77,3 +77,19 @@ def test_fractions_against_the_three_ceilings():
             "philox_update_ceiling_per_s": 2e12}
     f = bench.fractions(20e12, 1e12, ceil)
     assert f == {"frac_derived": 0.5, "frac_probe": 20 / 36, "frac_philox_ceiling": 0.5}
+
+
+def test_swendsen_wang_start_option_marks_every_job():
+    """--therm-update 1 --n-therm 100: every job of the scan starts from
+    Swendsen-Wang thermalisation, the workload's name says so, and a
+    Swendsen-Wang scan ignores the option (its start is already one)."""
+    w = bench.workload_for(2, 0, n_therm=100, therm_update=1)
+    assert all(j.therm_update == 1 and j.n_therm == 100 and j.update == 0 for j in w.jobs)
+    assert w.name.endswith("_therm100_swtherm")
+    s = bench.workload_for(2, 0, update="sw", therm_update=1)
+    assert all(j.therm_update == 0 and j.update == 1 for j in s.jobs)
+    plain = bench.workload_for(2, 0)
+    assert all(j.therm_update == 0 for j in plain.jobs)
+    # rank 1 of a weak-scaling run owns the next trajectory range of every job
+    r1 = bench.workload_for(2, 1, therm_update=1)
+    assert all(a.traj0 == b.traj0 + b.n_traj for a, b in zip(r1.jobs, w.jobs))
